@@ -1,0 +1,222 @@
+/*
+ * pr.h -- C ABI of the GB300 (sm_103a) IFP1 / IFP2 PageRank library.
+ *
+ * Method: "Two Parallel PageRank Algorithms via Improving Forward Push"
+ * (Zhang, Tang, Yao, Liang; arXiv 2302.03245).  PageRank / personalized
+ * PageRank pi solves (I - cP')pi = (1-c)p with P' = P + p d^T (Sec. 2.1,
+ * Eq. 1-2).  IFP1 (Alg. 2) and IFP2 (Alg. 3) push residual mass along the
+ * out-edges of non-dangling vertices only and normalise the kept mass
+ * (Sec. 3.1, Eq. 4); the Power method on P'' (Sec. 4, "SPI") is the baseline.
+ *
+ * Conventions for every call:
+ *  - Every function returns a pr_status; nothing throws across the ABI.  On
+ *    any status other than PR_OK, pr_last_error() gives a message (per
+ *    calling thread).
+ *  - Vertex ids are int32 in [0, n); edge offsets are int32 (m < 2^31 per
+ *    graph).  Arrays are plain pointers; "device" means a CUDA device pointer
+ *    on the current device, "host" ordinary (pageable or pinned) memory.
+ *  - The library owns the device memory it allocates (through the allocator
+ *    installed with pr_set_allocator, else cudaMalloc) and never keeps a
+ *    pointer to caller memory after a call returns.
+ *  - A pr_graph and everything solved on it run on the CUDA stream given at
+ *    creation.  One graph must not be used by two host threads at once.
+ */
+#ifndef PR_H
+#define PR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph;   /* opaque: device copy of a graph + solver workspace */
+typedef struct pr_server pr_server; /* opaque: continuous-batching request loop */
+
+typedef enum {
+    PR_OK = 0,
+    PR_EINVAL = 1,   /* invalid argument (message names it) */
+    PR_ENOMEM = 2,   /* device or host allocation failed */
+    PR_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error) */
+    PR_ENOTCONV = 4, /* round/iteration cap reached, or no vertex could be activated;
+                        `out` still holds the best-effort result */
+    PR_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+    PR_EAGAIN = 6,   /* server: over the HBM budget and the queue is full */
+    PR_EBUSY = 7     /* server: request not finished yet */
+} pr_status;
+
+typedef enum {
+    PR_POWER = 0, /* Power method on P'' (Sec. 4, SPI) -- the baseline */
+    PR_IFP1 = 1,  /* Alg. 2 (Sec. 3.2) */
+    PR_IFP2 = 2   /* Alg. 3 (Sec. 3.4): no pushes into dangling vertices in phase 1,
+                     one pull into each dangling vertex in phase 2 */
+} pr_algo;
+
+typedef enum {
+    PR_FP64 = 0, /* residual, reserve and pushed mass in double */
+    PR_FP32 = 1  /* residual, reserve and pushed mass in float; residual-L1 and
+                    dangling sums in double; at the end an FP64 correction sweep
+                    recomputes the residual from the reserve and FP64 rounds
+                    finish the solve (not in the paper; the arithmetic identity
+                    is that of Eq. 4) */
+} pr_prec;
+
+typedef enum {
+    PR_MODE_AUTO = 0, /* per round: atomic push when the frontier is small, else CSC pull */
+    PR_MODE_PUSH = 1, /* always atomic push over the frontier's out-lists */
+    PR_MODE_PULL = 2  /* always deterministic gather over in-lists */
+} pr_mode;
+
+/*
+ * Personalization vector p (Sec. 2.1).  nnz < 0: uniform p = e/n.
+ * nnz == n and idx == NULL: dense val[n].  Otherwise sparse: val[k] at
+ * vertex idx[k], k < nnz, other entries 0.  Entries must be finite and >= 0
+ * with a positive sum; p is divided by its sum (the factor is reported in
+ * pr_stats.p_scale).  is_device: idx/val are device pointers.
+ */
+typedef struct {
+    int32_t nnz;
+    const int32_t *idx;
+    const double *val;
+    int32_t is_device;
+} pr_pvec;
+
+/* Per-solve report. */
+typedef struct {
+    int32_t rounds;        /* IFP phase-1 rounds (Sec. 3.3.1 "iteration"), or Power iterations */
+    int32_t rounds_push;   /* rounds delivered by atomic push */
+    int32_t rounds_pull;   /* rounds delivered by in-list gather */
+    int32_t fp64_rounds;   /* FP32 form: rounds run in FP64 after the correction sweep */
+    int64_t pushes;        /* sum over rounds of |F_t| (active vertices) */
+    int64_t edges_pushed;  /* sum over rounds of the active vertices' valid out-edges
+                              (the paper's m(t) without the +1, Sec. 3.3.3), plus the
+                              IFP2 phase-2 in-edges of dangling vertices */
+    int64_t edges_scanned; /* adjacency entries actually read by the delivery kernels */
+    double resid_l1;       /* non-dangling residual L1 R at stop (Power: last ||delta||_1) */
+    double dangling_mass;  /* sum of the residual on dangling vertices at stop (IFP1) */
+    double err_bound;      /* guaranteed L1 distance of `out` from the exact PageRank:
+                              IFP1 2cR/(1-c), IFP2 2R/(1-c), Power c*delta/(1-c) */
+    double ms;             /* device time of the solve, CUDA events on the graph's stream */
+    double p_scale;        /* 1 / sum(p) as given */
+    int64_t launches;      /* kernels the solve launched (including those inside CUDA graphs) */
+} pr_stats;
+
+/* Kernel kinds of a solve, for pr_kernel_profile. */
+enum {
+    PR_K_ACTIVATE = 0, /* frontier selection, residual L1, dense pending push */
+    PR_K_COMMIT = 1,   /* push rounds: reserve update of the frontier */
+    PR_K_PUSH = 2,     /* push rounds: atomic push along out-lists */
+    PR_K_PULL = 3,     /* pull rounds: gather along in-lists */
+    PR_K_POWER = 4,    /* Power method iteration */
+    PR_K_OTHER = 5,    /* init, correction, phase 2, finalize */
+    PR_K_KINDS = 8
+};
+
+/* Per-kernel CUDA-event timing of one solve (opts.profile).  launches[k]
+ * counts launches that did work (a round kernel that returned at once because
+ * the round used the other delivery mode is not counted); ms[k] is their
+ * summed duration. */
+typedef struct {
+    int32_t launches[PR_K_KINDS];
+    double ms[PR_K_KINDS];
+} pr_kernel_profile;
+
+/* Tuning and tracing.  Zero-initialise, then set fields; 0 means default. */
+typedef struct {
+    double xi_act;        /* activation threshold on |r_i| (Alg. 2/3 "h_i > xi");
+                             0 => eps / n_nd, which guarantees progress while R > eps */
+    int32_t max_rounds;   /* 0 => 100000 */
+    int32_t mode;         /* pr_mode */
+    double pull_ratio;    /* AUTO: pull when the frontier's out-edges >= pull_ratio * m;
+                             0 => 0.04 */
+    int32_t use_graph;    /* 0 or 1 => rounds run inside a CUDA graph with a device-side
+                             while loop (no host sync per round); -1 => host-driven rounds */
+    int32_t trace_cap;    /* length of the host trace arrays below (may be 0) */
+    double *trace_R;      /* [trace_cap] R_t at the start of round t */
+    int64_t *trace_F;     /* [trace_cap] |F_t| */
+    int64_t *trace_E;     /* [trace_cap] edges pushed in round t */
+    int8_t *trace_mode;   /* [trace_cap] 1 push, 2 pull */
+    pr_kernel_profile *profile; /* non-NULL: run the rounds from the host and time every
+                                   kernel launch with CUDA events on the graph's stream */
+} pr_opts;
+
+/* Static facts about a created graph (the paper's Table 1 columns and more). */
+typedef struct {
+    int32_t n, n_nd, n_ref, n_d, n_u; /* vertices; non-dangling; non-dangling with in-edges;
+                                         dangling; unreferenced (in-degree 0) */
+    int64_t m, m_d;                   /* edges; edges into dangling vertices */
+    int32_t max_outdeg, max_indeg;
+    double ms_preprocess;             /* device time of pr_graph_create (Table 2 analogue) */
+    size_t device_bytes;              /* graph storage held on the device */
+} pr_graph_info;
+
+/*
+ * Device memory hooks (optional).  alloc(bytes, stream, ctx) returns a device
+ * pointer or NULL; free(ptr, bytes, stream, ctx).  Passing NULL restores
+ * cudaMalloc/cudaFree.  Set it before creating graphs; every object frees
+ * with the allocator it was allocated with.
+ */
+typedef void *(*pr_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*pr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
+
+/*
+ * Build the device form of G(V,E) (Sec. 2.1) and run the preprocessing of
+ * Alg. 2 line 2 / Alg. 3 line 2 (Sec. 3.4: "invalidate edges between dangling
+ * vertices and their source vertices"):
+ *   out-degree, in-degree, dangling (deg(v) = 0) and unreferenced (no in-link)
+ *   classes; vertices are renumbered internally so that every out-list is
+ *   [non-dangling targets | dangling targets] and every in-list is
+ *   [referenced sources | unreferenced sources], which makes the IFP2 edge
+ *   invalidation a per-row prefix; the caller's ids are restored on output.
+ *
+ * n >= 1, m >= 0.  out_off[n+1] (out_off[0] = 0, non-decreasing,
+ * out_off[n] = m) and out_dst[m] (ids in [0, n)) are the out-lists D(v).
+ * in_off/in_src (the in-lists S(v)) are optional (NULL): when given they must
+ * describe the same edge set and are checked against the out-lists.  A
+ * repeated edge is rejected (the adjacency matrix is 0/1, Sec. 2.1); self
+ * loops are allowed.  mem_is_device: all four arrays are device pointers,
+ * else host.  cuda_stream: the cudaStream_t to run on (NULL = legacy default).
+ * The arrays are copied; the caller keeps ownership.  Errors: PR_EINVAL
+ * (bad size, offsets, ids, duplicate edge, CSC mismatch), PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
+                          const int32_t *in_off, const int32_t *in_src, int mem_is_device,
+                          void *cuda_stream, pr_graph **g);
+
+/* Fill *info for a created graph. */
+pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);
+
+/*
+ * Solve PageRank / personalized PageRank on g.
+ *  c:   damping factor, 0 < c < 1 (Sec. 2.1).
+ *  eps: IFP: stop when the residual L1 over non-dangling vertices R <= eps
+ *       (reading of Alg. 2/3 "Management" as an L1 test; activation uses
+ *       |r_i| > xi_act).  POWER: stop when ||pi_{k+1} - pi_k||_1 <= eps.
+ *  a, prec: pr_algo, pr_prec.   p: personalization (NULL = uniform).
+ *  out[n]: the PageRank vector in the caller's vertex ids, sum 1, FP64;
+ *       out_is_device selects a device or host pointer.  Written on PR_OK and
+ *       PR_ENOTCONV.
+ *  st:  optional report.
+ * pr_solve_ex adds tuning/tracing options (NULL = defaults).
+ * Errors: PR_EINVAL (c, eps, p), PR_ENOTCONV, PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_solve(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec, const pr_pvec *p,
+                   double *out, int out_is_device, pr_stats *st);
+pr_status pr_solve_ex(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec, const pr_pvec *p,
+                      const pr_opts *opts, double *out, int out_is_device, pr_stats *st);
+
+/* Release a graph and its workspace (NULL is ignored). */
+void pr_destroy(pr_graph *g);
+
+/* Message for the last non-OK status returned to this thread. */
+const char *pr_last_error(void);
+
+/* Library version string. */
+const char *pr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PR_H */

@@ -1,0 +1,291 @@
+"""Python binding of the GB300 IFP1 / IFP2 PageRank library (libpr.so).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  The functions carry the C ABI's names (include/pr.h).  Host arrays
+are numpy arrays; device arrays are torch CUDA tensors (their data_ptr() is
+passed through).  PyTorch is used for device memory (optionally as the
+library's allocator) and streams.
+
+There is no CPU fallback: if libpr.so is missing or cannot be loaded the
+functions raise, and a CUDA-less machine can only inspect the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpr.so")
+
+PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY = range(8)
+PR_POWER, PR_IFP1, PR_IFP2 = 0, 1, 2
+PR_FP64, PR_FP32 = 0, 1
+PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL = 0, 1, 2
+STATUS_NAMES = ["PR_OK", "PR_EINVAL", "PR_ENOMEM", "PR_ECUDA", "PR_ENOTCONV", "PR_ETIMEOUT", "PR_EAGAIN",
+                "PR_EBUSY"]
+
+
+class PrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class pr_pvec(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int32), ("idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("is_device", ctypes.c_int32)]
+
+
+class pr_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("rounds_push", ctypes.c_int32), ("rounds_pull", ctypes.c_int32),
+                ("fp64_rounds", ctypes.c_int32), ("pushes", ctypes.c_int64), ("edges_pushed", ctypes.c_int64),
+                ("edges_scanned", ctypes.c_int64), ("resid_l1", ctypes.c_double),
+                ("dangling_mass", ctypes.c_double), ("err_bound", ctypes.c_double), ("ms", ctypes.c_double),
+                ("p_scale", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PR_K_ACTIVATE, PR_K_COMMIT, PR_K_PUSH, PR_K_PULL, PR_K_POWER, PR_K_OTHER = range(6)
+PR_K_KINDS = 8
+KERNEL_NAMES = {PR_K_ACTIVATE: "k_activate", PR_K_COMMIT: "k_commit", PR_K_PUSH: "k_push",
+                PR_K_PULL: "k_rows<OP_ROUND>", PR_K_POWER: "k_rows<OP_POWER>", PR_K_OTHER: "other"}
+
+
+class pr_kernel_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32 * PR_K_KINDS), ("ms", ctypes.c_double * PR_K_KINDS)]
+
+    def as_dict(self) -> dict:
+        return {KERNEL_NAMES[k]: dict(launches=self.launches[k], ms=self.ms[k])
+                for k in KERNEL_NAMES if self.launches[k]}
+
+
+class pr_opts(ctypes.Structure):
+    _fields_ = [("xi_act", ctypes.c_double), ("max_rounds", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("pull_ratio", ctypes.c_double), ("use_graph", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
+                ("trace_R", ctypes.c_void_p), ("trace_F", ctypes.c_void_p), ("trace_E", ctypes.c_void_p),
+                ("trace_mode", ctypes.c_void_p), ("profile", ctypes.POINTER(pr_kernel_profile))]
+
+
+class pr_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_nd", ctypes.c_int32), ("n_ref", ctypes.c_int32),
+                ("n_d", ctypes.c_int32), ("n_u", ctypes.c_int32), ("m", ctypes.c_int64), ("m_d", ctypes.c_int64),
+                ("max_outdeg", ctypes.c_int32), ("max_indeg", ctypes.c_int32), ("ms_preprocess", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libpr.so; raises if it is not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2302_03245_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.pr_graph_create.argtypes = [i32, i64, P, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+        L.pr_graph_create.restype = ctypes.c_int
+        L.pr_graph_get_info.argtypes = [P, ctypes.POINTER(pr_graph_info)]
+        L.pr_graph_get_info.restype = ctypes.c_int
+        L.pr_solve.argtypes = [P, dbl, dbl, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pr_pvec), P, ctypes.c_int,
+                               ctypes.POINTER(pr_stats)]
+        L.pr_solve.restype = ctypes.c_int
+        L.pr_solve_ex.argtypes = [P, dbl, dbl, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pr_pvec),
+                                  ctypes.POINTER(pr_opts), P, ctypes.c_int, ctypes.POINTER(pr_stats)]
+        L.pr_solve_ex.restype = ctypes.c_int
+        L.pr_destroy.argtypes = [P]
+        L.pr_destroy.restype = None
+        L.pr_last_error.restype = ctypes.c_char_p
+        L.pr_version.restype = ctypes.c_char_p
+        L.pr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
+        L.pr_set_allocator.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != PR_OK:
+        raise PrError(status, lib().pr_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> int | None:
+    """Address of a numpy array (host) or torch tensor (device or host)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def pr_last_error() -> str:
+    return lib().pr_last_error().decode(errors="replace")
+
+
+def pr_version() -> str:
+    return lib().pr_version().decode()
+
+
+def pr_graph_create(n: int, m: int, out_off, out_dst, in_off=None, in_src=None, mem_is_device: bool = False,
+                    stream=None) -> ctypes.c_void_p:
+    """Wraps pr_graph_create.  Arrays are int32 numpy (host) or torch (device)."""
+    for a in (out_off, out_dst, in_off, in_src):
+        if isinstance(a, np.ndarray) and (a.dtype != np.int32 or not a.flags.c_contiguous):
+            raise TypeError("graph arrays must be contiguous int32")
+    g = ctypes.c_void_p()
+    _check(lib().pr_graph_create(int(n), int(m), _ptr(out_off), _ptr(out_dst), _ptr(in_off), _ptr(in_src),
+                                 1 if mem_is_device else 0, _stream_handle(stream), ctypes.byref(g)))
+    return g
+
+
+def pr_graph_get_info(g) -> dict:
+    info = pr_graph_info()
+    _check(lib().pr_graph_get_info(g, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def pr_destroy(g) -> None:
+    if g is not None and g.value:
+        lib().pr_destroy(g)
+        g.value = None
+
+
+def make_pvec(n: int, p=None, idx=None, is_device: bool = False):
+    """pr_pvec for: None (uniform), a dense vector of length n, or (idx, val) sparse."""
+    v = pr_pvec()
+    keep = []
+    if p is None and idx is None:
+        v.nnz = -1
+        return v, keep
+    if idx is None:
+        val = p if is_device else np.ascontiguousarray(p, dtype=np.float64)
+        v.nnz, v.idx, v.val = n, None, _ptr(val)
+        keep.append(val)
+    else:
+        ii = idx if is_device else np.ascontiguousarray(idx, dtype=np.int32)
+        vv = p if is_device else np.ascontiguousarray(p, dtype=np.float64)
+        v.nnz, v.idx, v.val = len(ii), _ptr(ii), _ptr(vv)
+        keep += [ii, vv]
+    v.is_device = 1 if is_device else 0
+    return v, keep
+
+
+def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_idx=None, out=None,
+             p_is_device: bool = False, opts: dict | None = None, check: bool = True):
+    """Wraps pr_solve_ex.  Returns (out, stats dict, status).
+
+    out: None (a new host numpy array), a numpy float64 array, or a torch
+    float64 CUDA tensor (device output).  opts: pr_opts fields by name; with
+    trace_cap > 0 the per-round traces are returned in stats["trace"].
+    """
+    info = pr_graph_get_info(g)
+    n = info["n"]
+    pv, keep = make_pvec(n, p, p_idx, p_is_device)
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    out_dev = not isinstance(out, np.ndarray)
+    st = pr_stats()
+    o = pr_opts()
+    trace = None
+    prof = None
+    if opts:
+        for k, v in opts.items():
+            if k in ("trace_cap", "profile"):
+                continue
+            setattr(o, k, v)
+        if opts.get("profile"):
+            prof = pr_kernel_profile()
+            o.profile = ctypes.pointer(prof)
+        cap = int(opts.get("trace_cap", 0))
+        if cap > 0:
+            trace = dict(R=np.zeros(cap), F=np.zeros(cap, np.int64), E=np.zeros(cap, np.int64),
+                         mode=np.zeros(cap, np.int8))
+            o.trace_cap = cap
+            o.trace_R, o.trace_F = trace["R"].ctypes.data, trace["F"].ctypes.data
+            o.trace_E, o.trace_mode = trace["E"].ctypes.data, trace["mode"].ctypes.data
+    status = lib().pr_solve_ex(g, float(c), float(eps), int(algo), int(prec), ctypes.byref(pv), ctypes.byref(o),
+                               _ptr(out), 1 if out_dev else 0, ctypes.byref(st))
+    if check and status not in (PR_OK, PR_ENOTCONV):
+        _check(status)
+    d = st.as_dict()
+    if trace is not None:
+        d["trace"] = trace
+    if prof is not None:
+        d["profile"] = prof.as_dict()
+    return out, d, status
+
+
+# ------------------------------------------------------- torch allocator hook
+_hooks = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device allocations through torch's caching allocator."""
+    global _hooks
+    L = lib()
+    if not enable:
+        _check(L.pr_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        _hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(L.pr_set_allocator(_hooks[0], _hooks[1], None))
+
+
+class Graph:
+    """RAII wrapper: pr_graph_create on construction, pr_destroy on close."""
+
+    def __init__(self, n, m, out_off, out_dst, in_off=None, in_src=None, mem_is_device=False, stream=None):
+        self.h = pr_graph_create(n, m, out_off, out_dst, in_off, in_src, mem_is_device, stream)
+        self.info = pr_graph_get_info(self.h)
+
+    def solve(self, c, eps, algo, prec=PR_FP64, **kw):
+        return pr_solve(self.h, c, eps, algo, prec, **kw)
+
+    def close(self):
+        pr_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,619 @@
+// pr_graph.cu -- error state, device allocator, and pr_graph_create: the
+// preprocessing of Alg. 2 line 2 / Alg. 3 line 2 (Sec. 3.4) on the GPU.
+//
+// From the caller's out-lists this builds, on the device:
+//   * out-degree / in-degree, the dangling (deg = 0) and unreferenced
+//     (in-degree 0) classes (Sec. 2.1);
+//   * an internal vertex numbering [referenced non-dangling | unreferenced
+//     non-dangling | dangling], each class sorted by in-degree (descending);
+//   * sorted internal out-lists, whose non-dangling targets form a prefix of
+//     length ndeg[i] -- the IFP2 edge invalidation of Sec. 3.4 is then a
+//     per-row length, no edge is moved or deleted;
+//   * in-lists split into a "ref" segment (sources with in-edges) and an
+//     "unref" segment (unreferenced sources), both sorted.
+// Sorting uses CUB's device radix sort; everything else is hand-written.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pr_internal.cuh"
+
+namespace pr {
+
+// ------------------------------------------------------------ error state
+static thread_local std::string t_err;
+void set_error(const std::string &msg) { t_err = msg; }
+pr_status fail(pr_status st, const std::string &msg) {
+    t_err = msg;
+    return st;
+}
+pr_status cuda_fail(cudaError_t e, const char *what) {
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PR_ECUDA;
+}
+
+// ------------------------------------------------------------ allocator
+static pr_alloc_fn g_alloc = nullptr;
+static pr_free_fn g_free = nullptr;
+static void *g_ctx = nullptr;
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) g_free(p, bytes, (void *)s, g_ctx);
+    else cudaFree(p);
+}
+
+// A buffer remembers the allocator that made it, so a later pr_set_allocator
+// does not hand it to the wrong free function.
+pr_status Buf::alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    if (nbytes == 0) nbytes = 16;
+    if (g_alloc) {
+        p = g_alloc(nbytes, (void *)stream, g_ctx);
+        ffn = g_free;
+        fctx = g_ctx;
+    } else {
+        if (cudaMalloc(&p, nbytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        ffn = nullptr;
+        fctx = nullptr;
+    }
+    if (!p) return fail(PR_ENOMEM, "device allocation of " + std::to_string(nbytes) + " bytes failed");
+    bytes = nbytes;
+    return PR_OK;
+}
+
+void Buf::release() {
+    if (p) {
+        if (ffn) ffn(p, bytes, (void *)s, fctx);
+        else cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+// ------------------------------------------------------------ kernels
+static __global__ void k_validate(int32_t n, int64_t m, const int32_t *off, const int32_t *dst,
+                                  unsigned long long *bad) {
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i <= n; i += stride) {
+        int32_t o = off[i];
+        if (i == 0 && o != 0) atomicAdd(&bad[0], 1ULL);
+        if (i == n && (int64_t)o != m) atomicAdd(&bad[0], 1ULL);
+        if (i < n && off[i + 1] < o) atomicAdd(&bad[0], 1ULL);
+        if (o < 0 || (int64_t)o > m) atomicAdd(&bad[0], 1ULL);
+    }
+    for (int64_t e = tid; e < m; e += stride) {
+        int32_t d = dst[e];
+        if (d < 0 || d >= n) atomicAdd(&bad[1], 1ULL);
+    }
+}
+
+static __global__ void k_indeg(int64_t m, const int32_t *dst, int32_t *indeg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+        atomicAdd(&indeg[dst[e]], 1);
+}
+
+// class 0: deg>0 & indeg>0, class 1: deg>0 & indeg==0, class 2: deg==0
+static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_t *indeg,
+                                     uint64_t *keys, int32_t *vals, unsigned int *class_cnt) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int32_t deg = off[i + 1] - off[i];
+        int32_t id = indeg[i];
+        uint32_t cls = deg == 0 ? 2u : (id == 0 ? 1u : 0u);
+        keys[i] = ((uint64_t)cls << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
+        vals[i] = i;
+        atomicAdd(&class_cnt[cls], 1u);
+    }
+}
+
+static __global__ void k_invert(int32_t n, const int32_t *perm, int32_t *inv) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) inv[perm[i]] = i;
+}
+
+// key = (inv[src] << B) | inv[dst]; the source row is found by binary search
+static __global__ void k_edge_keys(int32_t n, int64_t m, const int32_t *off, const int32_t *dst,
+                                   const int32_t *inv, int B, uint64_t *keys) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+        int32_t lo = 0, hi = n;  // largest row with off[row] <= e
+        while (hi - lo > 1) {
+            int32_t mid = lo + ((hi - lo) >> 1);
+            if ((int64_t)off[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        keys[e] = ((uint64_t)inv[lo] << B) | (uint64_t)inv[dst[e]];
+    }
+}
+
+static __global__ void k_count_dups(int64_t m, const uint64_t *keys, unsigned long long *cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t e = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+        c += keys[e] == keys[e - 1];
+    if (c) atomicAdd(cnt, c);
+}
+
+// low field of a sorted key array -> int32 column array; high field -> counted elsewhere
+static __global__ void k_low_field(int64_t m, const uint64_t *keys, int B, int32_t *col) {
+    const uint64_t mask = (1ULL << B) - 1;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+        col[e] = (int32_t)(keys[e] & mask);
+}
+
+// off[r] = first e in [lo, hi) with keys[e] >= base + (r << B), minus lo; off[n] = hi - lo
+static __global__ void k_row_offsets(int32_t n, const uint64_t *keys, int64_t lo, int64_t hi,
+                                     uint64_t base, int B, int32_t *off) {
+    int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += stride) {
+        uint64_t target = base + ((uint64_t)r << B);
+        int64_t a = lo, b = hi;
+        while (a < b) {
+            int64_t mid = a + ((b - a) >> 1);
+            if (keys[mid] < target) a = mid + 1;
+            else b = mid;
+        }
+        off[r] = (int32_t)(a - lo);
+    }
+}
+
+// CSR key (src << B | dst) -> CSC key (flag << 2B | dst << B | src), flag = src is unreferenced
+static __global__ void k_csc_keys(int64_t m, const uint64_t *csr, int B, int32_t n_ref,
+                                  uint64_t *csc) {
+    const uint64_t mask = (1ULL << B) - 1;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint64_t k = csr[e];
+        uint64_t s = k >> B, d = k & mask;
+        uint64_t flag = s >= (uint64_t)n_ref ? 1ULL : 0ULL;
+        csc[e] = (flag << (2 * B)) | (d << B) | s;
+    }
+}
+
+// first index with keys[e] >= target (single thread)
+static __global__ void k_lower_bound(const uint64_t *keys, int64_t m, uint64_t target, int64_t *out) {
+    int64_t a = 0, b = m;
+    while (a < b) {
+        int64_t mid = a + ((b - a) >> 1);
+        if (keys[mid] < target) a = mid + 1;
+        else b = mid;
+    }
+    *out = a;
+}
+
+static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const int32_t *dst,
+                                       int32_t *ndeg, double *inv64, float *inv32) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_nd; i += stride) {
+        int32_t a = off[i], b = off[i + 1];
+        int32_t lo = a, hi = b;  // first target >= n_nd
+        while (lo < hi) {
+            int32_t mid = lo + ((hi - lo) >> 1);
+            if (dst[mid] < n_nd) lo = mid + 1;
+            else hi = mid;
+        }
+        ndeg[i] = lo - a;
+        double inv = 1.0 / (double)(b - a);
+        inv64[i] = inv;
+        inv32[i] = (float)inv;
+    }
+}
+
+// rows of one class in [lo, hi) are sorted by in-degree (descending): count rows above thresholds
+static __global__ void k_degree_facts(int32_t n, int32_t n_nd, int32_t n_ref, const int32_t *perm,
+                                      const int32_t *indeg_ext, const int32_t *off_int,
+                                      int32_t t_warp, int32_t t_cta, unsigned int *cnt,
+                                      int *maxes, unsigned long long *m_d) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int32_t id = indeg_ext[perm[i]];
+        int32_t od = off_int[i + 1] - off_int[i];
+        int base = i < n_ref ? 0 : (i >= n_nd ? 2 : -1);
+        if (base >= 0) {
+            if (id > t_cta) atomicAdd(&cnt[base], 1u);
+            else if (id > t_warp) atomicAdd(&cnt[base + 1], 1u);
+        }
+        if (i >= n_nd) atomicAdd(m_d, (unsigned long long)id);
+        if (id == 0) atomicAdd(&cnt[4], 1u);
+        atomicMax(&maxes[0], od);
+        atomicMax(&maxes[1], id);
+    }
+}
+
+// (hi << B | lo) -> (lo << B | hi)
+static __global__ void k_swap_halves(int64_t m, uint64_t *k, int B) {
+    const uint64_t mask = (1ULL << B) - 1;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+        k[e] = ((k[e] & mask) << B) | (k[e] >> B);
+}
+
+static __global__ void k_count_diff(int64_t m, const uint64_t *a, const uint64_t *b,
+                                    unsigned long long *cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+        c += a[e] != b[e];
+    if (c) atomicAdd(cnt, c);
+}
+
+static int grid_for(int64_t items, int num_sms) {
+    int64_t b = (items + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms * 16;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+static int bits_for(int32_t n) {
+    int B = 1;
+    while (B < 31 && ((int64_t)1 << B) < (int64_t)n) B++;
+    return B;
+}
+
+// ------------------------------------------------------------ plans
+Plan make_plan(int num_sms, const int32_t (*ranges)[3], int nranges) {
+    Plan P{};
+    int blk = 0;
+    for (int k = 0; k < nranges && P.nseg < kMaxSeg; k++) {
+        int32_t lo = ranges[k][0], hi = ranges[k][1], kind = ranges[k][2];
+        if (hi <= lo) continue;
+        int64_t rows = hi - lo;
+        int64_t nb;
+        if (kind == SEG_THREAD) nb = (rows + kThreads - 1) / kThreads;
+        else if (kind == SEG_WARP) nb = (rows + (kThreads / 32) - 1) / (kThreads / 32);
+        else nb = rows;
+        nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)num_sms * 32));
+        Seg &s = P.seg[P.nseg++];
+        s.lo = lo;
+        s.hi = hi;
+        s.kind = kind;
+        s.blk0 = blk;
+        s.nblk = (int32_t)nb;
+        blk += (int)nb;
+    }
+    P.nblocks = std::max(blk, 1);
+    return P;
+}
+
+void build_plans(pr_graph *g) {
+    const int32_t n = g->G.n, n_nd = g->G.n_nd, n_ref = g->G.n_ref;
+    int32_t nd_r[4][3] = {{0, g->ref_heavy, SEG_CTA},
+                          {g->ref_heavy, g->ref_med, SEG_WARP},
+                          {g->ref_med, n_ref, SEG_THREAD},
+                          {n_ref, n_nd, SEG_THREAD}};
+    int32_t d_r[3][3] = {{n_nd, g->d_heavy, SEG_CTA},
+                         {g->d_heavy, g->d_med, SEG_WARP},
+                         {g->d_med, n, SEG_THREAD}};
+    int32_t all_r[7][3];
+    for (int k = 0; k < 4; k++) std::memcpy(all_r[k], nd_r[k], sizeof(nd_r[k]));
+    for (int k = 0; k < 3; k++) std::memcpy(all_r[4 + k], d_r[k], sizeof(d_r[k]));
+    g->plan_nd = make_plan(g->num_sms, nd_r, 4);
+    g->plan_d = make_plan(g->num_sms, d_r, 3);
+    g->plan_all = make_plan(g->num_sms, all_r, 7);
+}
+
+}  // namespace pr
+
+using namespace pr;
+
+// ------------------------------------------------------------ ABI
+extern "C" const char *pr_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char *pr_version(void) { return "pr-gb300 0.1 (sm_103a)"; }
+
+extern "C" pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(PR_EINVAL, "pr_set_allocator: alloc and free must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_ctx = ctx;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info) {
+    if (!g || !info) return fail(PR_EINVAL, "pr_graph_get_info: NULL argument");
+    *info = g->info;
+    return PR_OK;
+}
+
+extern "C" void pr_destroy(pr_graph *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    destroy_workspace(g);
+    delete g;
+}
+
+static pr_status validate_host(int32_t n, int64_t m, const int32_t *off, const int32_t *dst) {
+    if (off[0] != 0) return fail(PR_EINVAL, "out_off[0] must be 0");
+    for (int32_t i = 0; i < n; i++)
+        if (off[i + 1] < off[i])
+            return fail(PR_EINVAL, "out_off is not non-decreasing at row " + std::to_string(i));
+    if ((int64_t)off[n] != m) return fail(PR_EINVAL, "out_off[n] != m");
+    for (int64_t e = 0; e < m; e++)
+        if (dst[e] < 0 || dst[e] >= n)
+            return fail(PR_EINVAL, "out_dst[" + std::to_string(e) + "] out of range");
+    return PR_OK;
+}
+
+namespace {
+// CUB helper that takes temporary storage from the library allocator
+struct Temp {
+    Buf b;
+    pr_status need(size_t bytes, cudaStream_t s) {
+        if (bytes <= b.bytes) return PR_OK;
+        return b.alloc(bytes, s);
+    }
+};
+
+pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int end_bit,
+                    cudaStream_t s) {
+    if (m <= 1) return PR_OK;
+    cub::DoubleBuffer<uint64_t> db(keys, alt);
+    size_t bytes = 0;
+    PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, db, (int)m, 0, end_bit, s));
+    PR_TRY(tmp.need(bytes, s));
+    PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, db, (int)m, 0, end_bit, s));
+    if (db.Current() != keys) std::swap(keys, alt);
+    return PR_OK;
+}
+
+pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
+                      const int32_t *in_off, const int32_t *in_src, int mem_is_device,
+                      cudaStream_t s, pr_graph *g) {
+    int dev = 0;
+    PR_CK(cudaGetDevice(&dev));
+    int sms = 0;
+    PR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    g->device = dev;
+    g->num_sms = sms;
+    g->stream = s;
+    cudaEvent_t e0, e1;
+    PR_CK(cudaEventCreate(&e0));
+    PR_CK(cudaEventCreate(&e1));
+    PR_CK(cudaEventRecord(e0, s));
+
+    // caller arrays on the device
+    Buf c_off, c_dst, c_ioff, c_isrc;
+    const int32_t *d_off = out_off, *d_dst = out_dst, *d_ioff = in_off, *d_isrc = in_src;
+    if (!mem_is_device) {
+        PR_TRY(c_off.alloc(sizeof(int32_t) * (n + 1), s));
+        PR_TRY(c_dst.alloc(sizeof(int32_t) * m, s));
+        PR_CK(cudaMemcpyAsync(c_off.p, out_off, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        if (m) PR_CK(cudaMemcpyAsync(c_dst.p, out_dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        d_off = c_off.as<int32_t>();
+        d_dst = c_dst.as<int32_t>();
+        if (in_off) {
+            PR_TRY(c_ioff.alloc(sizeof(int32_t) * (n + 1), s));
+            PR_TRY(c_isrc.alloc(sizeof(int32_t) * m, s));
+            PR_CK(cudaMemcpyAsync(c_ioff.p, in_off, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+            if (m) PR_CK(cudaMemcpyAsync(c_isrc.p, in_src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+            d_ioff = c_ioff.as<int32_t>();
+            d_isrc = c_isrc.as<int32_t>();
+        }
+    }
+    // small device scratch: [0..1] validation, [2] dup count, [3] m_d, class counts, facts
+    Buf scratch;
+    PR_TRY(scratch.alloc(256, s));
+    PR_CK(cudaMemsetAsync(scratch.p, 0, 256, s));
+    unsigned long long *bad = scratch.as<unsigned long long>();         // [0],[1]
+    unsigned long long *dups = bad + 2;                                 // [2]
+    unsigned long long *m_d = bad + 3;                                  // [3]
+    unsigned int *class_cnt = reinterpret_cast<unsigned int *>(bad + 4);// 3 entries
+    unsigned int *fact_cnt = class_cnt + 4;                             // 5 entries
+    int *maxes = reinterpret_cast<int *>(fact_cnt + 6);                 // 2 entries
+    int64_t *lb = reinterpret_cast<int64_t *>(bad + 12);                // lower bounds
+
+    const int gm = grid_for(std::max<int64_t>(m, n + 1), sms), gn = grid_for(n + 1, sms);
+    if (mem_is_device) {
+        k_validate<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, bad);
+        if (d_ioff) k_validate<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, bad);
+        unsigned long long hb[2];
+        PR_CK(cudaMemcpyAsync(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        if (hb[0]) return fail(PR_EINVAL, "offsets are not a valid CSR/CSC offset array");
+        if (hb[1]) return fail(PR_EINVAL, "an edge endpoint is outside [0, n)");
+    }
+    const int B = bits_for(n);
+    // degrees and classes
+    Buf indeg;
+    PR_TRY(indeg.alloc(sizeof(int32_t) * n, s));
+    PR_CK(cudaMemsetAsync(indeg.p, 0, sizeof(int32_t) * n, s));
+    if (m) k_indeg<<<gm, kThreads, 0, s>>>(m, d_dst, indeg.as<int32_t>());
+    Buf vk, vk2, vv, vv2;
+    PR_TRY(vk.alloc(sizeof(uint64_t) * n, s));
+    PR_TRY(vk2.alloc(sizeof(uint64_t) * n, s));
+    PR_TRY(vv.alloc(sizeof(int32_t) * n, s));
+    PR_TRY(vv2.alloc(sizeof(int32_t) * n, s));
+    k_vertex_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), vk.as<uint64_t>(),
+                                          vv.as<int32_t>(), class_cnt);
+    Temp tmp;
+    {
+        cub::DoubleBuffer<uint64_t> dk(vk.as<uint64_t>(), vk2.as<uint64_t>());
+        cub::DoubleBuffer<int32_t> dv(vv.as<int32_t>(), vv2.as<int32_t>());
+        size_t bytes = 0;
+        PR_CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, dk, dv, n, 0, 34, s));
+        PR_TRY(tmp.need(bytes, s));
+        PR_CK(cub::DeviceRadixSort::SortPairs(tmp.b.p, bytes, dk, dv, n, 0, 34, s));
+        PR_TRY(g->perm.alloc(sizeof(int32_t) * n, s));
+        PR_CK(cudaMemcpyAsync(g->perm.p, dv.Current(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    vk2.release();
+    vv.release();
+    vv2.release();
+    vk.release();
+    PR_TRY(g->inv.alloc(sizeof(int32_t) * n, s));
+    k_invert<<<gn, kThreads, 0, s>>>(n, g->perm.as<int32_t>(), g->inv.as<int32_t>());
+    unsigned int hc[3];
+    PR_CK(cudaMemcpyAsync(hc, class_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaStreamSynchronize(s));
+    const int32_t n_ref = (int32_t)hc[0], n_nd = (int32_t)(hc[0] + hc[1]);
+
+    // out-lists in internal ids
+    Buf ek, ek2;
+    PR_TRY(ek.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    PR_TRY(ek2.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    uint64_t *keys = ek.as<uint64_t>(), *alt = ek2.as<uint64_t>();
+    if (m) k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, g->inv.as<int32_t>(), B, keys);
+    PR_TRY(sort_keys(tmp, keys, alt, m, 2 * B, s));
+    if (m > 1) k_count_dups<<<gm, kThreads, 0, s>>>(m, keys, dups);
+    PR_TRY(g->out_off.alloc(sizeof(int32_t) * (n + 1), s));
+    PR_TRY(g->out_dst.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m, 0, B, g->out_off.as<int32_t>());
+    if (m) k_low_field<<<gm, kThreads, 0, s>>>(m, keys, B, g->out_dst.as<int32_t>());
+    // optional caller in-lists: same edge set?
+    if (d_ioff) {
+        // transpose keys of the caller's CSC: (inv[src] << B | inv[dst]) sorted must equal `keys`
+        Buf ck;
+        PR_TRY(ck.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+        uint64_t *ckeys = ck.as<uint64_t>();
+        // in-list row = dst; entry = src.  k_edge_keys builds (inv[row] << B | inv[entry]);
+        // swap the two halves to compare with the out-list keys.
+        if (m) k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, g->inv.as<int32_t>(), B, ckeys);
+        if (m) k_swap_halves<<<gm, kThreads, 0, s>>>(m, ckeys, B);
+        uint64_t *calt = alt;  // reuse the spare buffer
+        PR_TRY(sort_keys(tmp, ckeys, calt, m, 2 * B, s));
+        if (m) k_count_diff<<<gm, kThreads, 0, s>>>(m, keys, ckeys, bad + 1);
+        unsigned long long hb = 0;
+        PR_CK(cudaMemcpyAsync(&hb, bad + 1, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        if (hb) return fail(PR_EINVAL, "in_off/in_src do not describe the same edges as out_off/out_dst");
+    }
+    // in-lists: flag(src unreferenced) << 2B | dst << B | src, sorted
+    if (m) k_csc_keys<<<gm, kThreads, 0, s>>>(m, keys, B, n_ref, alt);
+    std::swap(keys, alt);
+    PR_TRY(sort_keys(tmp, keys, alt, m, 2 * B + 1, s));
+    k_lower_bound<<<1, 1, 0, s>>>(keys, m, 1ULL << (2 * B), lb);
+    int64_t m_ref = 0;
+    unsigned long long hdup = 0;
+    PR_CK(cudaMemcpyAsync(&m_ref, lb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(&hdup, dups, sizeof(hdup), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaStreamSynchronize(s));
+    if (hdup) return fail(PR_EINVAL, std::to_string(hdup) + " repeated edge(s): the adjacency is 0/1");
+    const int64_t m_unref = m - m_ref;
+    PR_TRY(g->inr_off.alloc(sizeof(int32_t) * (n + 1), s));
+    PR_TRY(g->inu_off.alloc(sizeof(int32_t) * (n + 1), s));
+    PR_TRY(g->inr_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_ref, 1), s));
+    PR_TRY(g->inu_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_unref, 1), s));
+    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m_ref, 0, B, g->inr_off.as<int32_t>());
+    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, m_ref, m, 1ULL << (2 * B), B, g->inu_off.as<int32_t>());
+    if (m_ref) k_low_field<<<gm, kThreads, 0, s>>>(m_ref, keys, B, g->inr_src.as<int32_t>());
+    if (m_unref) k_low_field<<<gm, kThreads, 0, s>>>(m_unref, keys + m_ref, B, g->inu_src.as<int32_t>());
+    ek.release();
+    ek2.release();
+    tmp.b.release();
+    // per-vertex arrays
+    PR_TRY(g->ndeg.alloc(sizeof(int32_t) * std::max(n_nd, 1), s));
+    PR_TRY(g->inv_deg64.alloc(sizeof(double) * std::max(n_nd, 1), s));
+    PR_TRY(g->inv_deg32.alloc(sizeof(float) * std::max(n_nd, 1), s));
+    if (n_nd)
+        k_vertex_arrays<<<grid_for(n_nd, sms), kThreads, 0, s>>>(
+            n_nd, g->out_off.as<int32_t>(), g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
+            g->inv_deg64.as<double>(), g->inv_deg32.as<float>());
+    k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, n_ref, g->perm.as<int32_t>(), indeg.as<int32_t>(),
+                                           g->out_off.as<int32_t>(), kWarpRowMin, kCtaRowMin, fact_cnt,
+                                           maxes, m_d);
+    unsigned int hf[5];
+    int hm[2];
+    unsigned long long hmd = 0;
+    PR_CK(cudaMemcpyAsync(hf, fact_cnt, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(&hmd, m_d, sizeof(hmd), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaEventRecord(e1, s));
+    PR_CK(cudaStreamSynchronize(s));
+    float ms = 0;
+    PR_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+
+    g->ref_heavy = (int32_t)hf[0];
+    g->ref_med = (int32_t)(hf[0] + hf[1]);
+    g->d_heavy = n_nd + (int32_t)hf[2];
+    g->d_med = n_nd + (int32_t)(hf[2] + hf[3]);
+    DevGraph &G = g->G;
+    G.n = n;
+    G.n_nd = n_nd;
+    G.n_ref = n_ref;
+    G.m = m;
+    G.m_ref = m_ref;
+    G.m_unref = m_unref;
+    G.out_off = g->out_off.as<int32_t>();
+    G.out_dst = g->out_dst.as<int32_t>();
+    G.ndeg = g->ndeg.as<int32_t>();
+    G.inv_deg64 = g->inv_deg64.as<double>();
+    G.inv_deg32 = g->inv_deg32.as<float>();
+    G.inr_off = g->inr_off.as<int32_t>();
+    G.inr_src = g->inr_src.as<int32_t>();
+    G.inu_off = g->inu_off.as<int32_t>();
+    G.inu_src = g->inu_src.as<int32_t>();
+    G.perm = g->perm.as<int32_t>();
+    G.inv = g->inv.as<int32_t>();
+    build_plans(g);
+
+    pr_graph_info &I = g->info;
+    I.n = n;
+    I.n_nd = n_nd;
+    I.n_ref = n_ref;
+    I.n_d = n - n_nd;
+    I.n_u = (int32_t)hf[4];
+    I.m = m;
+    I.m_d = (int64_t)hmd;
+    I.max_outdeg = hm[0];
+    I.max_indeg = hm[1];
+    I.ms_preprocess = ms;
+    I.device_bytes = g->out_off.bytes + g->out_dst.bytes + g->ndeg.bytes + g->inv_deg64.bytes +
+                     g->inv_deg32.bytes + g->inr_off.bytes + g->inr_src.bytes + g->inu_off.bytes +
+                     g->inu_src.bytes + g->perm.bytes + g->inv.bytes;
+    return PR_OK;
+}
+}  // namespace
+
+extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off,
+                                     const int32_t *out_dst, const int32_t *in_off,
+                                     const int32_t *in_src, int mem_is_device, void *cuda_stream,
+                                     pr_graph **g) {
+    if (!g) return fail(PR_EINVAL, "pr_graph_create: g is NULL");
+    *g = nullptr;
+    if (n < 1) return fail(PR_EINVAL, "n must be >= 1");
+    if (m < 0 || m >= ((int64_t)1 << 31)) return fail(PR_EINVAL, "m must be in [0, 2^31)");
+    if (!out_off || (m > 0 && !out_dst)) return fail(PR_EINVAL, "out_off/out_dst missing");
+    if (!in_off && in_src) return fail(PR_EINVAL, "in_src given without in_off");
+    if (in_off && m > 0 && !in_src) return fail(PR_EINVAL, "in_off given without in_src");
+    if (!mem_is_device) {  // host arrays are checked before any CUDA call
+        PR_TRY(validate_host(n, m, out_off, out_dst));
+        if (in_off) PR_TRY(validate_host(n, m, in_off, in_src));
+    }
+    pr_graph *G = new (std::nothrow) pr_graph();
+    if (!G) return fail(PR_ENOMEM, "host allocation failed");
+    pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
+                               (cudaStream_t)cuda_stream, G);
+    if (st != PR_OK) {
+        std::string msg = pr_last_error();
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        cudaGetLastError();
+        delete G;
+        set_error(msg);
+        return st;
+    }
+    *g = G;
+    return PR_OK;
+}

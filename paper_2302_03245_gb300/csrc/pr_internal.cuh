@@ -1,0 +1,122 @@
+// pr_internal.cuh -- device-side layout and helpers shared by the library's
+// translation units (graph build, solver).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pr.h"
+
+namespace pr {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+pr_status fail(pr_status st, const std::string &msg);
+pr_status cuda_fail(cudaError_t e, const char *what);
+
+#define PR_CK(call)                                                     \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::pr::cuda_fail(_e, #call);       \
+    } while (0)
+
+#define PR_TRY(call)                                                    \
+    do {                                                                \
+        pr_status _s = (call);                                          \
+        if (_s != PR_OK) return _s;                                     \
+    } while (0)
+
+// ---------------------------------------------------------------- memory
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, size_t bytes, cudaStream_t s);
+
+// A device buffer owned by the library (allocator hook aware).
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    pr_free_fn ffn = nullptr;  // allocator hook that made p (nullptr: cudaMalloc)
+    void *fctx = nullptr;
+    pr_status alloc(size_t nbytes, cudaStream_t stream);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+    ~Buf() { release(); }
+    Buf() = default;
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+};
+
+// ---------------------------------------------------------------- graph
+// Vertex renumbering: internal ids are ordered by class and, inside a class,
+// by total in-degree (descending):
+//   [0, n_ref)      non-dangling with in-edges   ("referenced")
+//   [n_ref, n_nd)   non-dangling without in-edges ("unreferenced", Sec. 2.1)
+//   [n_nd, n)       dangling (deg = 0)
+// Out-lists are sorted by target, so the targets < n_nd (non-dangling) form
+// a prefix of length ndeg[i]: the IFP2 valid edges.  In-lists are split into
+// two segments: sources < n_ref ("ref") and sources in [n_ref, n_nd)
+// ("unref", which can only push while their residual is not yet spent).
+struct DevGraph {
+    int32_t n, n_nd, n_ref;
+    int64_t m, m_ref, m_unref;
+    const int32_t *out_off;   // [n+1]
+    const int32_t *out_dst;   // [m]
+    const int32_t *ndeg;      // [n_nd]
+    const double *inv_deg64;  // [n_nd] 1/deg
+    const float *inv_deg32;   // [n_nd]
+    const int32_t *inr_off;   // [n+1]
+    const int32_t *inr_src;   // [m_ref]
+    const int32_t *inu_off;   // [n+1]
+    const int32_t *inu_src;   // [m_unref]
+    const int32_t *perm;      // [n] internal -> caller id
+    const int32_t *inv;       // [n] caller id -> internal
+};
+
+// Row ranges of a gather kernel, by work-group size.  Rows inside each
+// class are sorted by in-degree, so each bin is a contiguous range.
+enum { SEG_THREAD = 0, SEG_WARP = 1, SEG_CTA = 2 };
+struct Seg {
+    int32_t lo, hi;   // rows [lo, hi)
+    int32_t kind;     // SEG_*
+    int32_t blk0;     // first block of this segment
+    int32_t nblk;     // blocks assigned
+};
+constexpr int kMaxSeg = 8;
+struct Plan {
+    Seg seg[kMaxSeg];
+    int32_t nseg;
+    int32_t nblocks;
+};
+
+constexpr int kThreads = 256;   // block size of every row/vertex kernel
+constexpr int kWarpRowMin = 32; // in-degree above which a row gets a warp
+constexpr int kCtaRowMin = 4096;// in-degree above which a row gets a CTA
+
+}  // namespace pr
+
+// The opaque ABI handle.
+struct pr_graph {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    pr::DevGraph G{};
+    pr_graph_info info{};
+    // storage
+    pr::Buf out_off, out_dst, ndeg, inv_deg64, inv_deg32, inr_off, inr_src, inu_off, inu_src, perm,
+        inv;
+    // bin boundaries of the in-degree sorted classes
+    int32_t ref_heavy = 0, ref_med = 0;  // rows [0, ref_heavy) CTA, [ref_heavy, ref_med) warp
+    int32_t d_heavy = 0, d_med = 0;      // same for dangling rows, absolute ids
+    pr::Plan plan_nd{}, plan_d{}, plan_all{};
+    int32_t max_rows_heavy = 0;
+    // solver workspace (lazily allocated, reused across solves)
+    void *ws = nullptr;
+};
+
+namespace pr {
+pr::Plan make_plan(int num_sms, const int32_t (*ranges)[3], int nranges);
+void build_plans(pr_graph *g);
+void destroy_workspace(pr_graph *g);
+}  // namespace pr

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every function include/pr.h declares, and rejects bad host input before
+touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def prlib():
+    import paper_2302_03245_gb300 as pr
+    pr.build()
+    return pr
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "pr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(pr_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pr_graph_create", "pr_solve", "pr_solve_ex", "pr_destroy", "pr_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(prlib):
+    lib = prlib.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", prlib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pr_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_header_compiles_as_c():
+    src = "#include \"pr.h\"\nint main(void){pr_stats s; pr_opts o; pr_kernel_profile k; (void)s; (void)o; (void)k; return 0;}\n"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-x", "c",
+                        "-", "-o", "/dev/null"], input=src, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_struct_layouts_match_binding(prlib):
+    # offsets of the C structs as gcc lays them out, compared with ctypes
+    src = r'''#include <stdio.h>
+#include <stddef.h>
+#include "pr.h"
+int main(void){
+ printf("%zu %zu %zu %zu %zu\n", sizeof(pr_stats), sizeof(pr_opts), sizeof(pr_graph_info), sizeof(pr_pvec), sizeof(pr_kernel_profile));
+ printf("%zu %zu %zu\n", offsetof(pr_stats, ms), offsetof(pr_opts, trace_mode), offsetof(pr_graph_info, device_bytes));
+ return 0;}'''
+    exe = os.path.join(ROOT, "tests", ".layout_probe")
+    r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-x", "c", "-", "-o", exe], input=src,
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lines = subprocess.run([exe], capture_output=True, text=True).stdout.split("\n")
+    os.remove(exe)
+    sizes = list(map(int, lines[0].split()))
+    offs = list(map(int, lines[1].split()))
+    assert sizes == [ctypes.sizeof(prlib.pr_stats), ctypes.sizeof(prlib.pr_opts),
+                     ctypes.sizeof(prlib.pr_graph_info), ctypes.sizeof(prlib.pr_pvec),
+                     ctypes.sizeof(prlib.pr_kernel_profile)]
+    assert offs == [prlib.pr_stats.ms.offset, prlib.pr_opts.trace_mode.offset,
+                    prlib.pr_graph_info.device_bytes.offset]
+
+
+@pytest.mark.parametrize("case", ["dup_free_but_bad_offsets", "range", "negative_n", "off0", "offn"])
+def test_host_validation_without_gpu(prlib, case):
+    g = gg.random_small(30, 3.0, 0.2, 0.1, seed=1)
+    off, dst = [a.copy() for a in g.csr32()]
+    n, m = g.n, g.m
+    if case == "dup_free_but_bad_offsets":
+        off[3], off[4] = off[4] + 1, off[3]
+    elif case == "range":
+        dst[-1] = n + 3
+    elif case == "negative_n":
+        n = 0
+    elif case == "off0":
+        off[0] = 1
+    else:
+        m = m + 1
+    with pytest.raises(prlib.PrError) as e:
+        prlib.pr_graph_create(n, m, off, dst)
+    assert e.value.status == prlib.PR_EINVAL
+
+
+def test_allocator_arguments_checked(prlib):
+    lib = prlib.lib()
+    st = lib.pr_set_allocator(prlib._ALLOC_FN(lambda a, b, c: None), prlib._FREE_FN(), None)
+    assert st == prlib.PR_EINVAL
+    assert lib.pr_set_allocator(prlib._ALLOC_FN(), prlib._FREE_FN(), None) == prlib.PR_OK
