@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
     ap.add_argument("--eps", type=float, default=1e-9)
     ap.add_argument("--skip-extras", action="store_true", help="only the timed IFP2 steps")
+    ap.add_argument("--host-rounds", action="store_true",
+                    help="launch rounds from the host instead of the CUDA-graph while loop (same kernels; "
+                         "lets a profiler see each launch)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args()
 
@@ -226,8 +229,11 @@ def main():
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
-    def solve(algo=pr.PR_IFP2, prec=pr.PR_FP64, eps=args.eps, **kw):
-        _, st, status = G.solve(C, eps, algo, prec, out=out, **kw)
+    def solve(algo=pr.PR_IFP2, prec=pr.PR_FP64, eps=args.eps, opts=None):
+        opts = dict(opts or {})
+        if args.host_rounds:
+            opts.setdefault("use_graph", -1)
+        _, st, status = G.solve(C, eps, algo, prec, out=out, opts=opts)
         assert status == pr.PR_OK, st
         return st
 

@@ -115,6 +115,10 @@ static __global__ void k_indeg(int64_t m, const int32_t *dst, int32_t *indeg) {
 // class 0: deg>0 & indeg>0, class 1: deg>0 & indeg==0, class 2: deg==0
 static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_t *indeg,
                                      uint64_t *keys, int32_t *vals, unsigned int *class_cnt) {
+    __shared__ unsigned int cnt[3];
+    if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned int local[3] = {0, 0, 0};
     int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         int32_t deg = off[i + 1] - off[i];
@@ -122,8 +126,12 @@ static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_
         uint32_t cls = deg == 0 ? 2u : (id == 0 ? 1u : 0u);
         keys[i] = ((uint64_t)cls << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
         vals[i] = i;
-        atomicAdd(&class_cnt[cls], 1u);
+        local[cls]++;
     }
+    for (int k = 0; k < 3; k++)
+        if (local[k]) atomicAdd(&cnt[k], local[k]);
+    __syncthreads();
+    if (threadIdx.x < 3 && cnt[threadIdx.x]) atomicAdd(&class_cnt[threadIdx.x], cnt[threadIdx.x]);
 }
 
 static __global__ void k_invert(int32_t n, const int32_t *perm, int32_t *inv) {
@@ -220,25 +228,65 @@ static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const i
     }
 }
 
-// rows of one class in [lo, hi) are sorted by in-degree (descending): count rows above thresholds
-static __global__ void k_degree_facts(int32_t n, int32_t n_nd, int32_t n_ref, const int32_t *perm,
-                                      const int32_t *indeg_ext, const int32_t *off_int,
-                                      int32_t t_warp, int32_t t_cta, unsigned int *cnt,
+// internal in-degree (total, both in-list segments), m_d, n_u, max degrees (block-aggregated)
+static __global__ void k_degree_facts(int32_t n, int32_t n_nd, const int32_t *perm, const int32_t *indeg_ext,
+                                      const int32_t *off_int, int32_t *indeg_int, unsigned int *n_u,
                                       int *maxes, unsigned long long *m_d) {
+    __shared__ unsigned int s_u;
+    __shared__ int s_max[2];
+    __shared__ unsigned long long s_md;
+    if (threadIdx.x == 0) {
+        s_u = 0;
+        s_max[0] = s_max[1] = 0;
+        s_md = 0;
+    }
+    __syncthreads();
+    unsigned int u = 0;
+    int mo = 0, mi = 0;
+    unsigned long long md = 0;
     int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         int32_t id = indeg_ext[perm[i]];
         int32_t od = off_int[i + 1] - off_int[i];
-        int base = i < n_ref ? 0 : (i >= n_nd ? 2 : -1);
-        if (base >= 0) {
-            if (id > t_cta) atomicAdd(&cnt[base], 1u);
-            else if (id > t_warp) atomicAdd(&cnt[base + 1], 1u);
-        }
-        if (i >= n_nd) atomicAdd(m_d, (unsigned long long)id);
-        if (id == 0) atomicAdd(&cnt[4], 1u);
-        atomicMax(&maxes[0], od);
-        atomicMax(&maxes[1], id);
+        indeg_int[i] = id;
+        if (i >= n_nd) md += (unsigned long long)id;
+        u += id == 0;
+        mo = max(mo, od);
+        mi = max(mi, id);
     }
+    if (u) atomicAdd(&s_u, u);
+    if (md) atomicAdd(&s_md, md);
+    atomicMax(&s_max[0], mo);
+    atomicMax(&s_max[1], mi);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_u) atomicAdd(n_u, s_u);
+        if (s_md) atomicAdd(m_d, s_md);
+        atomicMax(&maxes[0], s_max[0]);
+        atomicMax(&maxes[1], s_max[1]);
+    }
+}
+
+// bins[k] = number of rows in [lo, hi) (in-degree sorted descending) with indeg > thr[k]
+static __global__ void k_bin_bounds(const int32_t *indeg_int, int32_t lo, int32_t hi, const int32_t *thr,
+                                    int nthr, int32_t *bounds) {
+    int k = threadIdx.x;
+    if (k >= nthr) return;
+    int32_t a = lo, b = hi;  // first row with indeg <= thr
+    while (a < b) {
+        int32_t mid = a + ((b - a) >> 1);
+        if (indeg_int[mid] > thr[k]) a = mid + 1;
+        else b = mid;
+    }
+    bounds[k] = a;
+}
+
+// edges of the ref+unref in-list segments in [lo, hi) of rows (for block budgets)
+static __global__ void k_range_edges(const int32_t *inr_off, const int32_t *inu_off, const int32_t *rows,
+                                     int nrows, long long *edges) {
+    int k = threadIdx.x;
+    if (k >= nrows) return;
+    edges[k] = (long long)inr_off[rows[k]] + inu_off[rows[k]];
 }
 
 // (hi << B | lo) -> (lo << B | hi)
@@ -271,45 +319,69 @@ static int bits_for(int32_t n) {
 }
 
 // ------------------------------------------------------------ plans
-Plan make_plan(int num_sms, const int32_t (*ranges)[3], int nranges) {
+// Blocks go to segments in proportion to their work (in-list entries + 2 per
+// row), at most as many as the segment has row groups, within a budget of
+// block_budget + one per segment (< kMaxBlocks).
+struct RangeSpec {
+    int32_t lo, hi, lanes;
+    long long edges;
+};
+
+static Plan make_plan(const RangeSpec *r, int nr, int budget) {
     Plan P{};
+    double total = 0;
+    for (int k = 0; k < nr; k++)
+        if (r[k].hi > r[k].lo) total += (double)r[k].edges + 2.0 * (r[k].hi - r[k].lo);
     int blk = 0;
-    for (int k = 0; k < nranges && P.nseg < kMaxSeg; k++) {
-        int32_t lo = ranges[k][0], hi = ranges[k][1], kind = ranges[k][2];
-        if (hi <= lo) continue;
-        int64_t rows = hi - lo;
-        int64_t nb;
-        if (kind == SEG_THREAD) nb = (rows + kThreads - 1) / kThreads;
-        else if (kind == SEG_WARP) nb = (rows + (kThreads / 32) - 1) / (kThreads / 32);
-        else nb = rows;
-        nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)num_sms * 32));
-        Seg &s = P.seg[P.nseg++];
-        s.lo = lo;
-        s.hi = hi;
-        s.kind = kind;
-        s.blk0 = blk;
-        s.nblk = (int32_t)nb;
+    for (int k = 0; k < nr && P.nseg < kMaxSeg; k++) {
+        if (r[k].hi <= r[k].lo) continue;
+        const int64_t rows = r[k].hi - r[k].lo;
+        const double work = (double)r[k].edges + 2.0 * rows;
+        const int64_t groups_per_block = r[k].lanes ? kThreads / r[k].lanes : 1;
+        const int64_t need = (rows + groups_per_block - 1) / groups_per_block;
+        int64_t nb = (int64_t)(budget * (work / std::max(total, 1.0)) + 0.5);
+        nb = std::max<int64_t>(1, std::min(nb, need));
+        Seg &sg = P.seg[P.nseg++];
+        sg.lo = r[k].lo;
+        sg.hi = r[k].hi;
+        sg.lanes = r[k].lanes;
+        sg.blk0 = blk;
+        sg.nblk = (int32_t)nb;
         blk += (int)nb;
     }
     P.nblocks = std::max(blk, 1);
     return P;
 }
 
+// rows [lo, hi) of one class split at bounds[0..5] into block / 32 / 16 / 8 / 4 / 2 / 1 lanes
+static int class_ranges(int32_t lo, int32_t hi, const int32_t *bounds, const long long *e_lo,
+                        const long long *e_b, long long e_hi, RangeSpec *out) {
+    static const int lanes[kNumThr + 1] = {0, 32, 16, 8, 4, 2, 1};
+    int32_t a = lo;
+    long long ea = *e_lo;
+    for (int k = 0; k <= kNumThr; k++) {
+        const int32_t b = k < kNumThr ? bounds[k] : hi;
+        const long long eb = k < kNumThr ? e_b[k] : e_hi;
+        out[k] = RangeSpec{a, b, lanes[k], eb - ea};
+        a = b;
+        ea = eb;
+    }
+    return kNumThr + 1;
+}
+
 void build_plans(pr_graph *g) {
     const int32_t n = g->G.n, n_nd = g->G.n_nd, n_ref = g->G.n_ref;
-    int32_t nd_r[4][3] = {{0, g->ref_heavy, SEG_CTA},
-                          {g->ref_heavy, g->ref_med, SEG_WARP},
-                          {g->ref_med, n_ref, SEG_THREAD},
-                          {n_ref, n_nd, SEG_THREAD}};
-    int32_t d_r[3][3] = {{n_nd, g->d_heavy, SEG_CTA},
-                         {g->d_heavy, g->d_med, SEG_WARP},
-                         {g->d_med, n, SEG_THREAD}};
-    int32_t all_r[7][3];
-    for (int k = 0; k < 4; k++) std::memcpy(all_r[k], nd_r[k], sizeof(nd_r[k]));
-    for (int k = 0; k < 3; k++) std::memcpy(all_r[4 + k], d_r[k], sizeof(d_r[k]));
-    g->plan_nd = make_plan(g->num_sms, nd_r, 4);
-    g->plan_d = make_plan(g->num_sms, d_r, 3);
-    g->plan_all = make_plan(g->num_sms, all_r, 7);
+    // edges_at layout: [0..5] at bound_ref, [6..11] at bound_d, [12] row 0, [13] n_ref, [14] n_nd, [15] n
+    const long long *E = g->edges_at;
+    RangeSpec nd[kNumThr + 2], d[kNumThr + 1], all[2 * kNumThr + 3];
+    int k1 = class_ranges(0, n_ref, g->bound_ref, &E[12], &E[0], E[13], nd);
+    nd[k1++] = RangeSpec{n_ref, n_nd, 1, E[14] - E[13]};
+    int k2 = class_ranges(n_nd, n, g->bound_d, &E[14], &E[6], E[15], d);
+    for (int k = 0; k < k1; k++) all[k] = nd[k];
+    for (int k = 0; k < k2; k++) all[k1 + k] = d[k];
+    g->plan_nd = make_plan(nd, k1, g->block_budget);
+    g->plan_d = make_plan(d, k2, g->block_budget);
+    g->plan_all = make_plan(all, k1 + k2, g->block_budget);
 }
 
 }  // namespace pr
@@ -529,13 +601,41 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
         k_vertex_arrays<<<grid_for(n_nd, sms), kThreads, 0, s>>>(
             n_nd, g->out_off.as<int32_t>(), g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
             g->inv_deg64.as<double>(), g->inv_deg32.as<float>());
-    k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, n_ref, g->perm.as<int32_t>(), indeg.as<int32_t>(),
-                                           g->out_off.as<int32_t>(), kWarpRowMin, kCtaRowMin, fact_cnt,
-                                           maxes, m_d);
-    unsigned int hf[5];
+    Buf indeg_int, dev_small;
+    PR_TRY(indeg_int.alloc(sizeof(int32_t) * n, s));
+    PR_TRY(dev_small.alloc(1024, s));
+    k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, g->perm.as<int32_t>(), indeg.as<int32_t>(),
+                                           g->out_off.as<int32_t>(), indeg_int.as<int32_t>(), fact_cnt, maxes,
+                                           m_d);
+    // pull-bin boundaries: binary searches in the in-degree sorted classes
+    for (int k = 0; k < kNumThr; k++) g->thr[k] = kDefaultThr[k];
+    g->block_budget = sms * 16;
+    int32_t *d_thr = dev_small.as<int32_t>();            // [6]
+    int32_t *d_bounds = d_thr + 8;                      // [12]
+    int32_t *d_rows = d_thr + 24;                       // [16]
+    long long *d_edges = reinterpret_cast<long long *>(d_thr + 48);  // [16]
+    PR_CK(cudaMemcpyAsync(d_thr, g->thr, sizeof(g->thr), cudaMemcpyHostToDevice, s));
+    k_bin_bounds<<<1, 32, 0, s>>>(indeg_int.as<int32_t>(), 0, n_ref, d_thr, kNumThr, d_bounds);
+    k_bin_bounds<<<1, 32, 0, s>>>(indeg_int.as<int32_t>(), n_nd, n, d_thr, kNumThr, d_bounds + kNumThr);
+    PR_CK(cudaMemcpyAsync(g->bound_ref, d_bounds, sizeof(int32_t) * kNumThr, cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(g->bound_d, d_bounds + kNumThr, sizeof(int32_t) * kNumThr, cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaStreamSynchronize(s));
+    int32_t rows[2 * kNumThr + 4];
+    for (int k = 0; k < kNumThr; k++) {
+        rows[k] = g->bound_ref[k];
+        rows[kNumThr + k] = g->bound_d[k];
+    }
+    rows[12] = 0;
+    rows[13] = n_ref;
+    rows[14] = n_nd;
+    rows[15] = n;
+    PR_CK(cudaMemcpyAsync(d_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, s));
+    k_range_edges<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_rows, 16, d_edges);
+    PR_CK(cudaMemcpyAsync(g->edges_at, d_edges, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
+    unsigned int hu = 0;
     int hm[2];
     unsigned long long hmd = 0;
-    PR_CK(cudaMemcpyAsync(hf, fact_cnt, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(&hu, fact_cnt, sizeof(hu), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(&hmd, m_d, sizeof(hmd), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaEventRecord(e1, s));
@@ -545,10 +645,6 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
 
-    g->ref_heavy = (int32_t)hf[0];
-    g->ref_med = (int32_t)(hf[0] + hf[1]);
-    g->d_heavy = n_nd + (int32_t)hf[2];
-    g->d_med = n_nd + (int32_t)(hf[2] + hf[3]);
     DevGraph &G = g->G;
     G.n = n;
     G.n_nd = n_nd;
@@ -568,13 +664,15 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     G.perm = g->perm.as<int32_t>();
     G.inv = g->inv.as<int32_t>();
     build_plans(g);
+    if (g->plan_all.nblocks > kMaxBlocks || g->plan_nd.nblocks > kMaxBlocks)
+        return fail(PR_ECUDA, "internal: pull plan exceeds the partial-sum slots");
 
     pr_graph_info &I = g->info;
     I.n = n;
     I.n_nd = n_nd;
     I.n_ref = n_ref;
     I.n_d = n - n_nd;
-    I.n_u = (int32_t)hf[4];
+    I.n_u = (int32_t)hu;
     I.m = m;
     I.m_d = (int64_t)hmd;
     I.max_outdeg = hm[0];

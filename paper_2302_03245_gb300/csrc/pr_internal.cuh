@@ -75,24 +75,30 @@ struct DevGraph {
 };
 
 // Row ranges of a gather kernel, by work-group size.  Rows inside each
-// class are sorted by in-degree, so each bin is a contiguous range.
-enum { SEG_THREAD = 0, SEG_WARP = 1, SEG_CTA = 2 };
+// class are sorted by in-degree, so each bin is a contiguous range.  A
+// segment's rows are processed by groups of `lanes` threads (1..32, a power
+// of two; 0 = the whole block per row).
 struct Seg {
     int32_t lo, hi;   // rows [lo, hi)
-    int32_t kind;     // SEG_*
+    int32_t lanes;    // threads per row; 0 = one block per row
     int32_t blk0;     // first block of this segment
     int32_t nblk;     // blocks assigned
 };
-constexpr int kMaxSeg = 8;
+constexpr int kMaxSeg = 16;
 struct Plan {
     Seg seg[kMaxSeg];
     int32_t nseg;
     int32_t nblocks;
 };
 
-constexpr int kThreads = 256;   // block size of every row/vertex kernel
-constexpr int kWarpRowMin = 32; // in-degree above which a row gets a warp
-constexpr int kCtaRowMin = 4096;// in-degree above which a row gets a CTA
+constexpr int kThreads = 256;       // block size of every row/vertex kernel
+constexpr int kMaxBlocks = 16384;   // partial-sum slots of a reduction (>= any grid)
+constexpr int kWarpRowMin = 32;     // push bins: out-degree above which a vertex gets a warp
+constexpr int kCtaRowMin = 4096;    // push bins: out-degree above which a vertex gets a CTA
+// Pull bins (in-degree d): d > thr[0] block per row; thr[k] < d <= thr[k-1]
+// gets 32 >> (k-1) lanes; d <= thr[5] one lane.
+constexpr int kNumThr = 6;
+constexpr int32_t kDefaultThr[kNumThr] = {4096, 32, 16, 8, 4, 2};
 
 }  // namespace pr
 
@@ -106,17 +112,18 @@ struct pr_graph {
     // storage
     pr::Buf out_off, out_dst, ndeg, inv_deg64, inv_deg32, inr_off, inr_src, inu_off, inu_src, perm,
         inv;
-    // bin boundaries of the in-degree sorted classes
-    int32_t ref_heavy = 0, ref_med = 0;  // rows [0, ref_heavy) CTA, [ref_heavy, ref_med) warp
-    int32_t d_heavy = 0, d_med = 0;      // same for dangling rows, absolute ids
+    // pull bins: row boundaries of the in-degree sorted classes and the in-list
+    // entries in front of each boundary (ref + unref segments)
+    int32_t thr[pr::kNumThr] = {};
+    int32_t bound_ref[pr::kNumThr] = {}, bound_d[pr::kNumThr] = {};
+    long long edges_at[2 * pr::kNumThr + 4] = {};
+    int32_t block_budget = 0;
     pr::Plan plan_nd{}, plan_d{}, plan_all{};
-    int32_t max_rows_heavy = 0;
     // solver workspace (lazily allocated, reused across solves)
     void *ws = nullptr;
 };
 
 namespace pr {
-pr::Plan make_plan(int num_sms, const int32_t (*ranges)[3], int nranges);
 void build_plans(pr_graph *g);
 void destroy_workspace(pr_graph *g);
 }  // namespace pr

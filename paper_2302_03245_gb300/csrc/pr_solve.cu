@@ -35,7 +35,6 @@ namespace pr {
 
 enum { MODE_PUSH = 1, MODE_PULL = 2 };
 enum { OP_ROUND = 0, OP_POWER = 1, OP_CORRECT = 2, OP_PHASE2 = 3 };
-constexpr int kMaxBlocks = 8192;  // partial-sum slots per reduction
 
 struct Ctl {
     // parameters (host-written per solve)
@@ -413,26 +412,21 @@ template <typename T> struct RowArgs {
     Trace tr;
 };
 
-template <typename A, typename T>
-__device__ __forceinline__ A row_sum_seq(const int32_t *off, const int32_t *src, int j, const T *val) {
-    const int a = off[j], b = off[j + 1];
-    A acc0 = A(0), acc1 = A(0);
-    int e = a;
-    for (; e + 1 < b; e += 2) {
-        acc0 += (A)val[src[e]];
-        acc1 += (A)val[src[e + 1]];
+// sum of val[src[e]] over e in [off[j] + start, off[j+1]) stepping by `step`;
+// in-list entries are streamed once (evict-first), gathered values go through
+// the read-only cache (they are not written during the kernel)
+template <typename T>
+__device__ __forceinline__ T row_sum(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int j,
+                                     const T *__restrict__ val, int start, int step) {
+    const int a = __ldg(&off[j]), b = __ldg(&off[j + 1]);
+    T acc0 = T(0), acc1 = T(0);
+    int e = a + start;
+    for (; e + step < b; e += 2 * step) {
+        acc0 += __ldg(&val[__ldcs(&src[e])]);
+        acc1 += __ldg(&val[__ldcs(&src[e + step])]);
     }
-    if (e < b) acc0 += (A)val[src[e]];
+    if (e < b) acc0 += __ldg(&val[__ldcs(&src[e])]);
     return acc0 + acc1;
-}
-
-template <typename A, typename T>
-__device__ __forceinline__ A row_sum_strided(const int32_t *off, const int32_t *src, int j, const T *val,
-                                             int start, int step) {
-    const int a = off[j], b = off[j + 1];
-    A acc = A(0);
-    for (int e = a + start; e < b; e += step) acc += (A)val[src[e]];
-    return acc;
 }
 
 template <typename T, int OP>
@@ -469,6 +463,26 @@ __device__ __forceinline__ void row_epilogue(const DevGraph &G, const Ctl *ctl, 
     }
 }
 
+// rows of a segment handled by groups of LANES threads; the loop bound is
+// uniform across the block so the width-LANES shuffles always see full warps
+template <typename T, int OP, int LANES>
+__device__ __forceinline__ void rows_lanes(const DevGraph &G, const Seg &S, int lb, Ctl *ctl, RowArgs<T> &a,
+                                           bool use_unref, double &s1, double &s2, double &s3) {
+    constexpr int GPB = kThreads / LANES;
+    const int grp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    for (int base = S.lo + lb * GPB; base < S.hi; base += S.nblk * GPB) {
+        const int j = base + grp;
+        T acc = T(0);
+        if (j < S.hi) {
+            acc = row_sum<T>(G.inr_off, G.inr_src, j, a.val, lane, LANES);
+            if (use_unref) acc += row_sum<T>(G.inu_off, G.inu_src, j, a.val, lane, LANES);
+        }
+#pragma unroll
+        for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LANES);
+        if (j < S.hi && lane == 0) row_epilogue<T, OP>(G, ctl, a, j, acc, s1, s2, s3);
+    }
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads) k_rows(DevGraph G, Plan PL, Ctl *ctl, RowArgs<T> a) {
     // the loop kernels stop with the device flag; the one-shot sweeps
@@ -483,27 +497,20 @@ __global__ void __launch_bounds__(kThreads) k_rows(DevGraph G, Plan PL, Ctl *ctl
     double s1 = 0, s2 = 0, s3 = 0;
     __shared__ double shd[32];
     __shared__ T sht[32];
-    if (S.kind == SEG_THREAD) {
-        for (int j = S.lo + lb * blockDim.x + threadIdx.x; j < S.hi; j += S.nblk * blockDim.x) {
-            T acc = row_sum_seq<T>(G.inr_off, G.inr_src, j, a.val);
-            if (use_unref) acc += row_sum_seq<T>(G.inu_off, G.inu_src, j, a.val);
-            row_epilogue<T, OP>(G, ctl, a, j, acc, s1, s2, s3);
-        }
-    } else if (S.kind == SEG_WARP) {
-        const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-        for (int j = S.lo + lb * wpb + (threadIdx.x >> 5); j < S.hi; j += S.nblk * wpb) {
-            T acc = row_sum_strided<T>(G.inr_off, G.inr_src, j, a.val, lane, 32);
-            if (use_unref) acc += row_sum_strided<T>(G.inu_off, G.inu_src, j, a.val, lane, 32);
-            acc = warp_sum(acc);
-            if (lane == 0) row_epilogue<T, OP>(G, ctl, a, j, acc, s1, s2, s3);
-        }
-    } else {
-        for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
-            T acc = row_sum_strided<T>(G.inr_off, G.inr_src, j, a.val, threadIdx.x, blockDim.x);
-            if (use_unref) acc += row_sum_strided<T>(G.inu_off, G.inu_src, j, a.val, threadIdx.x, blockDim.x);
-            acc = block_sum(acc, sht);
-            if (threadIdx.x == 0) row_epilogue<T, OP>(G, ctl, a, j, acc, s1, s2, s3);
-        }
+    switch (S.lanes) {
+        case 1: rows_lanes<T, OP, 1>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        case 2: rows_lanes<T, OP, 2>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        case 4: rows_lanes<T, OP, 4>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        case 8: rows_lanes<T, OP, 8>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        case 16: rows_lanes<T, OP, 16>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        case 32: rows_lanes<T, OP, 32>(G, S, lb, ctl, a, use_unref, s1, s2, s3); break;
+        default:
+            for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
+                T acc = row_sum<T>(G.inr_off, G.inr_src, j, a.val, threadIdx.x, blockDim.x);
+                if (use_unref) acc += row_sum<T>(G.inu_off, G.inu_src, j, a.val, threadIdx.x, blockDim.x);
+                acc = block_sum(acc, sht);
+                if (threadIdx.x == 0) row_epilogue<T, OP>(G, ctl, a, j, acc, s1, s2, s3);
+            }
     }
     if (OP != OP_POWER) return;
     // Power: ||pi_{k+1} - pi_k||_1, d^T pi_{k+1}, e^T pi_{k+1}
