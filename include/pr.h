@@ -207,6 +207,37 @@ pr_status pr_solve(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec, c
 pr_status pr_solve_ex(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec, const pr_pvec *p,
                       const pr_opts *opts, double *out, int out_is_device, pr_stats *st);
 
+/*
+ * Allocation-free Power-method PageRank.  The paper has no counterpart: this
+ * is the Power iteration of its Sec. 4 baseline, packaged for callers that
+ * cannot allocate device memory -- a framework that owns the whole device
+ * memory pool, code on a path where cudaMalloc/cudaFree could synchronise the
+ * device, a plug-in that is only handed buffers.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: its working vectors live in one
+ * fixed array compiled into this library (about 12.6 MB, held on every GPU
+ * that loads the library until the process exits).  Hence:
+ *   - n must be at most 524,288; larger n returns PR_EINVAL;
+ *   - all calls on a device share that array and the next call overwrites
+ *     it: calls that overlap on the GPU (other host threads, other streams)
+ *     race, and the caller must serialise them;
+ *   - the first call on each device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ * Inputs (device pointers in the caller's vertex ids; not validated, they
+ * must describe one valid graph): out_off[n+1] (out-list offsets, giving
+ * deg(v)), in_off[n+1] and in_src[m] (in-lists S(v)).  p is uniform.  From
+ * pi_0 = e/n it iterates pi_{k+1} = c P pi_k + (c d^T pi_k + (1-c) e^T pi_k) e/n
+ * until ||pi_{k+1} - pi_k||_1 <= tol or max_iter iterations, and writes the
+ * normalised last iterate to pi[n] (device, owned by the caller).  iters
+ * (host, may be NULL) receives the iteration count.  Runs on cuda_stream and
+ * synchronises it before returning.
+ * Errors: PR_EINVAL (sizes, c, tol, max_iter), PR_ENOTCONV (max_iter reached;
+ * pi still written), PR_ECUDA.
+ */
+pr_status pr_power_noalloc(int32_t n, const int32_t *out_off, const int32_t *in_off, const int32_t *in_src,
+                           double c, double tol, int32_t max_iter, double *pi, void *cuda_stream,
+                           int32_t *iters);
+
 /* Release a graph and its workspace (NULL is ignored). */
 void pr_destroy(pr_graph *g);
 
