@@ -5,8 +5,10 @@ Workload: the single-graph configuration -- directed R-MAT (a,b,c,d) =
 (0.57,0.19,0.19,0.05), scale 22 (4,194,304 vertices), edge factor 16
 (67,108,864 sampled edges; self-loops and repeats removed), out-edges of a
 seeded 20% of vertices and in-edges of an independent 10% deleted, vertex
-ids randomly relabelled; c = 0.85, uniform p, IFP2 in FP64 stopped at
-residual L1 <= 1e-9.  One step = one pr_solve on the resident, preprocessed
+ids randomly relabelled; c = 0.85, uniform p, IFP2 stopped at residual L1
+<= 1e-9, mass carried as double-float pairs (48-bit significand on FP32
+instructions; GB300's FP64 pipe is 1/64 of its FP32 rate), with the IEEE
+FP64 and FP32 forms measured alongside.  One step = one pr_solve on the resident, preprocessed
 graph (frontier activation, push/pull rounds, phase 2, normalisation).
 
 Metric: GEdges pushed per second = (sum over rounds of the frontier's valid
@@ -54,10 +56,10 @@ def parse():
 
 
 def workload(scale):
-    return dict(workload=f"rmat{scale}_ifp2_fp64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
+    return dict(workload=f"rmat{scale}_ifp2_df64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
                 vertices=1 << scale, edge_factor=16, sampled_edges=16 << scale, dangling_deleted=0.20,
                 unref_deleted=0.10, relabel="seeded random permutation", seed=1, c=C, p="uniform",
-                algo="IFP2", precision="fp64")
+                algo="IFP2", precision="df64", eps=1e-9)
 
 
 def make_graph(scale):
@@ -114,9 +116,10 @@ class Clocks:
 
 # ------------------------------------------------------------------ roofline
 def algorithmic_bytes_pull_round(info, s, scan_entries, rows, active_rows):
-    """k_rows pull round: per scanned in-list entry 4 B (source id) + s (gathered w);
-    per row 4 B (offset) + 2s (r read and write); per active row 2s (x read and write)."""
-    return scan_entries * (4 + s) + rows * (4 + 2 * s) + active_rows * 2 * s
+    """k_round_pull: per scanned in-list entry 4 B (source id) + s (gathered w);
+    per row 4 B (offset) + 2s (r read and write) + the next activation's s (w write)
+    + s (1/deg) + 4 B (valid out-degree); per active row 2s (x read and write)."""
+    return scan_entries * (4 + s) + rows * (8 + 4 * s) + active_rows * 2 * s
 
 
 def algorithmic_bytes_activate(n_nd, s):
@@ -229,7 +232,7 @@ def main():
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
-    def solve(algo=pr.PR_IFP2, prec=pr.PR_FP64, eps=args.eps, opts=None):
+    def solve(algo=pr.PR_IFP2, prec=pr.PR_DF64, eps=args.eps, opts=None):
         opts = dict(opts or {})
         if args.host_rounds:
             opts.setdefault("use_graph", -1)
@@ -275,7 +278,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "df64 (fp32 hi+lo pairs; fp64 final sums and output)",
+            "data": "synthetic",
             "config": dict(workload(args.scale), l2="512 MB buffer written between timed steps",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "gpu_launches": int(launches), "clocks": clk,
@@ -318,7 +322,7 @@ def main():
     scan_ref = pull_scan_total / max(len(pull_rounds), 1)
     kernels = {k: dict(launches=v["launches"] // prof_runs, avg_ms=v["ms"] / max(v["launches"], 1),
                        share=v["ms"] / total_k_ms) for k, v in agg.items()}
-    if dom == "k_rows<OP_ROUND>":
+    if dom == "k_round_pull":
         F = trace["F"][pull_rounds].astype(np.float64)
         rows = info["n_nd"]
         bytes_per = [algorithmic_bytes_pull_round(info, s, scan_ref, rows, f) for f in F]
@@ -343,9 +347,10 @@ def main():
     solve()
     ifp2_l1 = float((out - truth).abs().sum())
     ifp2_ms = t_step
-    legs = {"reference_solution": f"GPU Power FP64 to ||delta||_1 <= 1e-14 (certified L1 <= {ref_bound:.2e})",
-            "ifp2_fp64": dict(ms=ifp2_ms, l1=ifp2_l1, rounds=rounds[0], gedges_s=value)}
-    for nm, algo, prec, eps in (("ifp1_fp64", pr.PR_IFP1, pr.PR_FP64, args.eps),
+    legs = {"reference_solution": f"GPU Power IEEE FP64 to ||delta||_1 <= 1e-14 (certified L1 <= {ref_bound:.2e})",
+            "ifp2_df64": dict(ms=ifp2_ms, l1=ifp2_l1, rounds=rounds[0], gedges_s=value)}
+    for nm, algo, prec, eps in (("ifp2_fp64", pr.PR_IFP2, pr.PR_FP64, args.eps),
+                                ("ifp1_df64", pr.PR_IFP1, pr.PR_DF64, args.eps),
                                 ("ifp2_fp32", pr.PR_IFP2, pr.PR_FP32, 1e-6)):
         tms = []
         for _ in range(3):
@@ -355,21 +360,22 @@ def main():
         legs[nm] = dict(ms=statistics.median(tms), l1=float((out - truth).abs().sum()), rounds=st["rounds"],
                         fp64_rounds=st["fp64_rounds"], eps=eps,
                         gedges_s=st["edges_pushed"] / (statistics.median(tms) / 1e3) / 1e9)
-    power = []
-    for tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11):
-        tms = []
-        for _ in range(3):
-            flush.zero_()
-            st = solve(algo=pr.PR_POWER, eps=tol)
-            tms.append(st["ms"])
-        err = float((out - truth).abs().sum())
-        power.append(dict(tol=tol, ms=statistics.median(tms), l1=err, iters=st["rounds"]))
-        if err <= ifp2_l1:
-            break
-    eq = next((p for p in power if p["l1"] <= ifp2_l1), None)
-    legs["power_fp64_ladder"] = power
-    if eq:
-        legs["power_at_equal_l1"] = dict(eq, speedup_ifp2=eq["ms"] / ifp2_ms)
+    for pname, pprec in (("df64", pr.PR_DF64), ("fp64", pr.PR_FP64)):
+        power = []
+        for tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11):
+            tms = []
+            for _ in range(3):
+                flush.zero_()
+                st = solve(algo=pr.PR_POWER, prec=pprec, eps=tol)
+                tms.append(st["ms"])
+            err = float((out - truth).abs().sum())
+            power.append(dict(tol=tol, ms=statistics.median(tms), l1=err, iters=st["rounds"]))
+            if err <= ifp2_l1:
+                break
+        eq = next((q for q in power if q["l1"] <= ifp2_l1), None)
+        legs[f"power_{pname}_ladder"] = power
+        if eq:
+            legs[f"power_{pname}_at_equal_l1"] = dict(eq, speedup_ifp2=eq["ms"] / ifp2_ms)
     line["vs_power"] = legs
     pre = []
     for _ in range(3):
@@ -397,7 +403,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gh = pr.pr_graph_create(g.n, g.m, h_off, h_dst, mem_is_device=False, stream=stream)
-        _, st, status = pr.pr_solve(gh, C, args.eps, pr.PR_IFP2, pr.PR_FP64, out=h_out)
+        _, st, status = pr.pr_solve(gh, C, args.eps, pr.PR_IFP2, pr.PR_DF64, out=h_out)
         pr.pr_destroy(gh)
         torch.cuda.synchronize()
         if k > 0:
@@ -407,7 +413,7 @@ def main():
                    "h2d_bytes_per_step": int(off.nbytes + dst.nbytes), "d2h_bytes_per_step": int(8 * g.n),
                    "ms_per_step": statistics.median(e2e_ms),
                    "includes": "pr_graph_create from pinned host CSR (copy, validation, preprocessing) + "
-                               "pr_solve IFP2 FP64 + copy of pi to pinned host memory"}
+                               "pr_solve IFP2 df64 + copy of pi to pinned host memory"}
 
     # ---- the oracle on the host cores (bounded sample)
     import oracle

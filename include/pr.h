@@ -54,12 +54,16 @@ typedef enum {
 } pr_algo;
 
 typedef enum {
-    PR_FP64 = 0, /* residual, reserve and pushed mass in double */
-    PR_FP32 = 1  /* residual, reserve and pushed mass in float; residual-L1 and
-                    dangling sums in double; at the end an FP64 correction sweep
-                    recomputes the residual from the reserve and FP64 rounds
-                    finish the solve (not in the paper; the arithmetic identity
-                    is that of Eq. 4) */
+    PR_FP64 = 0, /* residual, reserve and pushed mass in IEEE double (on GB300 the
+                    FP64 pipe runs at 1/64 of FP32: the reference form, slow) */
+    PR_FP32 = 1, /* residual, reserve and pushed mass in float; sums of the
+                    residual L1 and dangling mass in double-float with a final
+                    FP64 sum; at the end an FP64 correction sweep recomputes the
+                    residual from the reserve, and double-float rounds finish the
+                    solve (not in the paper; the identity used is that of Eq. 4) */
+    PR_DF64 = 2  /* residual, reserve and pushed mass as double-float pairs
+                    (hi + lo floats, 48-bit significand, FP32 instructions only);
+                    final sums and the output in FP64 */
 } pr_prec;
 
 typedef enum {
@@ -105,9 +109,9 @@ typedef struct {
 /* Kernel kinds of a solve, for pr_kernel_profile. */
 enum {
     PR_K_ACTIVATE = 0, /* frontier selection, residual L1, dense pending push */
-    PR_K_COMMIT = 1,   /* push rounds: reserve update of the frontier */
-    PR_K_PUSH = 2,     /* push rounds: atomic push along out-lists */
-    PR_K_PULL = 3,     /* pull rounds: gather along in-lists */
+    PR_K_COMMIT = 1,   /* reserved (the push kernel commits the frontier itself) */
+    PR_K_PUSH = 2,     /* push rounds: reserve update + atomic push along out-lists */
+    PR_K_PULL = 3,     /* pull rounds: gather along in-lists + next activation */
     PR_K_POWER = 4,    /* Power method iteration */
     PR_K_OTHER = 5,    /* init, correction, phase 2, finalize */
     PR_K_KINDS = 8
@@ -237,6 +241,67 @@ pr_status pr_solve_ex(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec
 pr_status pr_power_noalloc(int32_t n, const int32_t *out_off, const int32_t *in_off, const int32_t *in_src,
                            double c, double tol, int32_t max_iter, double *pi, void *cuda_stream,
                            int32_t *iters);
+
+/*
+ * Solve many independent problems at once: IFP1 or IFP2 (Alg. 2 / Alg. 3) on
+ * graphs gs[0..count) of any sizes, with damping c[k] and stopping threshold
+ * eps[k] (as in pr_solve), uniform personalization (ps may be NULL; any
+ * ps[k].nnz >= 0 is rejected), all on gs[0]'s stream and device.  Every
+ * problem keeps its own state in one packed device arena; each round phase
+ * of all problems is one persistent kernel whose blocks take row tiles of
+ * any problem from a device work queue, and the phases run inside a CUDA
+ * graph until every problem has stopped.  The arithmetic and stopping rule
+ * of each problem are those of pr_solve with the same options (opts may be
+ * NULL; traces and profile are ignored).  outs[k][gs[k] n] receives problem
+ * k's PageRank (device pointers if outs_are_device, else host).  sts
+ * (optional, count entries) gets per-problem reports; ms is the batch time.
+ * Errors: PR_EINVAL, PR_ENOTCONV (some problem hit its cap; all outputs are
+ * written), PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_solve_batch(pr_graph *const *gs, int32_t count, const double *c, const double *eps, pr_algo a,
+                         pr_prec prec, const pr_pvec *ps, const pr_opts *opts, double *const *outs,
+                         int outs_are_device, pr_stats *sts);
+
+/*
+ * Serving: continuous batching of IFP2 requests (Alg. 3) on resident graphs.
+ * A server owns one host thread and a CUDA stream.  The thread admits queued
+ * requests while their device memory fits the budget.  On every step it
+ * advances all active requests by a few round phases: one persistent kernel
+ * per phase takes row tiles of any request from a device work queue.  It
+ * finishes the requests that stopped and hands their results back.  A
+ * request that arrives while others run joins at the next step.  Arithmetic
+ * and stopping rule per request are pr_solve's IFP2 with the default
+ * options.
+ *
+ * pr_server_create: hbm_budget_bytes bounds the device memory of the
+ *   admitted requests' states (graphs are the caller's and not counted).
+ *   cuda_stream: the stream the server runs on (NULL = legacy default); the
+ *   current device is the server's.  *out receives the handle.
+ *   Errors: PR_EINVAL (NULL out, zero budget), PR_ENOMEM, PR_ECUDA.
+ * pr_server_submit: queue one request on graph g (created on the server's
+ *   device; it must stay alive until every ticket on it has been polled
+ *   to completion).  c, eps as in pr_solve; prec is PR_DF64 or PR_FP32 (float
+ *   rounds, correction sweep, double-float rounds: see pr_prec); p is a host pr_pvec
+ *   (NULL = uniform; sparse seeds for personalized PageRank), copied.
+ *   *ticket receives the request's id.  Thread-safe.  Errors: PR_EINVAL
+ *   (arguments, p, a request larger than the whole budget), PR_EAGAIN
+ *   (queue full: retry later), PR_ENOMEM.
+ * pr_server_poll: PR_EBUSY while the request runs.  Once it has finished:
+ *   out[g n] (host, may be NULL) receives the PageRank in the caller's ids
+ *   (sum 1, FP64), st (may be NULL) the report (ms = submit to finish), and
+ *   the ticket is released: PR_OK, or PR_ENOTCONV (round cap reached, or no
+ *   vertex left above the activation threshold before R <= eps; out is
+ *   written), or the error that stopped the server's thread (PR_ECUDA,
+ *   PR_ENOMEM; out is not written).  PR_EINVAL for an unknown or released
+ *   ticket.  Thread-safe.
+ * pr_server_destroy: stop the thread, drop unfinished requests, free the
+ *   server's device memory (NULL is ignored).
+ */
+pr_status pr_server_create(size_t hbm_budget_bytes, void *cuda_stream, pr_server **out);
+pr_status pr_server_submit(pr_server *s, pr_graph *g, double c, double eps, pr_prec prec, const pr_pvec *p,
+                           int64_t *ticket);
+pr_status pr_server_poll(pr_server *s, int64_t ticket, double *out, pr_stats *st);
+void pr_server_destroy(pr_server *s);
 
 /* Release a graph and its workspace (NULL is ignored). */
 void pr_destroy(pr_graph *g);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libpr.so")
 
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY = range(8)
 PR_POWER, PR_IFP1, PR_IFP2 = 0, 1, 2
-PR_FP64, PR_FP32 = 0, 1
+PR_FP64, PR_FP32, PR_DF64 = 0, 1, 2
 PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL = 0, 1, 2
 STATUS_NAMES = ["PR_OK", "PR_EINVAL", "PR_ENOMEM", "PR_ECUDA", "PR_ENOTCONV", "PR_ETIMEOUT", "PR_EAGAIN",
                 "PR_EBUSY"]
@@ -52,7 +52,7 @@ class pr_stats(ctypes.Structure):
 PR_K_ACTIVATE, PR_K_COMMIT, PR_K_PUSH, PR_K_PULL, PR_K_POWER, PR_K_OTHER = range(6)
 PR_K_KINDS = 8
 KERNEL_NAMES = {PR_K_ACTIVATE: "k_activate", PR_K_COMMIT: "k_commit", PR_K_PUSH: "k_push",
-                PR_K_PULL: "k_rows<OP_ROUND>", PR_K_POWER: "k_rows<OP_POWER>", PR_K_OTHER: "other"}
+                PR_K_PULL: "k_round_pull", PR_K_POWER: "k_sweep<OP_POWER>", PR_K_OTHER: "other"}
 
 
 class pr_kernel_profile(ctypes.Structure):
@@ -109,8 +109,20 @@ def lib() -> ctypes.CDLL:
         L.pr_solve_ex.argtypes = [P, dbl, dbl, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pr_pvec),
                                   ctypes.POINTER(pr_opts), P, ctypes.c_int, ctypes.POINTER(pr_stats)]
         L.pr_solve_ex.restype = ctypes.c_int
+        L.pr_solve_batch.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(pr_pvec), ctypes.POINTER(pr_opts),
+                                     ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(pr_stats)]
+        L.pr_solve_batch.restype = ctypes.c_int
         L.pr_destroy.argtypes = [P]
         L.pr_destroy.restype = None
+        L.pr_server_create.argtypes = [ctypes.c_size_t, P, ctypes.POINTER(P)]
+        L.pr_server_create.restype = ctypes.c_int
+        L.pr_server_submit.argtypes = [P, P, dbl, dbl, ctypes.c_int, ctypes.POINTER(pr_pvec), ctypes.POINTER(i64)]
+        L.pr_server_submit.restype = ctypes.c_int
+        L.pr_server_poll.argtypes = [P, i64, P, ctypes.POINTER(pr_stats)]
+        L.pr_server_poll.restype = ctypes.c_int
+        L.pr_server_destroy.argtypes = [P]
+        L.pr_server_destroy.restype = None
         L.pr_last_error.restype = ctypes.c_char_p
         L.pr_version.restype = ctypes.c_char_p
         L.pr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
@@ -236,6 +248,108 @@ def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_
     if prof is not None:
         d["profile"] = prof.as_dict()
     return out, d, status
+
+
+def pr_solve_batch(graphs, c, eps, algo, prec=PR_DF64, outs=None, opts: dict | None = None, check: bool = True):
+    """Wraps pr_solve_batch.  graphs: list of handles (or Graph objects); c, eps:
+    scalars or per-graph sequences; outs: None (new host arrays), a list of numpy
+    float64 arrays, or a list of torch float64 CUDA tensors.  Returns
+    (outs, list of stats dicts, status)."""
+    hs = [g.h if isinstance(g, Graph) else g for g in graphs]
+    k = len(hs)
+    ns = [pr_graph_get_info(h)["n"] for h in hs]
+    cs = (ctypes.c_double * k)(*([float(c)] * k if np.isscalar(c) else [float(v) for v in c]))
+    es = (ctypes.c_double * k)(*([float(eps)] * k if np.isscalar(eps) else [float(v) for v in eps]))
+    if outs is None:
+        outs = [np.empty(n, dtype=np.float64) for n in ns]
+    dev = not isinstance(outs[0], np.ndarray)
+    optr = (ctypes.c_void_p * k)(*[_ptr(o) for o in outs])
+    harr = (ctypes.c_void_p * k)(*[h.value for h in hs])
+    sts = (pr_stats * k)()
+    o = pr_opts()
+    for key, v in (opts or {}).items():
+        setattr(o, key, v)
+    status = lib().pr_solve_batch(harr, k, cs, es, int(algo), int(prec), None, ctypes.byref(o), optr,
+                                  1 if dev else 0, sts)
+    if check and status not in (PR_OK, PR_ENOTCONV):
+        _check(status)
+    return outs, [s.as_dict() for s in sts], status
+
+
+# ------------------------------------------------------------------ serving
+def pr_server_create(hbm_budget_bytes: int, stream=None) -> ctypes.c_void_p:
+    """Wraps pr_server_create (current device; stream: torch stream, raw handle or None)."""
+    s = ctypes.c_void_p()
+    _check(lib().pr_server_create(int(hbm_budget_bytes), _stream_handle(stream), ctypes.byref(s)))
+    return s
+
+
+def pr_server_submit(server, g, c: float, eps: float, prec: int = PR_DF64, p=None, p_idx=None) -> int:
+    """Wraps pr_server_submit; p/p_idx as in pr_solve (host only).  Returns the ticket."""
+    n = pr_graph_get_info(g)["n"]
+    pv, keep = make_pvec(n, p, p_idx, False)
+    t = ctypes.c_int64()
+    _check(lib().pr_server_submit(server, g, float(c), float(eps), int(prec), ctypes.byref(pv), ctypes.byref(t)))
+    return t.value
+
+
+def pr_server_poll(server, ticket: int, n: int):
+    """Wraps pr_server_poll.  Returns None while the request runs (PR_EBUSY), else
+    (out, stats dict, status) with status PR_OK or PR_ENOTCONV; raises on errors."""
+    out = np.empty(n, dtype=np.float64)
+    st = pr_stats()
+    status = lib().pr_server_poll(server, int(ticket), out.ctypes.data, ctypes.byref(st))
+    if status == PR_EBUSY:
+        return None
+    if status not in (PR_OK, PR_ENOTCONV):
+        _check(status)
+    return out, st.as_dict(), status
+
+
+def pr_server_destroy(server) -> None:
+    if server is not None and server.value:
+        lib().pr_server_destroy(server)
+        server.value = None
+
+
+class Server:
+    """RAII wrapper of a pr_server with a blocking wait()."""
+
+    def __init__(self, hbm_budget_bytes: int, stream=None):
+        self.h = pr_server_create(hbm_budget_bytes, stream)
+        self._n = {}
+
+    def submit(self, g, c, eps, prec=PR_DF64, p=None, p_idx=None) -> int:
+        h = g.h if isinstance(g, Graph) else g
+        t = pr_server_submit(self.h, h, c, eps, prec, p, p_idx)
+        self._n[t] = pr_graph_get_info(h)["n"]
+        return t
+
+    def poll(self, ticket):
+        r = pr_server_poll(self.h, ticket, self._n[ticket])
+        if r is not None:
+            self._n.pop(ticket, None)
+        return r
+
+    def wait(self, ticket, timeout_s: float = 120.0, sleep_s: float = 0.0005):
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not finished after {timeout_s} s")
+            time.sleep(sleep_s)
+
+    def close(self):
+        pr_server_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ------------------------------------------------------- torch allocator hook

@@ -15,6 +15,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -211,7 +212,7 @@ static __global__ void k_lower_bound(const uint64_t *keys, int64_t m, uint64_t t
 }
 
 static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const int32_t *dst,
-                                       int32_t *ndeg, double *inv64, float *inv32) {
+                                       int32_t *ndeg, double *inv64, float *inv32, float2 *invdf) {
     int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_nd; i += stride) {
         int32_t a = off[i], b = off[i + 1];
@@ -225,6 +226,8 @@ static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const i
         double inv = 1.0 / (double)(b - a);
         inv64[i] = inv;
         inv32[i] = (float)inv;
+        const float inv_hi = __double2float_rn(inv);
+        invdf[i] = make_float2(inv_hi, __double2float_rn(inv - (double)inv_hi));
     }
 }
 
@@ -597,10 +600,11 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_TRY(g->ndeg.alloc(sizeof(int32_t) * std::max(n_nd, 1), s));
     PR_TRY(g->inv_deg64.alloc(sizeof(double) * std::max(n_nd, 1), s));
     PR_TRY(g->inv_deg32.alloc(sizeof(float) * std::max(n_nd, 1), s));
+    PR_TRY(g->inv_degdf.alloc(sizeof(float2) * std::max(n_nd, 1), s));
     if (n_nd)
         k_vertex_arrays<<<grid_for(n_nd, sms), kThreads, 0, s>>>(
             n_nd, g->out_off.as<int32_t>(), g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
-            g->inv_deg64.as<double>(), g->inv_deg32.as<float>());
+            g->inv_deg64.as<double>(), g->inv_deg32.as<float>(), g->inv_degdf.as<float2>());
     Buf indeg_int, dev_small;
     PR_TRY(indeg_int.alloc(sizeof(int32_t) * n, s));
     PR_TRY(dev_small.alloc(1024, s));
@@ -632,6 +636,9 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_CK(cudaMemcpyAsync(d_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, s));
     k_range_edges<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_rows, 16, d_edges);
     PR_CK(cudaMemcpyAsync(g->edges_at, d_edges, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
+    int32_t hnd[2] = {0, 0};
+    PR_CK(cudaMemcpyAsync(&hnd[0], g->inr_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(&hnd[1], g->inu_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     unsigned int hu = 0;
     int hm[2];
     unsigned long long hmd = 0;
@@ -657,12 +664,15 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     G.ndeg = g->ndeg.as<int32_t>();
     G.inv_deg64 = g->inv_deg64.as<double>();
     G.inv_deg32 = g->inv_deg32.as<float>();
+    G.inv_degdf = g->inv_degdf.as<float2>();
     G.inr_off = g->inr_off.as<int32_t>();
     G.inr_src = g->inr_src.as<int32_t>();
     G.inu_off = g->inu_off.as<int32_t>();
     G.inu_src = g->inu_src.as<int32_t>();
     G.perm = g->perm.as<int32_t>();
     G.inv = g->inv.as<int32_t>();
+    g->scan_nd_ref = hnd[0];
+    g->scan_nd_unref = hnd[1];
     build_plans(g);
     if (g->plan_all.nblocks > kMaxBlocks || g->plan_nd.nblocks > kMaxBlocks)
         return fail(PR_ECUDA, "internal: pull plan exceeds the partial-sum slots");
@@ -679,7 +689,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     I.max_indeg = hm[1];
     I.ms_preprocess = ms;
     I.device_bytes = g->out_off.bytes + g->out_dst.bytes + g->ndeg.bytes + g->inv_deg64.bytes +
-                     g->inv_deg32.bytes + g->inr_off.bytes + g->inr_src.bytes + g->inu_off.bytes +
+                     g->inv_deg32.bytes + g->inv_degdf.bytes + g->inr_off.bytes + g->inr_src.bytes + g->inu_off.bytes +
                      g->inu_src.bytes + g->perm.bytes + g->inv.bytes;
     return PR_OK;
 }
@@ -702,6 +712,8 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_of
     }
     pr_graph *G = new (std::nothrow) pr_graph();
     if (!G) return fail(PR_ENOMEM, "host allocation failed");
+    static std::atomic<uint64_t> serial{0};
+    G->uid = ++serial;
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
                                (cudaStream_t)cuda_stream, G);
     if (st != PR_OK) {

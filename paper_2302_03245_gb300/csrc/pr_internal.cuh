@@ -16,15 +16,15 @@ void set_error(const std::string &msg);
 pr_status fail(pr_status st, const std::string &msg);
 pr_status cuda_fail(cudaError_t e, const char *what);
 
-#define PR_CK(call)                                                     \
+#define PR_CK(...)                                                      \
     do {                                                                \
-        cudaError_t _e = (call);                                        \
-        if (_e != cudaSuccess) return ::pr::cuda_fail(_e, #call);       \
+        cudaError_t _e = (__VA_ARGS__);                                 \
+        if (_e != cudaSuccess) return ::pr::cuda_fail(_e, #__VA_ARGS__); \
     } while (0)
 
-#define PR_TRY(call)                                                    \
+#define PR_TRY(...)                                                     \
     do {                                                                \
-        pr_status _s = (call);                                          \
+        pr_status _s = (__VA_ARGS__);                                   \
         if (_s != PR_OK) return _s;                                     \
     } while (0)
 
@@ -66,6 +66,7 @@ struct DevGraph {
     const int32_t *ndeg;      // [n_nd]
     const double *inv_deg64;  // [n_nd] 1/deg
     const float *inv_deg32;   // [n_nd]
+    const float2 *inv_degdf;  // [n_nd] 1/deg as a double-float pair (hi, lo)
     const int32_t *inr_off;   // [n+1]
     const int32_t *inr_src;   // [m_ref]
     const int32_t *inu_off;   // [n+1]
@@ -104,20 +105,22 @@ constexpr int32_t kDefaultThr[kNumThr] = {4096, 32, 16, 8, 4, 2};
 
 // The opaque ABI handle.
 struct pr_graph {
+    uint64_t uid = 0;  // process-unique serial number (caches keyed by graph use it, not the address)
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
     pr::DevGraph G{};
     pr_graph_info info{};
     // storage
-    pr::Buf out_off, out_dst, ndeg, inv_deg64, inv_deg32, inr_off, inr_src, inu_off, inu_src, perm,
-        inv;
+    pr::Buf out_off, out_dst, ndeg, inv_deg64, inv_deg32, inv_degdf, inr_off, inr_src, inu_off, inu_src,
+        perm, inv;
     // pull bins: row boundaries of the in-degree sorted classes and the in-list
     // entries in front of each boundary (ref + unref segments)
     int32_t thr[pr::kNumThr] = {};
     int32_t bound_ref[pr::kNumThr] = {}, bound_d[pr::kNumThr] = {};
     long long edges_at[2 * pr::kNumThr + 4] = {};
     int32_t block_budget = 0;
+    int64_t scan_nd_ref = 0, scan_nd_unref = 0;  // in-list entries of the non-dangling rows, per segment
     pr::Plan plan_nd{}, plan_d{}, plan_all{};
     // solver workspace (lazily allocated, reused across solves)
     void *ws = nullptr;

@@ -1,0 +1,955 @@
+// pr_kernels.cuh -- device code of the IFP1 / IFP2 rounds (Alg. 2, Alg. 3),
+// the Power-method iteration (Sec. 4), the FP64 correction sweep, the IFP2
+// phase-2 pull and the normalisation.
+//
+// Round semantics: synchronous snapshot rounds (Sec. 3.3.1 counts one
+// "iteration" as one scan over all vertices) with a (1-c) reserve, which does
+// not change the normalised result (Sec. 3.1, after Eq. 4):
+//
+//   R_t = sum_{i non-dangling} |r_i|            stop when R_t <= eps
+//   F_t = { i non-dangling : |r_i| > xi_act }   snapshot before any push
+//   i in F_t:  x_i += (1-c) r_i,  r_i = 0,  w_i = c r_i / deg(i)
+//   j:         r_j += sum_{i in S(j) & F_t} w_i  (IFP2: non-dangling j only)
+//
+// Kernels and the state machine (ctl->mode names the pending action):
+//   k_activate    (mode ACT or PUSH): activation of round t = ctl->round from r:
+//                 R_t, |F_t|, edges, w_t (and the frontier bins + snapshot v
+//                 when an atomic-push delivery is expected); its last block
+//                 takes the stop decision and picks the delivery of round t.
+//   k_round_pull  (mode PULL): delivers round t-1 by gathering w_{t-1} along
+//                 every in-list (each row commits its own activation: the
+//                 same |r_j| > xi_act test on the same r_j), then takes round
+//                 t's activation decision for the same row -- one kernel per
+//                 round, deterministic.
+//   k_push        (mode PUSH): delivers round t-1 from the frontier bins:
+//                 x_i += (1-c) v_i, r_i -= v_i, and an atomic add of
+//                 c v_i/deg(i) along the out-list (IFP2: its non-dangling
+//                 prefix).  The subtraction is order-independent, so the
+//                 commit needs no separate pass; k_activate follows.
+// A round is [k_round_pull, k_push, k_activate]; kernels whose mode is not
+// pending return at once, and all of them return once ctl->done is set.
+//
+// Number formats.  GB300's FP64 pipe retires a warp instruction in about 64
+// cycles of one SM sub-partition, even when a single lane executes it, so
+// the state type T is one of
+//   double  -- IEEE FP64 (reference form, PR_FP64);
+//   float   -- FP32 state (PR_FP32);
+//   float2  -- double-float (hi, lo) pairs, value hi + lo, 48-bit significand,
+//              arithmetic on FP32 instructions only (PR_DF64).
+// The pushed mass is gathered as float (FP32) or double-float pairs, and the
+// residual-L1 and other sums run in double-float with a final FP64 sum.
+#pragma once
+
+#include <cmath>
+
+#include "pr_internal.cuh"
+
+namespace pr {
+
+enum { MODE_ACT = 0, MODE_PUSH = 1, MODE_PULL = 2 };
+
+struct Ctl {
+    // parameters (host-written per solve), in every format the kernels use
+    double c, one_minus_c, eps, xi, pull_edges, pu, inv_om;
+    float c_f, om_f, xi_f, pu_f, inv_om_f, pad5;
+    float2 c_df, om_df, xi_df, pu_df, inv_om_df;
+    int32_t algo, policy, max_rounds, p_dense;
+    int64_t scan_ref, scan_unref;  // in-list entries read by one pull round
+    int32_t trace_cap, pad0;
+    // evolving state (device-written)
+    int32_t round;         // next round to activate
+    int32_t cur;           // round awaiting delivery
+    int32_t done, status, mode, want_bins, unref_active, pad3;
+    uint32_t ticket, pad1;
+    uint32_t bin_cnt[2][3];
+    double R, D;
+    long long F, E;
+    long long pushes, edges_pushed, edges_scanned;
+    int32_t rounds_push, rounds_pull;
+    // power / finalize
+    double gamma, delta, zsum;
+    float gamma_f, pad4;
+    float2 gamma_df, zinv_df;
+    int32_t iter, pad2;
+};
+
+struct Partials {
+    double *a, *b, *c;   // [kMaxBlocks] each (double-float sums reuse the 8-byte slots)
+    long long *F, *E;    // [kMaxBlocks]
+    int *u;              // [kMaxBlocks]
+};
+
+struct Trace {
+    double *R;
+    long long *F, *E;
+    int8_t *mode;
+};
+
+// personalization in each format (dense) -- one of them is used by a kernel
+struct PVals {
+    const double *p64;
+    const float *p32;
+    const float2 *pdf;
+};
+
+// ------------------------------------------------------------ double-float
+// value = hi + lo with |lo| <= ulp(hi)/2 (Dekker 1971; Knuth TAOCP 4.2.2)
+__host__ __device__ __forceinline__ float2 df_from_d(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);  // exact error of the high product
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_abs(float2 a) { return a.x < 0.f ? df_neg(a) : a; }
+__device__ __forceinline__ bool df_gt(float2 a, float2 b) { return a.x > b.x || (a.x == b.x && a.y > b.y); }
+__device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
+
+// atomic a += v on a double-float pair (64-bit compare-and-swap loop)
+__device__ __forceinline__ void df_atomic_add(float2 *a, float2 v) {
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(a);
+    unsigned long long old = *p, assumed;
+    do {
+        assumed = old;
+        float2 cur;
+        memcpy(&cur, &assumed, 8);
+        const float2 nv = df_add(cur, v);
+        unsigned long long nb;
+        memcpy(&nb, &nv, 8);
+        old = atomicCAS(p, assumed, nb);
+    } while (old != assumed);
+}
+
+// ------------------------------------------------------------ gathered element types
+template <typename V> struct GT;
+template <> struct GT<double> {
+    using A = double;
+    static __device__ __forceinline__ A zero() { return 0.0; }
+    static __device__ __forceinline__ double vzero() { return 0.0; }
+    static __device__ __forceinline__ A add(A a, double v) { return a + v; }
+    static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
+};
+template <> struct GT<float> {
+    using A = float;
+    static __device__ __forceinline__ A zero() { return 0.f; }
+    static __device__ __forceinline__ float vzero() { return 0.f; }
+    static __device__ __forceinline__ A add(A a, float v) { return a + v; }
+    static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
+};
+template <> struct GT<float2> {
+    using A = float2;
+    static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ float2 vzero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ A add(A a, float2 v) { return df_add(a, v); }
+    static __device__ __forceinline__ A shfl_down(A a, int o, int w) {
+        return make_float2(__shfl_down_sync(0xffffffffu, a.x, o, w), __shfl_down_sync(0xffffffffu, a.y, o, w));
+    }
+};
+
+// ------------------------------------------------------------ state traits
+// R: the accumulator of sums (residual L1, Power deltas, normaliser)
+template <typename T> struct ST;
+template <> struct ST<double> {
+    using V = float2;  // pushed mass gathered as double-float pairs
+    using R = double;
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+    static __device__ __forceinline__ double absv(double a) { return fabs(a); }
+    static __device__ __forceinline__ bool gt(double a, double b) { return a > b; }
+    static __device__ __forceinline__ double c(const Ctl *k) { return k->c; }
+    static __device__ __forceinline__ double om(const Ctl *k) { return k->one_minus_c; }
+    static __device__ __forceinline__ double xi(const Ctl *k) { return k->xi; }
+    static __device__ __forceinline__ double gamma(const Ctl *k) { return k->gamma; }
+    static __device__ __forceinline__ double inv_om(const Ctl *k) { return k->inv_om; }
+    static __device__ __forceinline__ double p(const Ctl *k, const PVals &P, int j) {
+        return k->p_dense ? P.p64[j] : k->pu;
+    }
+    static __device__ __forceinline__ double invdeg(const DevGraph &G, int i) { return G.inv_deg64[i]; }
+    static __device__ __forceinline__ double from_acc(float2 a) { return df_to_d(a); }
+    static __device__ __forceinline__ float2 pack(double v) { return df_from_d(v); }
+    static __device__ __forceinline__ double to_d(double v) { return v; }
+    static __device__ __forceinline__ double pack_from_d(double v) { return v; }
+    static __device__ __forceinline__ R rval(double v) { return v; }
+    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R rzero() { return 0.0; }
+    static __device__ __forceinline__ R rshfl(R a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double r_to_d(R a) { return a; }
+    static __device__ __forceinline__ void atomic_add(double *a, double v) { atomicAdd(a, v); }
+};
+template <> struct ST<float> {
+    using V = float;
+    using R = float2;
+    static __device__ __forceinline__ float zero() { return 0.f; }
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+    static __device__ __forceinline__ float absv(float a) { return fabsf(a); }
+    static __device__ __forceinline__ bool gt(float a, float b) { return a > b; }
+    static __device__ __forceinline__ float c(const Ctl *k) { return k->c_f; }
+    static __device__ __forceinline__ float om(const Ctl *k) { return k->om_f; }
+    static __device__ __forceinline__ float xi(const Ctl *k) { return k->xi_f; }
+    static __device__ __forceinline__ float gamma(const Ctl *k) { return k->gamma_f; }
+    static __device__ __forceinline__ float inv_om(const Ctl *k) { return k->inv_om_f; }
+    static __device__ __forceinline__ float p(const Ctl *k, const PVals &P, int j) {
+        return k->p_dense ? P.p32[j] : k->pu_f;
+    }
+    static __device__ __forceinline__ float invdeg(const DevGraph &G, int i) { return G.inv_deg32[i]; }
+    static __device__ __forceinline__ float from_acc(float a) { return a; }
+    static __device__ __forceinline__ float pack(float v) { return v; }
+    static __device__ __forceinline__ double to_d(float v) { return (double)v; }
+    static __device__ __forceinline__ float pack_from_d(double v) { return (float)v; }
+    static __device__ __forceinline__ R rval(float v) { return make_float2(v, 0.f); }
+    static __device__ __forceinline__ R radd(R a, R b) { return df_add(a, b); }
+    static __device__ __forceinline__ R rzero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ R rshfl(R a, int o) { return GT<float2>::shfl_down(a, o, 32); }
+    static __device__ __forceinline__ double r_to_d(R a) { return df_to_d(a); }
+    static __device__ __forceinline__ void atomic_add(float *a, float v) { atomicAdd(a, v); }
+};
+template <> struct ST<float2> {
+    using V = float2;
+    using R = float2;
+    static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return df_add(a, b); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return df_mul(a, b); }
+    static __device__ __forceinline__ float2 neg(float2 a) { return df_neg(a); }
+    static __device__ __forceinline__ float2 absv(float2 a) { return df_abs(a); }
+    static __device__ __forceinline__ bool gt(float2 a, float2 b) { return df_gt(a, b); }
+    static __device__ __forceinline__ float2 c(const Ctl *k) { return k->c_df; }
+    static __device__ __forceinline__ float2 om(const Ctl *k) { return k->om_df; }
+    static __device__ __forceinline__ float2 xi(const Ctl *k) { return k->xi_df; }
+    static __device__ __forceinline__ float2 gamma(const Ctl *k) { return k->gamma_df; }
+    static __device__ __forceinline__ float2 inv_om(const Ctl *k) { return k->inv_om_df; }
+    static __device__ __forceinline__ float2 p(const Ctl *k, const PVals &P, int j) {
+        return k->p_dense ? P.pdf[j] : k->pu_df;
+    }
+    static __device__ __forceinline__ float2 invdeg(const DevGraph &G, int i) { return G.inv_degdf[i]; }
+    static __device__ __forceinline__ float2 from_acc(float2 a) { return a; }
+    static __device__ __forceinline__ float2 pack(float2 v) { return v; }
+    static __device__ __forceinline__ double to_d(float2 v) { return df_to_d(v); }
+    static __device__ __forceinline__ float2 pack_from_d(double v) { return df_from_d(v); }
+    static __device__ __forceinline__ R rval(float2 v) { return v; }
+    static __device__ __forceinline__ R radd(R a, R b) { return df_add(a, b); }
+    static __device__ __forceinline__ R rzero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ R rshfl(R a, int o) { return GT<float2>::shfl_down(a, o, 32); }
+    static __device__ __forceinline__ double r_to_d(R a) { return df_to_d(a); }
+    static __device__ __forceinline__ void atomic_add(float2 *a, float2 v) { df_atomic_add(a, v); }
+};
+
+// |v| > xi_act, evaluated identically wherever an activation is decided.
+// FP32: xi_f is the largest float <= xi, so the test equals (double)|v| > xi.
+template <typename T> __device__ __forceinline__ bool is_active(T v, const Ctl *ctl) {
+    return ST<T>::gt(ST<T>::absv(v), ST<T>::xi(ctl));
+}
+
+// ------------------------------------------------------------ reductions
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum (fixed tree: deterministic); result valid in thread 0
+template <typename V> __device__ __forceinline__ V block_sum(V v, V *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    V r = V(0);
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : V(0);
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// block-wide sum of an ST<T>::R accumulator
+template <typename T> __device__ __forceinline__ typename ST<T>::R block_sum_r(typename ST<T>::R v,
+                                                                             typename ST<T>::R *sh) {
+    using R = typename ST<T>::R;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = ST<T>::radd(v, ST<T>::rshfl(v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    R r = ST<T>::rzero();
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : ST<T>::rzero();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = ST<T>::radd(r, ST<T>::rshfl(r, o));
+    }
+    return r;
+}
+
+// block-wide sum of a gathered accumulator
+template <typename V> __device__ __forceinline__ typename GT<V>::A block_sum_gt(typename GT<V>::A v,
+                                                                              typename GT<V>::A *sh) {
+    using A = typename GT<V>::A;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = GT<V>::add(v, GT<V>::shfl_down(v, o, 32));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    A r = GT<V>::zero();
+    if (wid == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : GT<V>::zero();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = GT<V>::add(r, GT<V>::shfl_down(r, o, 32));
+    }
+    return r;
+}
+
+// last-block election: every block calls with its partials already stored
+__device__ __forceinline__ bool last_block(uint32_t *ticket) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// the last block's FP64 sum of the blocks' R partials (stored in 8-byte slots)
+template <typename T> __device__ __forceinline__ double final_sum(const double *slots, double *shd) {
+    using R = typename ST<T>::R;
+    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(slots);
+    double s = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        R v;
+        const unsigned long long bits = __ldcg(p + k);
+        memcpy(&v, &bits, 8);
+        s += ST<T>::r_to_d(v);
+    }
+    return block_sum(s, shd);
+}
+
+template <typename T> __device__ __forceinline__ void store_partial(double *slots, typename ST<T>::R v) {
+    memcpy(reinterpret_cast<char *>(slots) + 8 * (size_t)blockIdx.x, &v, 8);
+}
+
+// sum of val[src[e]] over e in [off[j] + start, off[j+1]) stepping by `step`;
+// in-list entries are streamed once (evict-first), gathered values go through
+// the read-only path (not written during the kernel)
+template <typename V>
+__device__ __forceinline__ typename GT<V>::A row_sum(const int32_t *__restrict__ off,
+                                                     const int32_t *__restrict__ src, int j,
+                                                     const V *__restrict__ val, int start, int step) {
+    using A = typename GT<V>::A;
+    const int a = __ldg(&off[j]), b = __ldg(&off[j + 1]);
+    A acc0 = GT<V>::zero(), acc1 = GT<V>::zero();
+    int e = a + start;
+    for (; e + step < b; e += 2 * step) {
+        const int s0 = __ldcs(&src[e]), s1 = __ldcs(&src[e + step]);
+        acc0 = GT<V>::add(acc0, __ldg(&val[s0]));
+        acc1 = GT<V>::add(acc1, __ldg(&val[s1]));
+    }
+    if (e < b) acc0 = GT<V>::add(acc0, __ldg(&val[__ldcs(&src[e])]));
+    return GT<V>::add(acc0, acc1);
+}
+
+// The sums of ROWS rows at once (rows js[r], valid[r]), interleaved so that the
+// in-list entry loads and then the gathers of all rows are in flight together.
+template <typename V, int ROWS>
+__device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
+                                         const int *js, const bool *valid, const V *__restrict__ val, int start,
+                                         int step, typename GT<V>::A *acc) {
+    int e[ROWS], b[ROWS];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        acc[r] = GT<V>::zero();
+        e[r] = 0;
+        b[r] = 0;
+        if (valid[r]) {
+            e[r] = __ldg(&off[js[r]]) + start;
+            b[r] = __ldg(&off[js[r] + 1]);
+        }
+        any |= e[r] < b[r];
+    }
+    while (any) {
+        int idx[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) idx[r] = e[r] < b[r] ? __ldcs(&src[e[r]]) : -1;
+        any = false;
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            if (idx[r] >= 0) {
+                acc[r] = GT<V>::add(acc[r], __ldg(&val[idx[r]]));
+                e[r] += step;
+            }
+            any |= e[r] < b[r];
+        }
+    }
+}
+
+// rows in flight per lane group: short rows (few lanes) interleave more of them
+template <int LANES> struct RowsInFlight {
+    static constexpr int value = LANES <= 2 ? 4 : (LANES <= 16 ? 2 : 1);
+};
+
+// ------------------------------------------------------------ round decision
+// Executed by thread 0 of the last block of an activation (round t).
+__device__ __forceinline__ void round_decision(Ctl *ctl, int t, double R, long long F, long long E, int u,
+                                               int want, const Trace &tr) {
+    ctl->ticket = 0;
+    ctl->R = R;
+    ctl->F = F;
+    ctl->E = E;
+    if (t < ctl->trace_cap) tr.R[t] = R;
+    uint32_t *nxt = ((t + 1) & 1) ? ctl->bin_cnt[1] : ctl->bin_cnt[0];
+    nxt[0] = nxt[1] = nxt[2] = 0;
+    if (R <= ctl->eps) {
+        ctl->done = 1;
+        ctl->status = 0;
+        return;
+    }
+    if (t >= ctl->max_rounds) {
+        ctl->done = 1;
+        ctl->status = 1;
+        return;
+    }
+    if (F == 0) {
+        ctl->done = 1;
+        ctl->status = 2;
+        return;
+    }
+    int mode;
+    if (ctl->policy == MODE_PUSH) mode = MODE_PUSH;
+    else if (ctl->policy == MODE_PULL) mode = MODE_PULL;
+    else mode = (want && (double)E < ctl->pull_edges) ? MODE_PUSH : MODE_PULL;
+    ctl->mode = mode;
+    ctl->cur = t;
+    ctl->round = t + 1;
+    ctl->unref_active = u;
+    ctl->pushes += F;
+    ctl->edges_pushed += E;
+    if (mode == MODE_PULL) {
+        ctl->edges_scanned += ctl->scan_ref + (u ? ctl->scan_unref : 0);
+        ctl->rounds_pull++;
+    } else {
+        ctl->edges_scanned += E;
+        ctl->rounds_push++;
+    }
+    if (t < ctl->trace_cap) {
+        tr.F[t] = F;
+        tr.E[t] = E;
+        tr.mode[t] = (int8_t)mode;
+    }
+    if (ctl->policy == 0) ctl->want_bins = (double)E < 2.0 * ctl->pull_edges;
+}
+
+struct RoundBuf {
+    void *x, *r, *vbuf;  // T arrays
+    void *w[2];          // ST<T>::V arrays; w[t & 1] written by the activation of round t
+    int32_t *bins;
+};
+
+// activation of one non-dangling vertex i with residual v (round t):
+// pending push w_t[i], snapshot v for a push delivery, frontier counters
+template <typename T, bool IFP2>
+__device__ __forceinline__ bool activate_one(const DevGraph &G, const Ctl *ctl, int i, T v, int want,
+                                             typename ST<T>::V *w, T *vbuf, int &pd, long long &F, long long &E,
+                                             int &u) {
+    const bool act = is_active(v, ctl);
+    pd = IFP2 ? G.ndeg[i] : (G.out_off[i + 1] - G.out_off[i]);
+    w[i] = ST<T>::pack(act ? ST<T>::mul(v, ST<T>::mul(ST<T>::c(ctl), ST<T>::invdeg(G, i))) : ST<T>::zero());
+    if (act) {
+        F++;
+        E += pd;
+        u |= (i >= G.n_ref);
+        if (want) vbuf[i] = v;
+    }
+    return act;
+}
+
+// warp-aggregated append of active vertices into the three out-degree bins
+__device__ __forceinline__ void bins_append(bool act, int pd, int i, uint32_t *bcnt, int32_t *bins, int n_nd) {
+    const int lane = threadIdx.x & 31;
+    const int bin = pd <= kWarpRowMin ? 0 : (pd <= kCtaRowMin ? 1 : 2);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const unsigned mask = __ballot_sync(0xffffffffu, act && bin == b);
+        if (!mask) continue;
+        unsigned pos0 = 0;
+        const int leader = __ffs(mask) - 1;
+        if (lane == leader) pos0 = atomicAdd(&bcnt[b], (unsigned)__popc(mask));
+        pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+        if (act && bin == b) bins[(size_t)b * n_nd + pos0 + __popc(mask & ((1u << lane) - 1u))] = i;
+    }
+}
+
+// ------------------------------------------------------------ k_push
+template <typename T>
+__device__ __forceinline__ void push_commit(const Ctl *ctl, T *x, T *r, int i, T v) {
+    x[i] = ST<T>::add(x[i], ST<T>::mul(ST<T>::om(ctl), v));
+    ST<T>::atomic_add(&r[i], ST<T>::neg(v));
+}
+
+template <typename T, bool IFP2>
+__global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, RoundBuf B, int nb_thread,
+                                                  int nb_warp) {
+    if (ctl->done || ctl->mode != MODE_PUSH) return;
+    const uint32_t *cnt = (ctl->cur & 1) ? ctl->bin_cnt[1] : ctl->bin_cnt[0];
+    const int n_nd = G.n_nd;
+    T *x = static_cast<T *>(B.x);
+    T *r = static_cast<T *>(B.r);
+    const T *vbuf = static_cast<const T *>(B.vbuf);
+    const int32_t *bins = B.bins;
+    const T cT = ST<T>::c(ctl);
+    const int b = blockIdx.x;
+    if (b < nb_thread) {
+        const uint32_t c0 = cnt[0];
+        for (uint32_t k = b * blockDim.x + threadIdx.x; k < c0; k += nb_thread * blockDim.x) {
+            const int i = bins[k];
+            const T v = vbuf[i];
+            push_commit<T>(ctl, x, r, i, v);
+            const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
+            const int e0 = G.out_off[i];
+            const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
+            for (int e = e0; e < e1; e++) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+        }
+    } else if (b < nb_thread + nb_warp) {
+        const uint32_t c1 = cnt[1];
+        const int lane = threadIdx.x & 31;
+        const int wpb = blockDim.x >> 5;
+        for (uint32_t k = (b - nb_thread) * wpb + (threadIdx.x >> 5); k < c1; k += nb_warp * wpb) {
+            const int i = bins[(size_t)n_nd + k];
+            const T v = vbuf[i];
+            if (lane == 0) push_commit<T>(ctl, x, r, i, v);
+            const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
+            const int e0 = G.out_off[i];
+            const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
+            for (int e = e0 + lane; e < e1; e += 32) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+        }
+    } else {
+        const uint32_t c2 = cnt[2];
+        const int nb_cta = gridDim.x - nb_thread - nb_warp;
+        for (uint32_t k = b - nb_thread - nb_warp; k < c2; k += nb_cta) {
+            const int i = bins[(size_t)2 * n_nd + k];
+            const T v = vbuf[i];
+            if (threadIdx.x == 0) push_commit<T>(ctl, x, r, i, v);
+            const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
+            const int e0 = G.out_off[i];
+            const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
+            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+        }
+    }
+}
+
+// ------------------------------------------------------------ k_round_pull
+// commit + update + next activation of row j (run by one lane per row)
+template <typename T, bool IFP2>
+__device__ __forceinline__ bool pull_row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                                  typename ST<T>::V *wnext, int j, T in, int want, int &pd,
+                                                  typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    T *x = static_cast<T *>(B.x);
+    T *r = static_cast<T *>(B.r);
+    if (j >= G.n_nd) {  // dangling vertex (IFP1): receives, never pushes
+        r[j] = ST<T>::add(r[j], in);
+        return false;
+    }
+    const T v = r[j];
+    T base_v = v;
+    if (is_active(v, ctl)) {  // commit of round t-1 (decided on this same r_j)
+        x[j] = ST<T>::add(x[j], ST<T>::mul(ST<T>::om(ctl), v));
+        base_v = ST<T>::zero();
+    }
+    const T rn = ST<T>::add(base_v, in);
+    r[j] = rn;
+    Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(rn)));
+    return activate_one<T, IFP2>(G, ctl, j, rn, want, wnext, static_cast<T *>(B.vbuf), pd, Fl, El, ul);
+}
+
+// Rows of a plan segment handled by groups of LANES threads, ROWS rows per
+// group at a time; the loop bound is uniform across the block so the
+// width-LANES shuffles always see full warps.
+template <typename T, bool IFP2, int LANES>
+__device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                           const RoundBuf &B, const typename ST<T>::V *wprev,
+                                           typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
+                                           typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    constexpr int GPB = kThreads / LANES;
+    constexpr int ROWS = RowsInFlight<LANES>::value;
+    const int grp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    const int stride = S.nblk * GPB;
+    for (int base = S.lo + lb * GPB; base < S.hi; base += ROWS * stride) {
+        int js[ROWS];
+        bool valid[ROWS];
+        A acc[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            js[r] = base + r * stride + grp;
+            valid[r] = js[r] < S.hi;
+        }
+        row_sums<V, ROWS>(G.inr_off, G.inr_src, js, valid, wprev, lane, LANES, acc);
+        if (use_unref) {
+            A extra[ROWS];
+            row_sums<V, ROWS>(G.inu_off, G.inu_src, js, valid, wprev, lane, LANES, extra);
+#pragma unroll
+            for (int r = 0; r < ROWS; r++) acc[r] = GT<V>::add(acc[r], extra[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+#pragma unroll
+            for (int o = LANES / 2; o > 0; o >>= 1) acc[r] = GT<V>::add(acc[r], GT<V>::shfl_down(acc[r], o, LANES));
+            bool act = false;
+            int pd = 0;
+            if (valid[r] && lane == 0)
+                act = pull_row_epilogue<T, IFP2>(G, ctl, B, wnext, js[r], ST<T>::from_acc(acc[r]), want, pd, Rl,
+                                                 Fl, El, ul);
+            if (want) bins_append(act, pd, js[r], bcnt, B.bins, G.n_nd);
+        }
+    }
+}
+
+// One segment (or tile) of a pull round: rows [S.lo, S.hi) with S.lanes threads per
+// row (0: the whole block per row); block lb of S.nblk.
+template <typename T, bool IFP2>
+__device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                              const RoundBuf &B, const typename ST<T>::V *wprev,
+                                              typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
+                                              typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul,
+                                              typename GT<typename ST<T>::V>::A *sha) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    switch (S.lanes) {
+        case 1: round_rows<T, IFP2, 1>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 2: round_rows<T, IFP2, 2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 4: round_rows<T, IFP2, 4>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 8: round_rows<T, IFP2, 8>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 16: round_rows<T, IFP2, 16>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 32: round_rows<T, IFP2, 32>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        default:  // one block per row
+            for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
+                A acc = row_sum<V>(G.inr_off, G.inr_src, j, wprev, threadIdx.x, blockDim.x);
+                if (use_unref)
+                    acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, wprev, threadIdx.x, blockDim.x));
+                acc = block_sum_gt<V>(acc, sha);
+                if (threadIdx.x == 0) {
+                    int pd = 0;
+                    const bool act = pull_row_epilogue<T, IFP2>(G, ctl, B, wnext, j, ST<T>::from_acc(acc), want,
+                                                                pd, Rl, Fl, El, ul);
+                    if (want && act) {
+                        const int bin = pd <= kWarpRowMin ? 0 : (pd <= kCtaRowMin ? 1 : 2);
+                        const unsigned pos = atomicAdd(&bcnt[bin], 1u);
+                        B.bins[(size_t)bin * G.n_nd + pos] = j;
+                    }
+                }
+            }
+    }
+}
+
+// Activation of rows [lo, hi) (non-dangling ids), stepping by `step` from
+// lo + first: the trip count is uniform across each warp.
+template <typename T, bool IFP2>
+__device__ __forceinline__ void activate_range(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                               typename ST<T>::V *w, int lo, int hi, int first, int step, int want,
+                                               uint32_t *bcnt, typename ST<T>::R &Rl, long long &Fl, long long &El,
+                                               int &ul) {
+    const T *r = static_cast<const T *>(B.r);
+    T *vbuf = static_cast<T *>(B.vbuf);
+    for (int base = lo + first; base < hi; base += step) {
+        const int i = base + (int)threadIdx.x;
+        bool act = false;
+        int pd = 0;
+        if (i < hi) {
+            const T v = r[i];
+            Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(v)));
+            act = activate_one<T, IFP2>(G, ctl, i, v, want, w, vbuf, pd, Fl, El, ul);
+        }
+        if (want) bins_append(act, pd, i, bcnt, B.bins, G.n_nd);
+    }
+}
+
+// ------------------------------------------------------------ k_activate
+template <typename T, bool IFP2>
+__global__ void __launch_bounds__(kThreads) k_activate(DevGraph G, Ctl *ctl, Partials P, RoundBuf B, Trace tr) {
+    using R = typename ST<T>::R;
+    using V = typename ST<T>::V;
+    if (ctl->done || ctl->mode == MODE_PULL) return;
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    __shared__ R shr[32];
+    const int want = ctl->want_bins;
+    const int t = ctl->round;
+    uint32_t *bcnt = (t & 1) ? ctl->bin_cnt[1] : ctl->bin_cnt[0];
+    V *w = static_cast<V *>((t & 1) ? B.w[1] : B.w[0]);
+    const int n_nd = G.n_nd;
+    R Rl = ST<T>::rzero();
+    long long Fl = 0, El = 0;
+    int ul = 0;
+    activate_range<T, IFP2>(G, ctl, B, w, 0, n_nd, blockIdx.x * blockDim.x, gridDim.x * blockDim.x, want, bcnt, Rl,
+                            Fl, El, ul);
+    const R Rb = block_sum_r<T>(Rl, shr);
+    const long long Fb = block_sum(Fl, shl);
+    const long long Eb = block_sum(El, shl);
+    const int ub = __syncthreads_or(ul);
+    if (threadIdx.x == 0) {
+        store_partial<T>(P.a, Rb);
+        P.F[blockIdx.x] = Fb;
+        P.E[blockIdx.x] = Eb;
+        P.u[blockIdx.x] = ub;
+    }
+    if (!last_block(&ctl->ticket)) return;
+    const double Rsum = final_sum<T>(P.a, shd);
+    long long F = 0, E = 0;
+    int u = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        F += __ldcg(&P.F[k]);
+        E += __ldcg(&P.E[k]);
+        u |= __ldcg(&P.u[k]);
+    }
+    F = block_sum(F, shl);
+    E = block_sum(E, shl);
+    u = __syncthreads_or(u);
+    if (threadIdx.x == 0) round_decision(ctl, t, Rsum, F, E, u, want, tr);
+}
+
+template <typename T, bool IFP2>
+__global__ void __launch_bounds__(kThreads) k_round_pull(DevGraph G, Plan PL, Ctl *ctl, Partials P, RoundBuf B,
+                                                        Trace tr) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    using R = typename ST<T>::R;
+    if (ctl->done || ctl->mode != MODE_PULL) return;
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    __shared__ A sha[32];
+    __shared__ R shr[32];
+    const int t = ctl->round;  // activation of round t; delivery of round t - 1
+    const int want = ctl->want_bins;
+    const bool use_unref = ctl->unref_active != 0;
+    uint32_t *bcnt = (t & 1) ? ctl->bin_cnt[1] : ctl->bin_cnt[0];
+    const V *wprev = static_cast<const V *>((t & 1) ? B.w[0] : B.w[1]);  // written by round t - 1
+    V *wnext = static_cast<V *>((t & 1) ? B.w[1] : B.w[0]);
+    int s = 0;
+    while (s + 1 < PL.nseg && (int)blockIdx.x >= PL.seg[s + 1].blk0) s++;
+    const Seg S = PL.seg[s];
+    const int lb = blockIdx.x - S.blk0;
+    R Rl = ST<T>::rzero();
+    long long Fl = 0, El = 0;
+    int ul = 0;
+    round_segment<T, IFP2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul, sha);
+    const R Rb = block_sum_r<T>(Rl, shr);
+    const long long Fb = block_sum(Fl, shl);
+    const long long Eb = block_sum(El, shl);
+    const int ub = __syncthreads_or(ul);
+    if (threadIdx.x == 0) {
+        store_partial<T>(P.a, Rb);
+        P.F[blockIdx.x] = Fb;
+        P.E[blockIdx.x] = Eb;
+        P.u[blockIdx.x] = ub;
+    }
+    if (!last_block(&ctl->ticket)) return;
+    const double Rsum = final_sum<T>(P.a, shd);
+    long long F = 0, E = 0;
+    int u = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        F += __ldcg(&P.F[k]);
+        E += __ldcg(&P.E[k]);
+        u |= __ldcg(&P.u[k]);
+    }
+    F = block_sum(F, shl);
+    E = block_sum(E, shl);
+    u = __syncthreads_or(u);
+    if (threadIdx.x == 0) round_decision(ctl, t, Rsum, F, E, u, want, tr);
+}
+
+// ------------------------------------------------------------ sweeps: Power, correction, phase 2
+enum { OP_POWER = 1, OP_CORRECT = 2, OP_PHASE2 = 3 };
+
+template <typename T> struct SweepArgs {
+    const typename ST<T>::V *val;  // gathered per source
+    T *r;                          // CORRECT / PHASE2 output residual
+    const T *x;                    // CORRECT reads the reserve
+    const T *pi_cur;               // POWER
+    T *pi_next;                    // POWER
+    typename ST<T>::V *q_next;     // POWER
+    PVals pv;
+    Partials P;
+    Trace tr;
+};
+
+template <typename T, int OP>
+__device__ __forceinline__ void sweep_epilogue(const DevGraph &G, const Ctl *ctl, SweepArgs<T> &a, int j, T in,
+                                               typename ST<T>::R &s1, typename ST<T>::R &s2,
+                                               typename ST<T>::R &s3) {
+    if constexpr (OP == OP_POWER) {
+        // pi_{k+1} = c P pi_k + gamma_k p, gamma_k = c d^T pi_k + (1-c) e^T pi_k  (Eq. 1)
+        const T y = ST<T>::add(ST<T>::mul(ST<T>::c(ctl), in), ST<T>::mul(ST<T>::gamma(ctl), ST<T>::p(ctl, a.pv, j)));
+        const T old = a.pi_cur[j];
+        s1 = ST<T>::radd(s1, ST<T>::rval(ST<T>::absv(ST<T>::add(y, ST<T>::neg(old)))));
+        if (j >= G.n_nd) s2 = ST<T>::radd(s2, ST<T>::rval(y));
+        s3 = ST<T>::radd(s3, ST<T>::rval(y));
+        a.pi_next[j] = y;
+        if (j < G.n_nd) a.q_next[j] = ST<T>::pack(ST<T>::mul(y, ST<T>::invdeg(G, j)));
+    } else if constexpr (OP == OP_CORRECT) {
+        // r = p + c P~ s - s with s = x / (1-c): the exact residual of the current reserve, in FP64
+        const double s = ST<T>::to_d(a.x[j]) / ctl->one_minus_c;
+        const double pj = ctl->p_dense ? a.pv.p64[j] : ctl->pu;
+        a.r[j] = (T)(pj + ctl->c * ST<T>::to_d(in) - s);
+    } else {  // OP_PHASE2: r_d = p_d + c sum_{u in S(d)} x_u / ((1-c) deg(u)); phase 1 never
+              // touches a dangling residual, so r_d still holds p_d
+        a.r[j] = ST<T>::add(a.r[j], ST<T>::mul(ST<T>::c(ctl), in));
+    }
+}
+
+template <typename T, int OP, int LANES>
+__device__ __forceinline__ void sweep_rows(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl, SweepArgs<T> &a,
+                                           typename ST<T>::R &s1, typename ST<T>::R &s2, typename ST<T>::R &s3) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    constexpr int GPB = kThreads / LANES;
+    constexpr int ROWS = RowsInFlight<LANES>::value;
+    const int grp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    const int stride = S.nblk * GPB;
+    for (int base = S.lo + lb * GPB; base < S.hi; base += ROWS * stride) {
+        int js[ROWS];
+        bool valid[ROWS];
+        A acc[ROWS], extra[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            js[r] = base + r * stride + grp;
+            valid[r] = js[r] < S.hi;
+        }
+        row_sums<V, ROWS>(G.inr_off, G.inr_src, js, valid, a.val, lane, LANES, acc);
+        row_sums<V, ROWS>(G.inu_off, G.inu_src, js, valid, a.val, lane, LANES, extra);
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            acc[r] = GT<V>::add(acc[r], extra[r]);
+#pragma unroll
+            for (int o = LANES / 2; o > 0; o >>= 1) acc[r] = GT<V>::add(acc[r], GT<V>::shfl_down(acc[r], o, LANES));
+            if (valid[r] && lane == 0) sweep_epilogue<T, OP>(G, ctl, a, js[r], ST<T>::from_acc(acc[r]), s1, s2, s3);
+        }
+    }
+}
+
+// One segment (or tile) of a sweep: rows [S.lo, S.hi), S.lanes threads per row.
+template <typename T, int OP>
+__device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                              SweepArgs<T> &a, typename ST<T>::R &s1, typename ST<T>::R &s2,
+                                              typename ST<T>::R &s3, typename GT<typename ST<T>::V>::A *sha) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    switch (S.lanes) {
+        case 1: sweep_rows<T, OP, 1>(G, S, lb, ctl, a, s1, s2, s3); break;
+        case 2: sweep_rows<T, OP, 2>(G, S, lb, ctl, a, s1, s2, s3); break;
+        case 4: sweep_rows<T, OP, 4>(G, S, lb, ctl, a, s1, s2, s3); break;
+        case 8: sweep_rows<T, OP, 8>(G, S, lb, ctl, a, s1, s2, s3); break;
+        case 16: sweep_rows<T, OP, 16>(G, S, lb, ctl, a, s1, s2, s3); break;
+        case 32: sweep_rows<T, OP, 32>(G, S, lb, ctl, a, s1, s2, s3); break;
+        default:
+            for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
+                A acc = row_sum<V>(G.inr_off, G.inr_src, j, a.val, threadIdx.x, blockDim.x);
+                acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, a.val, threadIdx.x, blockDim.x));
+                acc = block_sum_gt<V>(acc, sha);
+                if (threadIdx.x == 0) sweep_epilogue<T, OP>(G, ctl, a, j, ST<T>::from_acc(acc), s1, s2, s3);
+            }
+    }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) k_sweep(DevGraph G, Plan PL, Ctl *ctl, SweepArgs<T> a) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    using R = typename ST<T>::R;
+    if (OP == OP_POWER && ctl->done) return;  // the one-shot sweeps run after the stop flag is set
+    int s = 0;
+    while (s + 1 < PL.nseg && (int)blockIdx.x >= PL.seg[s + 1].blk0) s++;
+    const Seg S = PL.seg[s];
+    const int lb = blockIdx.x - S.blk0;
+    R s1 = ST<T>::rzero(), s2 = ST<T>::rzero(), s3 = ST<T>::rzero();
+    __shared__ double shd[32];
+    __shared__ A sha[32];
+    __shared__ R shr[32];
+    sweep_segment<T, OP>(G, S, lb, ctl, a, s1, s2, s3, sha);
+    if (OP != OP_POWER) return;
+    // Power: ||pi_{k+1} - pi_k||_1, d^T pi_{k+1}, e^T pi_{k+1}
+    const R b1 = block_sum_r<T>(s1, shr);
+    const R b2 = block_sum_r<T>(s2, shr);
+    const R b3 = block_sum_r<T>(s3, shr);
+    if (threadIdx.x == 0) {
+        store_partial<T>(a.P.a, b1);
+        store_partial<T>(a.P.b, b2);
+        store_partial<T>(a.P.c, b3);
+    }
+    if (!last_block(&ctl->ticket)) return;
+    const double d = final_sum<T>(a.P.a, shd);
+    const double dm = final_sum<T>(a.P.b, shd);
+    const double tm = final_sum<T>(a.P.c, shd);
+    if (threadIdx.x != 0) return;
+    ctl->ticket = 0;
+    const int it = ctl->iter + 1;
+    ctl->iter = it;
+    ctl->delta = d;
+    ctl->zsum = tm;
+    const double gamma = ctl->c * dm + ctl->one_minus_c * tm;
+    ctl->gamma = gamma;
+    ctl->gamma_f = (float)gamma;
+    ctl->gamma_df = df_from_d(gamma);
+    if (it < ctl->trace_cap) a.tr.R[it] = d;
+    if (d <= ctl->eps) {
+        ctl->done = 1;
+        ctl->status = 0;
+    } else if (it >= ctl->max_rounds) {
+        ctl->done = 1;
+        ctl->status = 1;
+    }
+}
+
+// IFP1: z = x + (1-c) r (Alg. 2 pibar + h);  IFP2: z = x (non-dangling), (1-c) r (dangling)
+// (Alg. 3 pibar);  POWER: z = pi.  pi = z / sum z, scattered back to caller ids.
+template <typename T>
+__device__ __forceinline__ T zval(const DevGraph &G, const Ctl *ctl, int kind, const T *x, const T *r, int i) {
+    if (kind == PR_IFP1) return ST<T>::add(x[i], ST<T>::mul(ST<T>::om(ctl), r[i]));
+    if (kind == PR_IFP2) return i < G.n_nd ? x[i] : ST<T>::mul(ST<T>::om(ctl), r[i]);
+    return x[i];
+}
+
+
+// host-side conversions of the scalar parameters
+inline float float_at_most(double v) {  // largest float <= v
+    float f = (float)v;
+    if ((double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+inline void fill_formats(Ctl &h) {
+    h.inv_om = 1.0 / h.one_minus_c;
+    h.c_f = (float)h.c;
+    h.om_f = (float)h.one_minus_c;
+    h.xi_f = float_at_most(h.xi);
+    h.pu_f = (float)h.pu;
+    h.inv_om_f = (float)h.inv_om;
+    h.c_df = df_from_d(h.c);
+    h.om_df = df_from_d(h.one_minus_c);
+    h.xi_df = df_from_d(h.xi);
+    h.pu_df = df_from_d(h.pu);
+    h.inv_om_df = df_from_d(h.inv_om);
+}
+
+}  // namespace pr

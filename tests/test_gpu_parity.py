@@ -68,7 +68,7 @@ def closed_forms():
 
 @pytest.mark.parametrize("case", closed_forms(), ids=lambda c: c[0])
 @pytest.mark.parametrize("algo", ALGOS)
-@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_FP32))
+@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_FP32, pr.PR_DF64))
 @pytest.mark.parametrize("mode", MODES)
 def test_closed_forms(case, algo, prec, mode):
     name, g, p, truth = case
@@ -76,10 +76,10 @@ def test_closed_forms(case, algo, prec, mode):
         fp32_power = algo == pr.PR_POWER and prec == pr.PR_FP32
         # FP32 Power: ||delta||_1 has an FP32 rounding floor near 1e-7, and its
         # certified error is c * delta / (1 - c)
-        eps = 1e-13 if algo != pr.PR_POWER else (1e-14 if prec == pr.PR_FP64 else 1e-6)
+        eps = 1e-13 if algo != pr.PR_POWER else {pr.PR_FP64: 1e-14, pr.PR_DF64: 1e-13, pr.PR_FP32: 1e-6}[prec]
         out, st, status = G.solve(C, eps, algo, prec, p=p, opts=dict(mode=mode))
         assert status == pr.PR_OK, st
-        tol = 1e-12 if prec == pr.PR_FP64 else (C * eps / (1 - C) + 1e-6 if fp32_power else 2e-7)
+        tol = 1e-12 if prec != pr.PR_FP32 else (C * eps / (1 - C) + 1e-6 if fp32_power else 2e-7)
         assert l1(out, truth) <= tol, (name, l1(out, truth), st)
         assert abs(out.sum() - 1.0) < 1e-12
 
@@ -132,7 +132,8 @@ ROUND_GRAPHS = [
 @pytest.mark.parametrize("gcase", ROUND_GRAPHS, ids=lambda c: c[0])
 @pytest.mark.parametrize("algo", (IFP1, IFP2))
 @pytest.mark.parametrize("mode", MODES)
-def test_rounds_match_oracle_exactly(gcase, algo, mode):
+@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_DF64))
+def test_rounds_match_oracle_exactly(gcase, algo, mode, prec):
     g = gcase[1]()
     p = gg.p_uniform(g.n)
     eps = 1e-10
@@ -141,7 +142,8 @@ def test_rounds_match_oracle_exactly(gcase, algo, mode):
     # the stop decision compares R_t with eps: keep away from exact ties
     assert np.all(np.abs(ref["R"] / eps - 1) > 1e-6)
     with gpu_graph(g) as G:
-        out, st, status = G.solve(C, eps, algo, opts=dict(xi_act=1e-300, mode=mode, trace_cap=ref["rounds"] + 5))
+        out, st, status = G.solve(C, eps, algo, prec,
+                                  opts=dict(xi_act=1e-300, mode=mode, trace_cap=ref["rounds"] + 5))
         assert status == pr.PR_OK
         k = ref["rounds"]
         assert st["rounds"] == k
@@ -168,10 +170,11 @@ def test_rmat_scale14_all_algorithms(seed):
     truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
     with gpu_graph(g) as G:
         for algo in ALGOS:
-            out, st, status = G.solve(C, 1e-10, algo, pr.PR_FP64)
-            err = l1(out, truth)
-            assert status == pr.PR_OK and err <= 1e-9, (algo, err)
-            assert err <= st["err_bound"] + 1e-13
+            for prec in (pr.PR_FP64, pr.PR_DF64):
+                out, st, status = G.solve(C, 1e-10, algo, prec)
+                err = l1(out, truth)
+                assert status == pr.PR_OK and err <= 1e-9, (algo, prec, err)
+                assert err <= st["err_bound"] + 1e-13
         for algo in (pr.PR_IFP1, pr.PR_IFP2):
             out, st, status = G.solve(C, 1e-7, algo, pr.PR_FP32)
             err = l1(out, truth)
@@ -192,16 +195,17 @@ def test_ifp1_ifp2_agree_and_ifp2_pushes_less():
 # ------------------------------------------------------------ personalization
 @pytest.mark.parametrize("k", (1, 5, 64))
 @pytest.mark.parametrize("algo", ALGOS)
-def test_ppr_sparse_seeds(k, algo):
+@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_DF64))
+def test_ppr_sparse_seeds(k, algo, prec):
     g = gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=5)
     idx, val = gg.p_seeds(g.n, k, seed=k)
     p = gg.dense_from_sparse(g.n, idx, val)
     truth = oracle.power(g, C, p, tol=1e-15)[0]
     with gpu_graph(g) as G:
-        out, st, status = G.solve(C, 1e-11, algo, p=val, p_idx=idx)
+        out, st, status = G.solve(C, 1e-11, algo, prec, p=val, p_idx=idx)
         assert status == pr.PR_OK and l1(out, truth) <= 1e-9
         # device-resident sparse p
-        out2, st2, _ = G.solve(C, 1e-11, algo, p=torch.tensor(val, device="cuda"),
+        out2, st2, _ = G.solve(C, 1e-11, algo, prec, p=torch.tensor(val, device="cuda"),
                                p_idx=torch.tensor(idx, device="cuda"), p_is_device=True)
         assert l1(out2, truth) <= 1e-9
 
@@ -212,9 +216,12 @@ def test_ppr_dense_unnormalised_p():
     truth = oracle.power(g, C, p / p.sum(), tol=1e-15)[0]
     with gpu_graph(g) as G:
         for algo in ALGOS:
-            out, st, status = G.solve(C, 1e-11, algo, p=p)
-            assert status == pr.PR_OK and l1(out, truth) <= 1e-9
-            assert abs(st["p_scale"] - 1.0 / p.sum()) < 1e-15
+            for prec in (pr.PR_FP64, pr.PR_DF64):
+                out, st, status = G.solve(C, 1e-11, algo, prec, p=p)
+                assert status == pr.PR_OK and l1(out, truth) <= 1e-9
+                assert abs(st["p_scale"] - 1.0 / p.sum()) < 1e-15
+            out, st, status = G.solve(C, 1e-7 if algo != pr.PR_POWER else 1e-6, algo, pr.PR_FP32, p=p)
+            assert status == pr.PR_OK and l1(out, truth) <= 1e-5
 
 
 # ------------------------------------------------------------ ABI behaviour
@@ -291,13 +298,15 @@ def test_round_cap_reports_not_converged():
         assert status == pr.PR_ENOTCONV and st["rounds"] == 0
 
 
-def test_pull_is_deterministic_and_graph_matches_host_loop():
+@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_FP32, pr.PR_DF64))
+def test_pull_is_deterministic_and_graph_matches_host_loop(prec):
     g = gg.rmat(13, 8, dangling=0.15, unref=0.1, seed=8)
     with gpu_graph(g) as G:
         for algo in ALGOS:
-            a = G.solve(C, 1e-11, algo, opts=dict(mode=pr.PR_MODE_PULL))[0]
-            b = G.solve(C, 1e-11, algo, opts=dict(mode=pr.PR_MODE_PULL))[0]
-            c = G.solve(C, 1e-11, algo, opts=dict(mode=pr.PR_MODE_PULL, use_graph=-1))[0]
+            eps = 1e-11 if prec != pr.PR_FP32 else 1e-7
+            a = G.solve(C, eps, algo, prec, opts=dict(mode=pr.PR_MODE_PULL))[0]
+            b = G.solve(C, eps, algo, prec, opts=dict(mode=pr.PR_MODE_PULL))[0]
+            c = G.solve(C, eps, algo, prec, opts=dict(mode=pr.PR_MODE_PULL, use_graph=-1))[0]
             assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
@@ -340,23 +349,25 @@ def test_fullsize_rmat22_bench_configuration(rmat22):
     g, truth, ref, pw9 = rmat22
     p = gg.p_uniform(g.n)
     with gpu_graph(g) as G:
-        # the benchmark's solve: IFP2, FP64, eps 1e-9, default options (CUDA-graph rounds)
-        out, st, status = G.solve(C, 1e-9, pr.PR_IFP2, pr.PR_FP64)
-        assert status == pr.PR_OK
-        assert abs(st["rounds"] - ref[1e-9]["rounds"]) <= 1
-        assert l1(out, ref[1e-9]["pi"]) <= 1e-9            # parity with the same algorithm
-        err = l1(out, truth)
-        assert err <= st["err_bound"] + 1e-12               # certified bound vs exact PageRank
-        assert err <= oracle.eq2_residual(g, C, p, out) / (1 - C) + 1e-12
+        # the benchmark's solve: IFP2, double-float and FP64, eps 1e-9, default options
+        for prec in (pr.PR_DF64, pr.PR_FP64):
+            out, st, status = G.solve(C, 1e-9, pr.PR_IFP2, prec)
+            assert status == pr.PR_OK
+            assert abs(st["rounds"] - ref[1e-9]["rounds"]) <= 1
+            assert l1(out, ref[1e-9]["pi"]) <= 1e-9            # parity with the same algorithm
+            err = l1(out, truth)
+            assert err <= st["err_bound"] + 1e-12               # certified bound vs exact PageRank
+            assert err <= oracle.eq2_residual(g, C, p, out) / (1 - C) + 1e-12
         # FP32 form (FP32 rounds, FP64 correction) against the FP64 oracle at the same eps
         out, st, status = G.solve(C, 1e-6, pr.PR_IFP2, pr.PR_FP32)
         assert status == pr.PR_OK and l1(out, ref[1e-6]["pi"]) <= 1e-6
         assert l1(out, truth) <= st["err_bound"] + 1e-9
         # Power at the same tolerance as the oracle's Power
-        out, st, status = G.solve(C, 1e-9, pr.PR_POWER, pr.PR_FP64)
-        assert status == pr.PR_OK and l1(out, pw9) <= 1e-9
-        assert l1(out, truth) <= st["err_bound"] + 1e-12
+        for prec in (pr.PR_FP64, pr.PR_DF64):
+            out, st, status = G.solve(C, 1e-9, pr.PR_POWER, prec)
+            assert status == pr.PR_OK and l1(out, pw9) <= 1e-9
+            assert l1(out, truth) <= st["err_bound"] + 1e-12
         # push-only and pull-only delivery give the same result up to rounding
         for mode in (pr.PR_MODE_PUSH, pr.PR_MODE_PULL):
-            out2, st2, _ = G.solve(C, 1e-9, pr.PR_IFP2, opts=dict(mode=mode))
+            out2, st2, _ = G.solve(C, 1e-9, pr.PR_IFP2, pr.PR_DF64, opts=dict(mode=mode))
             assert l1(out2, ref[1e-9]["pi"]) <= 1e-9
