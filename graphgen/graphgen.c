@@ -83,14 +83,34 @@ void gg_vertex_mask(int32_t n, double frac, uint64_t seed, uint64_t stream, uint
     for (int32_t i = 0; i < n; i++) mask[i] = draw_u01(seed, 200 + stream, (uint64_t)i) < frac;
 }
 
-/* Uniformly random permutation of [0, n) (Fisher-Yates, sequential). */
+/*
+ * Uniformly random permutation of [0, n): vertex i gets as its new id the rank
+ * of its 63-bit key draw(seed, 300 + stream, i) >> 1 among all keys (ties,
+ * which have probability about n^2 / 2^64, go to the smaller i).  Defined by
+ * sorting so that a data-parallel generator can produce the same permutation.
+ */
+typedef struct {
+    uint64_t k;
+    int32_t i;
+} gg_key_idx;
+
+static int cmp_key_idx(const void *x, const void *y) {
+    const gg_key_idx *a = (const gg_key_idx *)x, *b = (const gg_key_idx *)y;
+    if (a->k != b->k) return a->k < b->k ? -1 : 1;
+    return (a->i > b->i) - (a->i < b->i);
+}
+
 void gg_permutation(int32_t n, uint64_t seed, uint64_t stream, int32_t *perm) {
-    for (int32_t i = 0; i < n; i++) perm[i] = i;
-    for (int32_t i = n - 1; i > 0; i--) {
-        uint64_t h = draw(seed, 300 + stream, (uint64_t)i);
-        int32_t j = (int32_t)(((h >> 32) * (uint64_t)(i + 1)) >> 32);
-        int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    gg_key_idx *a = (gg_key_idx *)malloc(sizeof(gg_key_idx) * ((size_t)n + 1));
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < n; i++) {
+        a[i].k = draw(seed, 300 + stream, (uint64_t)i) >> 1;
+        a[i].i = i;
     }
+    qsort(a, (size_t)n, sizeof(gg_key_idx), cmp_key_idx);
+#pragma omp parallel for schedule(static)
+    for (int32_t r = 0; r < n; r++) perm[a[r].i] = r;
+    free(a);
 }
 
 /* Apply a vertex relabelling to an edge list in place: v -> perm[v]. */

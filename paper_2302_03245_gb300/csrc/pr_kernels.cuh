@@ -139,21 +139,18 @@ template <typename V> struct GT;
 template <> struct GT<double> {
     using A = double;
     static __device__ __forceinline__ A zero() { return 0.0; }
-    static __device__ __forceinline__ double vzero() { return 0.0; }
     static __device__ __forceinline__ A add(A a, double v) { return a + v; }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
 };
 template <> struct GT<float> {
     using A = float;
     static __device__ __forceinline__ A zero() { return 0.f; }
-    static __device__ __forceinline__ float vzero() { return 0.f; }
     static __device__ __forceinline__ A add(A a, float v) { return a + v; }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
 };
 template <> struct GT<float2> {
     using A = float2;
     static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ float2 vzero() { return make_float2(0.f, 0.f); }
     static __device__ __forceinline__ A add(A a, float2 v) { return df_add(a, v); }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) {
         return make_float2(__shfl_down_sync(0xffffffffu, a.x, o, w), __shfl_down_sync(0xffffffffu, a.y, o, w));
@@ -349,29 +346,45 @@ template <typename T> __device__ __forceinline__ void store_partial(double *slot
     memcpy(reinterpret_cast<char *>(slots) + 8 * (size_t)blockIdx.x, &v, 8);
 }
 
-// sum of val[src[e]] over e in [off[j] + start, off[j+1]) stepping by `step`;
-// in-list entries are streamed once (evict-first), gathered values go through
-// the read-only path (not written during the kernel)
+// Gathers of in-list sums.  A lane sums val[src[e]] over its entries
+// e = off[j] + start, + step, ... < off[j+1] strictly in that order (one
+// accumulator per row), so the result does not depend on how the loads are
+// batched.  The loads are batched U at a time: U in-list entries first (they
+// stream from HBM once, evict-first), then the U gathered values (read-only
+// path; L2-resident in practice), so that U dependent load pairs per row are
+// in flight instead of one.
+template <typename V, int U>
+__device__ __forceinline__ void row_acc_u(const int32_t *__restrict__ src, const V *__restrict__ val, int &e, int b,
+                                          int step, typename GT<V>::A &acc) {
+    int idx[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int ee = e + u * step;
+        idx[u] = ee < b ? __ldcs(&src[ee]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (idx[u] >= 0) acc = GT<V>::add(acc, __ldg(&val[idx[u]]));
+    e += U * step;
+}
+
+// one row, all of a block's threads (start = threadIdx.x, step = blockDim.x)
 template <typename V>
 __device__ __forceinline__ typename GT<V>::A row_sum(const int32_t *__restrict__ off,
                                                      const int32_t *__restrict__ src, int j,
                                                      const V *__restrict__ val, int start, int step) {
     using A = typename GT<V>::A;
-    const int a = __ldg(&off[j]), b = __ldg(&off[j + 1]);
-    A acc0 = GT<V>::zero(), acc1 = GT<V>::zero();
-    int e = a + start;
-    for (; e + step < b; e += 2 * step) {
-        const int s0 = __ldcs(&src[e]), s1 = __ldcs(&src[e + step]);
-        acc0 = GT<V>::add(acc0, __ldg(&val[s0]));
-        acc1 = GT<V>::add(acc1, __ldg(&val[s1]));
-    }
-    if (e < b) acc0 = GT<V>::add(acc0, __ldg(&val[__ldcs(&src[e])]));
-    return GT<V>::add(acc0, acc1);
+    const int b = __ldg(&off[j + 1]);
+    int e = __ldg(&off[j]) + start;
+    A acc = GT<V>::zero();
+    while (e < b) row_acc_u<V, 8>(src, val, e, b, step, acc);
+    return acc;
 }
 
-// The sums of ROWS rows at once (rows js[r], valid[r]), interleaved so that the
-// in-list entry loads and then the gathers of all rows are in flight together.
-template <typename V, int ROWS>
+// The sums of ROWS rows at once (rows js[r], valid[r]), U entries per row per
+// step: the in-list entry loads and then the gathers of all rows are in flight
+// together.
+template <typename V, int ROWS, int U>
 __device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
                                          const int *js, const bool *valid, const V *__restrict__ val, int start,
                                          int step, typename GT<V>::A *acc) {
@@ -389,16 +402,21 @@ __device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const 
         any |= e[r] < b[r];
     }
     while (any) {
-        int idx[ROWS];
+        int idx[ROWS][U];
 #pragma unroll
-        for (int r = 0; r < ROWS; r++) idx[r] = e[r] < b[r] ? __ldcs(&src[e[r]]) : -1;
+        for (int r = 0; r < ROWS; r++)
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int ee = e[r] + u * step;
+                idx[r][u] = ee < b[r] ? __ldcs(&src[ee]) : -1;
+            }
         any = false;
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
-            if (idx[r] >= 0) {
-                acc[r] = GT<V>::add(acc[r], __ldg(&val[idx[r]]));
-                e[r] += step;
-            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (idx[r][u] >= 0) acc[r] = GT<V>::add(acc[r], __ldg(&val[idx[r][u]]));
+            e[r] += U * step;
             any |= e[r] < b[r];
         }
     }
@@ -407,6 +425,13 @@ __device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const 
 // rows in flight per lane group: short rows (few lanes) interleave more of them
 template <int LANES> struct RowsInFlight {
     static constexpr int value = LANES <= 2 ? 4 : (LANES <= 16 ? 2 : 1);
+};
+// entries per row per step: the bins give rows of at most 2 * LANES entries
+// below 32 lanes (one step covers them; 1- and 2-lane rows interleave 4 rows
+// instead, which keeps the kernel at 48 registers); warp rows run up to 128
+// entries per lane
+template <int LANES> struct EntriesInFlight {
+    static constexpr int value = LANES <= 2 ? 1 : (LANES < 32 ? 2 : 8);
 };
 
 // ------------------------------------------------------------ round decision
@@ -605,10 +630,10 @@ __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int 
             js[r] = base + r * stride + grp;
             valid[r] = js[r] < S.hi;
         }
-        row_sums<V, ROWS>(G.inr_off, G.inr_src, js, valid, wprev, lane, LANES, acc);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inr_off, G.inr_src, js, valid, wprev, lane, LANES, acc);
         if (use_unref) {
             A extra[ROWS];
-            row_sums<V, ROWS>(G.inu_off, G.inu_src, js, valid, wprev, lane, LANES, extra);
+            row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inu_off, G.inu_src, js, valid, wprev, lane, LANES, extra);
 #pragma unroll
             for (int r = 0; r < ROWS; r++) acc[r] = GT<V>::add(acc[r], extra[r]);
         }
@@ -836,8 +861,8 @@ __device__ __forceinline__ void sweep_rows(const DevGraph &G, const Seg &S, int 
             js[r] = base + r * stride + grp;
             valid[r] = js[r] < S.hi;
         }
-        row_sums<V, ROWS>(G.inr_off, G.inr_src, js, valid, a.val, lane, LANES, acc);
-        row_sums<V, ROWS>(G.inu_off, G.inu_src, js, valid, a.val, lane, LANES, extra);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inr_off, G.inr_src, js, valid, a.val, lane, LANES, acc);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inu_off, G.inu_src, js, valid, a.val, lane, LANES, extra);
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
             acc[r] = GT<V>::add(acc[r], extra[r]);
