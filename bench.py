@@ -52,6 +52,12 @@ def parse():
                     help="launch rounds from the host instead of the CUDA-graph while loop (same kernels; "
                          "lets a profiler see each launch)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuned launch parameters (read if it has this graph, else written)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters")
+    ap.add_argument("--legs", default="dag,batch,serve",
+                    help="extra configurations after the headline: dag (scale-24 DAG-heavy, FP32 form), "
+                         "batch (512 graphs in one batch), serve (continuous batching); '' for none")
     return ap.parse_args()
 
 
@@ -65,6 +71,12 @@ def workload(scale):
 def make_graph(scale):
     import graphgen as gg
     return gg.rmat(scale, 16, dangling=0.20, unref=0.10, seed=1)
+
+
+def make_graph_device(scale):
+    """The same graph as make_graph, generated on the GPU (graphgen.torchgen)."""
+    from graphgen import torchgen as tg
+    return tg.rmat(scale, 16, dangling=0.20, unref=0.10, seed=1, device="cuda")
 
 
 # ------------------------------------------------------------------ clocks
@@ -154,6 +166,277 @@ def recorded_traffic(kernel, workload_name):
     return e.get("dram_bytes_per_launch")
 
 
+def info_sms(torch):
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def median_solve(G, flush, reps, *a, **kw):
+    """Median device ms of `reps` solves (L2 flushed before each) and the last stats."""
+    ms, st = [], None
+    for _ in range(reps):
+        flush.zero_()
+        _, st, status = G.solve(*a, **kw)
+        assert status == 0, st
+        ms.append(st["ms"])
+    return statistics.median(ms), st
+
+
+def pull_roofline(info, st, prof_ms, s_first, s_after, fp64_rounds, hbm_peak, peak_src):
+    """Algorithmic bytes of the pull rounds of one traced solve (state bytes s_first
+    before the correction, s_after after it) over their profiled device time."""
+    tr = st["trace"]
+    nr = st["rounds"]
+    modes = tr["mode"][:nr]
+    push_e = int(sum(tr["E"][t] for t in range(nr) if modes[t] == 1))
+    scan = st["edges_scanned"] - push_e - info["m_d"]
+    n_pull = max(int((modes == 2).sum()), 1)
+    scan_per = scan / n_pull
+    alg = 0.0
+    for t in range(nr):
+        if modes[t] == 2:
+            s = s_first if t < nr - fp64_rounds else s_after
+            alg += algorithmic_bytes_pull_round(info, s, scan_per, info["n_nd"], tr["F"][t])
+    achieved = alg / (prof_ms / 1e3) / 1e9 if prof_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": "k_round_pull", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (copy bandwidth)",
+            "alg_bytes_per_launch": alg / n_pull, "avg_launch_ms": prof_ms / n_pull, "traffic": None}
+
+
+def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
+    """Large DAG-heavy graph: R-MAT scale 24, edge factor 16, 70% of edges turned
+    forward in a seeded random order, 25% dangling; IFP2 in the FP32 form (float
+    state, FP64 sums, FP64 correction sweep, double-float finish), eps 1e-9;
+    delivery push-only, pull-only and AUTO; Power at equal L1."""
+    import numpy as np
+    from graphgen import torchgen as tg
+    t0 = time.perf_counter()
+    gd = tg.rmat(24, 16, dangling=0.25, unref=0.0, seed=1, dag_frac=0.7, device="cuda")
+    off, dst = gd.csr32()
+    G = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream)
+    del gd, off, dst
+    torch.cuda.synchronize()
+    res = {"workload": "rmat24_dag70_ifp2_fp32", "graph_s": time.perf_counter() - t0,
+           "graph": {k: G.info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_indeg",
+                                             "max_outdeg", "ms_preprocess")}}
+    t0 = time.perf_counter()
+    tuning, rep = G.autotune(pr.PR_FP32, max_ms=2000.0)
+    res["tuning"] = dict(tuning, autotune_s=time.perf_counter() - t0, report_last=rep.splitlines()[-1])
+    n = G.info["n"]
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    truth = torch.empty_like(out)
+    _, st_t, _ = G.solve(C, 1e-14, pr.PR_POWER, pr.PR_FP64, out=truth)
+    res["reference_solution"] = f"GPU Power FP64 to ||delta||_1 <= 1e-14 ({st_t['rounds']} iterations)"
+    eps = 1e-9
+    for name, mode, reps in (("auto", pr.PR_MODE_AUTO, 3), ("pull", pr.PR_MODE_PULL, 3), ("push", pr.PR_MODE_PUSH, 2)):
+        ms, st = median_solve(G, flush, reps, C, eps, pr.PR_IFP2, pr.PR_FP32, out=out, opts=dict(mode=mode))
+        res[f"ifp2_fp32_{name}"] = dict(ms=ms, rounds=st["rounds"], rounds_push=st["rounds_push"],
+                                        rounds_pull=st["rounds_pull"], fp64_rounds=st["fp64_rounds"],
+                                        l1=float((out - truth).abs().sum()), err_bound=st["err_bound"],
+                                        gedges_s=st["edges_pushed"] / ms / 1e6)
+    ms, st = median_solve(G, flush, 3, C, eps, pr.PR_IFP2, pr.PR_DF64, out=out)
+    res["ifp2_df64_auto"] = dict(ms=ms, rounds=st["rounds"], l1=float((out - truth).abs().sum()),
+                                 err_bound=st["err_bound"], gedges_s=st["edges_pushed"] / ms / 1e6)
+    # roofline of the dominant kernel from a traced, profiled FP32-form solve
+    flush.zero_()
+    _, st, _ = G.solve(C, eps, pr.PR_IFP2, pr.PR_FP32, out=out, opts=dict(profile=1, trace_cap=4096))
+    prof = st["profile"]
+    tot = sum(v["ms"] for v in prof.values())
+    res["kernels"] = {k: dict(launches=v["launches"], ms=v["ms"], share=v["ms"] / tot) for k, v in prof.items()}
+    if "k_round_pull" in prof:
+        res["roofline"] = pull_roofline(G.info, st, prof["k_round_pull"]["ms"], 4, 8, st["fp64_rounds"], hbm_peak,
+                                        peak_src)
+    target = res["ifp2_fp32_auto"]["l1"]
+    for pname, pprec in (("fp32", pr.PR_FP32), ("df64", pr.PR_DF64)):
+        ladder = []
+        for tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10):
+            ms, st = median_solve(G, flush, 2, C, tol, pr.PR_POWER, pprec, out=out)
+            ladder.append(dict(tol=tol, ms=ms, iters=st["rounds"], l1=float((out - truth).abs().sum())))
+            if ladder[-1]["l1"] <= target:
+                break
+        res[f"power_{pname}_ladder"] = ladder
+        eq = next((q for q in ladder if q["l1"] <= target), None)
+        if eq:
+            res[f"power_{pname}_at_equal_l1"] = dict(eq, speedup_ifp2=eq["ms"] / res["ifp2_fp32_auto"]["ms"])
+    G.close()
+    return res
+
+
+def batch_specs(count=512, seed=4):
+    """Graph sizes and kinds of the batched configuration."""
+    import math
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    specs = []
+    for j in range(count):
+        n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e6))))
+        dang = float(rng.uniform(0.1, 0.3))
+        if j % 2 == 0:
+            specs.append(dict(kind="rmat", scale=max(1, math.ceil(math.log2(n))), edge_factor=float(rng.uniform(8, 16)),
+                              nverts=n, dangling=dang, unref=0.0, seed=1000 + j))
+        else:
+            specs.append(dict(kind="er", n=n, avg_deg=float(rng.uniform(4, 32)), dangling=dang, unref=0.0,
+                              seed=1000 + j, permute=True))
+    return specs
+
+
+def make_spec(tg, sp):
+    kw = {k: v for k, v in sp.items() if k != "kind"}
+    return tg.rmat(device="cuda", **kw) if sp["kind"] == "rmat" else tg.er(device="cuda", **kw)
+
+
+def leg_batch(pr, torch, stream, flush, hbm_peak, peak_src):
+    """512 independent graphs (n log-uniform in [1e3, 2e6]; even: R-MAT with edge
+    factor 8-16 cut to n vertices, odd: Erdos-Renyi with mean out-degree 4-32;
+    10-30% dangling) solved by IFP2 in the FP32 form to eps 1e-6 in one
+    pr_solve_batch, against the same 512 solves one at a time."""
+    from graphgen import torchgen as tg
+    t0 = time.perf_counter()
+    hs = []
+    for sp in batch_specs():
+        gd = make_spec(tg, sp)
+        off, dst = gd.csr32()
+        hs.append(pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream))
+        del gd, off, dst
+    torch.cuda.synchronize()
+    res = {"workload": "batch512_ifp2_fp32", "graphs": len(hs), "graph_s": time.perf_counter() - t0,
+           "n_total": sum(h.info["n"] for h in hs), "m_total": sum(h.info["m"] for h in hs)}
+    outs = [torch.empty(h.info["n"], dtype=torch.float64, device="cuda") for h in hs]
+    eps = 1e-6
+    bt = []
+    for k in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, sts, status = pr.pr_solve_batch(hs, C, eps, pr.PR_IFP2, pr.PR_FP32, outs=outs)
+        torch.cuda.synchronize()
+        if k:
+            bt.append(1e3 * (time.perf_counter() - t0))
+    edges = sum(s["edges_pushed"] for s in sts)
+    res["batch"] = dict(ms=statistics.median(bt), device_ms=sts[0]["ms"], status=status, edges_pushed=edges,
+                        gedges_s=edges / statistics.median(bt) / 1e6,
+                        rounds_max=max(s["rounds"] for s in sts), rounds_min=min(s["rounds"] for s in sts))
+    for h, o in zip(hs, outs):  # warm each graph's own workspace
+        h.solve(C, eps, pr.PR_IFP2, pr.PR_FP32, out=o)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e1 = 0
+    for h, o in zip(hs, outs):
+        _, st, _ = h.solve(C, eps, pr.PR_IFP2, pr.PR_FP32, out=o)
+        e1 += st["edges_pushed"]
+    torch.cuda.synchronize()
+    single_ms = 1e3 * (time.perf_counter() - t0)
+    res["one_at_a_time"] = dict(ms=single_ms, edges_pushed=e1, gedges_s=e1 / single_ms / 1e6)
+    res["speedup_batch"] = single_ms / res["batch"]["ms"]
+    # accuracy on a sample of the batch
+    _, sts, _ = pr.pr_solve_batch(hs, C, eps, pr.PR_IFP2, pr.PR_FP32, outs=outs)
+    worst = 0.0
+    for k in range(0, len(hs), 64):
+        truth = torch.empty_like(outs[k])
+        hs[k].solve(C, 1e-14, pr.PR_POWER, pr.PR_FP64, out=truth)
+        worst = max(worst, float((outs[k] - truth).abs().sum()) / max(sts[k]["err_bound"], 1e-300))
+    res["sample_l1_over_bound_max"] = worst
+    for h in hs:
+        h.close()
+    return res
+
+
+def leg_serve(pr, torch, stream, flush, hbm_peak, peak_src):
+    """Continuous batching: Poisson arrivals at each rate; 90% personalized
+    PageRank (1-64 seeded vertices, weights 1/k) on a resident R-MAT scale-23
+    graph, 10% full PageRank on one of 8 other resident graphs (n log-uniform in
+    [1e4, 1e6], R-MAT / Erdos-Renyi alternating); FP32 form, c = 0.85,
+    eps 1e-6, 120 GB device budget.  Latency = submit to finish (server clock)
+    plus any delay of the submission behind its scheduled arrival."""
+    import math
+    import numpy as np
+    from graphgen import torchgen as tg
+    t0 = time.perf_counter()
+    gd = tg.rmat(23, 16, dangling=0.20, unref=0.10, seed=3, device="cuda")
+    off, dst = gd.csr32()
+    R = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream)
+    del gd, off, dst
+    rng = np.random.default_rng(7)
+    pool = []
+    for j in range(8):
+        n = int(math.exp(rng.uniform(math.log(1e4), math.log(1e6))))
+        sp = (dict(kind="rmat", scale=math.ceil(math.log2(n)), edge_factor=16.0, nverts=n, dangling=0.2, unref=0.1,
+                   seed=50 + j) if j % 2 == 0 else
+              dict(kind="er", n=n, avg_deg=8.0, dangling=0.2, unref=0.1, seed=50 + j, permute=True))
+        gd = make_spec(tg, sp)
+        off, dst = gd.csr32()
+        pool.append(pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream))
+        del gd, off, dst
+    torch.cuda.synchronize()
+    n_res = R.info["n"]
+    res = {"workload": "serve_rmat23_ppr90_fp32", "graph_s": time.perf_counter() - t0,
+           "resident": {k: R.info[k] for k in ("n", "m", "n_nd")}, "pool_n": [h.info["n"] for h in pool]}
+
+    def request(rr):
+        if rr.uniform() < 0.9:
+            k = int(rr.integers(1, 65))
+            idx = rr.choice(n_res, size=k, replace=False).astype(np.int32)
+            return R, np.full(k, 1.0 / k), idx
+        return pool[int(rr.integers(0, len(pool)))], None, None
+
+    # one at a time through pr_solve (the same requests), for the throughput comparison
+    rr = np.random.default_rng(11)
+    alone = []
+    for _ in range(3):
+        h, pv, pi = request(rr)
+        h.solve(C, 1e-6, pr.PR_IFP2, pr.PR_FP32, p=pv, p_idx=pi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(40):
+        h, pv, pi = request(rr)
+        _, st, _ = h.solve(C, 1e-6, pr.PR_IFP2, pr.PR_FP32, p=pv, p_idx=pi)
+        alone.append(st["ms"])
+    res["one_at_a_time"] = dict(solves_s=40 / (time.perf_counter() - t0), p50_ms=float(np.percentile(alone, 50)),
+                                p99_ms=float(np.percentile(alone, 99)))
+    rates = []
+    with pr.Server(120 << 30, stream=None) as S:
+        for _ in range(8):  # warm-up: the server's tables and the per-graph tiles
+            h, pv, pi = request(rr)
+            S.wait(S.submit(h, C, 1e-6, pr.PR_FP32, pv, pi))
+        for rate in (100, 300, 1000, 3000, 10000, 20000):
+            N = min(int(rate * 2.0), 400)
+            arr = np.cumsum(rng.exponential(1.0 / rate, N))
+            reqs = [request(rr) for _ in range(N)]
+            lat, lag, pending = [], {}, {}
+            t_start = time.perf_counter()
+            i = 0
+            statuses = set()
+            while i < N or pending:
+                now = time.perf_counter() - t_start
+                while i < N and arr[i] <= now:
+                    h, pv, pi = reqs[i]
+                    tk = S.submit(h, C, 1e-6, pr.PR_FP32, pv, pi)
+                    pending[tk] = max(0.0, (time.perf_counter() - t_start) - arr[i])
+                    i += 1
+                done = []
+                for tk, lg in pending.items():
+                    r = S.poll(tk)
+                    if r is not None:
+                        statuses.add(r[2])
+                        lat.append(r[1]["ms"] + 1e3 * lg)
+                        done.append(tk)
+                for tk in done:
+                    del pending[tk]
+                if not done:
+                    time.sleep(0.0002)
+            wall = time.perf_counter() - t_start
+            rates.append(dict(rate=rate, requests=N, solves_s=N / wall, p50_ms=float(np.percentile(lat, 50)),
+                              p99_ms=float(np.percentile(lat, 99)), status=sorted(statuses)))
+    res["rates"] = rates
+    R.close()
+    for h in pool:
+        h.close()
+    return res
+
+
+LEGS = {"dag": leg_dag, "batch": leg_batch, "serve": leg_serve}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     """The FP64 oracle's synchronous-round IFP2 on the same graph, on host cores:
@@ -221,15 +504,27 @@ def main():
 
     stream = torch.cuda.current_stream()
     pr.use_torch_allocator(True)
-    g = make_graph(args.scale)
-    st_g = g.stats()
-    off, dst = g.csr32()
-    d_off = torch.from_numpy(off).cuda()
-    d_dst = torch.from_numpy(dst).cuda()
+    tgen0 = time.perf_counter()
+    gd = make_graph_device(args.scale)
+    d_off, d_dst = gd.csr32()
     torch.cuda.synchronize()
-    G = pr.Graph(g.n, g.m, d_off, d_dst, mem_is_device=True, stream=stream)
+    gen_s = time.perf_counter() - tgen0
+    n_v, m_e = gd.n, gd.m
+    G = pr.Graph(n_v, m_e, d_off, d_dst, mem_is_device=True, stream=stream)
+    g = gd.to_host()  # for the host-side legs (e2e copies, the oracle)
+    del gd
     info = G.info
-    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    tune_report = "default launch parameters"
+    tune_s = 0.0
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        if args.tune_cache:
+            tuning, tune_report = G.autotune(pr.PR_DF64, max_ms=1500.0, cache_path=args.tune_cache)
+        else:
+            tuning, tune_report = G.autotune(pr.PR_DF64, max_ms=1500.0)
+        tune_s = time.perf_counter() - t0
+    tuning = G.tuning()
+    out = torch.empty(n_v, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
     def solve(algo=pr.PR_IFP2, prec=pr.PR_DF64, eps=args.eps, opts=None):
@@ -285,7 +580,9 @@ def main():
             "gpu_launches": int(launches), "clocks": clk,
             "graph": {k: info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_outdeg",
                                              "max_indeg")},
-            "rounds": rounds[0], "edges_pushed_per_step": edges[0], "wall_s_timed": wall}
+            "rounds": rounds[0], "edges_pushed_per_step": edges[0], "wall_s_timed": wall,
+            "tuning": dict(tuning, autotune_s=tune_s, source=tune_report.splitlines()[-1] if tune_report else ""),
+            "graph_generation_s": gen_s}
     if rank != 0 or args.skip_extras:
         if rank == 0:
             emit(line, args)
@@ -379,7 +676,7 @@ def main():
     line["vs_power"] = legs
     pre = []
     for _ in range(3):
-        G2 = pr.Graph(g.n, g.m, d_off, d_dst, mem_is_device=True, stream=stream)
+        G2 = pr.Graph(n_v, m_e, d_off, d_dst, mem_is_device=True, stream=stream)
         pre.append(G2.info["ms_preprocess"])
         G2.close()
     line["preprocess_ms"] = statistics.median(pre)
@@ -395,6 +692,7 @@ def main():
     line["solve_hbm_frac"] = alg_solve / (t_step / 1e3) / 1e9 / hbm_peak
 
     # ---- end to end through the C ABI with pinned host buffers
+    off, dst = g.csr32()
     h_off = torch.from_numpy(off).pin_memory()
     h_dst = torch.from_numpy(dst).pin_memory()
     h_out = torch.empty(g.n, dtype=torch.float64).pin_memory()
@@ -412,8 +710,8 @@ def main():
     line["e2e"] = {"value": sum(e2e_edges) / (sum(e2e_ms) / 1e3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": int(off.nbytes + dst.nbytes), "d2h_bytes_per_step": int(8 * g.n),
                    "ms_per_step": statistics.median(e2e_ms),
-                   "includes": "pr_graph_create from pinned host CSR (copy, validation, preprocessing) + "
-                               "pr_solve IFP2 df64 + copy of pi to pinned host memory"}
+                   "includes": "pr_graph_create from pinned host CSR (copy, validation, preprocessing, default "
+                               "launch parameters) + pr_solve IFP2 df64 + copy of pi to pinned host memory"}
 
     # ---- the oracle on the host cores (bounded sample)
     import oracle
@@ -425,8 +723,40 @@ def main():
     line["cpu_baseline"] = {"value": float(o["E"].sum()) / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"first {rounds_cpu} synchronous IFP2 rounds of the FP64 oracle on the full "
                                       f"graph, single thread ({dt:.1f} s)"}
-    emit(line, args)
+    del g, o
+    # ---- default launch parameters against the tuned ones (same solve)
+    if not args.no_tune:
+        tuned = G.tuning()
+        G.set_tuning(pull_thr=[4096, 32, 16, 8, 4, 2], block_budget=info_sms(torch) * 16, pull_ratio=0.04)
+        tms = []
+        for _ in range(3):
+            flush.zero_()
+            tms.append(solve()["ms"])
+        G.set_tuning(pull_thr=tuned["pull_thr"], block_budget=tuned["block_budget"], pull_ratio=tuned["pull_ratio"])
+        line["tuning"]["default_params_ms"] = statistics.median(tms)
+        line["tuning"]["tuned_ms"] = t_step
     G.close()
+    legs = [x for x in args.legs.split(",") if x]
+    extra = {}
+    for leg in legs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            extra[leg] = LEGS[leg](pr, torch, stream, flush, hbm_peak, peak_src)
+        except Exception as e:  # a failed leg is reported, the headline line still prints
+            extra[leg] = {"error": f"{type(e).__name__}: {e}"}
+        extra[leg]["leg_wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    if "dag" in extra:
+        line["dag24"] = extra["dag"]
+    if "batch" in extra:
+        line["batch512"] = extra["batch"]
+    if "serve" in extra:
+        line["serving"] = extra["serve"]
+        sv = extra["serve"]
+        if "rates" in sv:
+            line["served_p50_p99_ms"] = {str(r["rate"]): [r["p50_ms"], r["p99_ms"]] for r in sv["rates"]}
+    emit(line, args)
     if dist:
         dist.destroy_process_group()
 

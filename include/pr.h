@@ -193,6 +193,49 @@ pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const in
 pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);
 
 /*
+ * Launch parameters of a graph's kernels.  They decide how the rounds of
+ * Sec. 3.2 / 3.4 map onto the GPU, never what a round computes (the paper has
+ * no counterpart: its K CPU threads scan static vertex sets).
+ *  pull_thr:     in-degree thresholds of the gather bins, non-increasing, >= 0.
+ *                Rows with in-degree above pull_thr[0] get a whole block; above
+ *                pull_thr[1..5] they get 32, 16, 8, 4, 2 lanes; the rest 1 lane.
+ *  block_budget: blocks of a dense gather launch, split across the bins in
+ *                proportion to their in-list entries (1 .. 8192).
+ *  pull_ratio:   the AUTO delivery switch used when a solve passes
+ *                pull_ratio = 0: a round pulls when its frontier's out-edges
+ *                reach pull_ratio x the valid edges (m, or m - m_d for IFP2).
+ *  bin_rows:     (read-only) non-dangling rows per bin, block bin first.
+ *  pull_blocks:  (read-only) blocks of a dense gather over the non-dangling rows.
+ * pr_graph_set_tuning reads pull_thr, block_budget and pull_ratio (0 keeps the
+ * current ratio).  Errors: PR_EINVAL (values; the graph keeps its tuning),
+ * PR_ECUDA.
+ */
+typedef struct {
+    int32_t pull_thr[6];
+    int32_t block_budget;
+    int32_t pad0;
+    double pull_ratio;
+    int32_t bin_rows[7];
+    int32_t pull_blocks;
+} pr_tuning;
+pr_status pr_graph_get_tuning(const pr_graph *g, pr_tuning *t);
+pr_status pr_graph_set_tuning(pr_graph *g, const pr_tuning *t);
+
+/*
+ * Autotuner for g's launch parameters (pr_tuning), on g's stream.  It times
+ * dense gather rounds (IFP2, state format prec) for a grid of bin thresholds
+ * and block budgets and keeps the fastest; then it times atomic push rounds
+ * and activation scans against the best gather round and sets pull_ratio at
+ * the frontier size where a push round costs as much as a pull round.
+ * max_ms bounds the device time of the trial solves (0 = 3000 ms); the best
+ * candidate found so far is kept when it runs out.  *t (may be NULL) receives
+ * the chosen tuning; report (may be NULL) receives one line per trial, as
+ * text, up to report_len bytes.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_graph_autotune(pr_graph *g, pr_prec prec, double max_ms, pr_tuning *t, char *report,
+                            size_t report_len);
+
+/*
  * Solve PageRank / personalized PageRank on g.
  *  c:   damping factor, 0 < c < 1 (Sec. 2.1).
  *  eps: IFP: stop when the residual L1 over non-dangling vertices R <= eps

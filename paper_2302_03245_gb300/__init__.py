@@ -80,6 +80,15 @@ class pr_graph_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pr_tuning(ctypes.Structure):
+    _fields_ = [("pull_thr", ctypes.c_int32 * 6), ("block_budget", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("pull_ratio", ctypes.c_double), ("bin_rows", ctypes.c_int32 * 7), ("pull_blocks", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"pull_thr": list(self.pull_thr), "block_budget": self.block_budget, "pull_ratio": self.pull_ratio,
+                "bin_rows": list(self.bin_rows), "pull_blocks": self.pull_blocks}
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -103,6 +112,13 @@ def lib() -> ctypes.CDLL:
         L.pr_graph_create.restype = ctypes.c_int
         L.pr_graph_get_info.argtypes = [P, ctypes.POINTER(pr_graph_info)]
         L.pr_graph_get_info.restype = ctypes.c_int
+        L.pr_graph_get_tuning.argtypes = [P, ctypes.POINTER(pr_tuning)]
+        L.pr_graph_get_tuning.restype = ctypes.c_int
+        L.pr_graph_set_tuning.argtypes = [P, ctypes.POINTER(pr_tuning)]
+        L.pr_graph_set_tuning.restype = ctypes.c_int
+        L.pr_graph_autotune.argtypes = [P, ctypes.c_int, dbl, ctypes.POINTER(pr_tuning), ctypes.c_char_p,
+                                        ctypes.c_size_t]
+        L.pr_graph_autotune.restype = ctypes.c_int
         L.pr_solve.argtypes = [P, dbl, dbl, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pr_pvec), P, ctypes.c_int,
                                ctypes.POINTER(pr_stats)]
         L.pr_solve.restype = ctypes.c_int
@@ -177,6 +193,67 @@ def pr_graph_get_info(g) -> dict:
     info = pr_graph_info()
     _check(lib().pr_graph_get_info(g, ctypes.byref(info)))
     return info.as_dict()
+
+
+def pr_graph_get_tuning(g) -> dict:
+    t = pr_tuning()
+    _check(lib().pr_graph_get_tuning(g, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def pr_graph_set_tuning(g, pull_thr=None, block_budget=None, pull_ratio=0.0) -> dict:
+    """Wraps pr_graph_set_tuning; unspecified fields keep the graph's values."""
+    t = pr_tuning()
+    _check(lib().pr_graph_get_tuning(g, ctypes.byref(t)))
+    if pull_thr is not None:
+        for k, v in enumerate(pull_thr):
+            t.pull_thr[k] = int(v)
+    if block_budget is not None:
+        t.block_budget = int(block_budget)
+    t.pull_ratio = float(pull_ratio)
+    _check(lib().pr_graph_set_tuning(g, ctypes.byref(t)))
+    return pr_graph_get_tuning(g)
+
+
+def pr_graph_autotune(g, prec: int = PR_DF64, max_ms: float = 0.0) -> tuple[dict, str]:
+    """Wraps pr_graph_autotune.  Returns (chosen tuning, trial report)."""
+    t = pr_tuning()
+    buf = ctypes.create_string_buffer(16384)
+    _check(lib().pr_graph_autotune(g, int(prec), float(max_ms), ctypes.byref(t), buf, len(buf)))
+    return t.as_dict(), buf.value.decode(errors="replace")
+
+
+def graph_signature(info: dict) -> str:
+    """Key of a tuning cache entry: the graph facts the launch parameters depend on."""
+    return "n{n}_m{m}_nd{n_nd}_ref{n_ref}_md{m_d}_maxin{max_indeg}_maxout{max_outdeg}".format(**info)
+
+
+def autotune_cached(g, cache_path: str, prec: int = PR_DF64, max_ms: float = 0.0) -> tuple[dict, str]:
+    """Autotune g, or apply the tuning stored for a graph with the same signature
+    (and the same GPU) in the JSON file cache_path; new results are added to it."""
+    import json
+    info = pr_graph_get_info(g)
+    try:
+        import torch
+        dev = torch.cuda.get_device_name()
+    except Exception:
+        dev = "unknown"
+    key = f"{dev}|{prec}|{graph_signature(info)}"
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        e = cache[key]
+        return pr_graph_set_tuning(g, e["pull_thr"], e["block_budget"], e["pull_ratio"]), "from cache"
+    t, rep = pr_graph_autotune(g, prec, max_ms)
+    cache[key] = {k: t[k] for k in ("pull_thr", "block_budget", "pull_ratio")}
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+    return t, rep
 
 
 def pr_destroy(g) -> None:
@@ -388,6 +465,17 @@ class Graph:
 
     def solve(self, c, eps, algo, prec=PR_FP64, **kw):
         return pr_solve(self.h, c, eps, algo, prec, **kw)
+
+    def tuning(self) -> dict:
+        return pr_graph_get_tuning(self.h)
+
+    def set_tuning(self, **kw) -> dict:
+        return pr_graph_set_tuning(self.h, **kw)
+
+    def autotune(self, prec=PR_DF64, max_ms=0.0, cache_path=None):
+        if cache_path:
+            return autotune_cached(self.h, cache_path, prec, max_ms)
+        return pr_graph_autotune(self.h, prec, max_ms)
 
     def close(self):
         pr_destroy(self.h)

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <vector>
 
+#include "pr_group.cuh"
 #include "pr_kernels.cuh"
 
 namespace pr {
@@ -494,7 +495,6 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     pr_opts opt{};
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
-    if (opt.pull_ratio <= 0) opt.pull_ratio = 0.04;
     if (opt.mode < 0 || opt.mode > 2) return fail(PR_EINVAL, "unknown mode");
     for (int k = 0; k < count; k++) {
         if (!gs[k]) return fail(PR_EINVAL, "pr_solve_batch: graph " + std::to_string(k) + " is NULL");
@@ -570,7 +570,7 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
         h.one_minus_c = 1.0 - c[k];
         h.eps = eps[k];
         h.xi = opt.xi_act > 0 ? opt.xi_act : eps[k] / (double)std::max(g->G.n_nd, 1);
-        h.pull_edges = opt.pull_ratio * (double)std::max<int64_t>(m_valid, 1);
+        h.pull_edges = (opt.pull_ratio > 0 ? opt.pull_ratio : g->pull_ratio) * (double)std::max<int64_t>(m_valid, 1);
         h.pu = 1.0 / (double)g->G.n;
         h.algo = algo;
         h.policy = opt.mode;
@@ -742,6 +742,13 @@ __global__ void k_gather_status(const BProb *probs, int count, ReqStat *out) {
     }
 }
 
+__global__ void k_gather_ctls(Ctl *const *ctls, int count, ReqStat *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const Ctl *c = ctls[k];
+        out[k] = ReqStat{c->done, c->status, c->round, 0};
+    }
+}
+
 // r = p for one request: zero everywhere, then the seeds (or uniform)
 template <typename T>
 __global__ void k_req_init(int32_t n, T *x, T *r, double pu, const int32_t *idx, const double *val, int nnz,
@@ -803,6 +810,8 @@ struct SReq {
     StateOffsets s_main{}, s_df{};
     size_t off_ctl = 0, off_out = 0, off_x64 = 0, off_r64 = 0, off_q64 = 0, off_p64 = 0, off_sidx = 0, off_sval = 0;
     int32_t rounds_first = 0;
+    void *group = nullptr;          // column group holding the request's rounds (nullptr: tile engine)
+    int gcol = -1;
     std::vector<double> result;
     pr_stats st{};
     std::chrono::steady_clock::time_point t_submit;
@@ -856,6 +865,25 @@ RoundBuf req_buf(const SReq &q, const StateOffsets &o) {
 }  // namespace
 
 struct ServerImpl {
+    // K requests on one graph whose rounds share every gather (pr_group.cu)
+    struct Group {
+        pr_graph *g = nullptr;
+        int fmt = 0;  // 0: float state, 1: double-float
+        void *mem = nullptr;
+        size_t bytes = 0;
+        GroupDev D{};
+        SReq *col[8] = {};
+        int32_t next_launch = 0;
+        int live() const {
+            int c = 0;
+            for (int k = 0; k < group_columns(fmt); k++) c += col[k] != nullptr;
+            return c;
+        }
+    };
+    std::vector<Group *> groups;
+    std::unordered_map<uint64_t, int> inflight;  // requests per graph (uid), submitted and not finished
+    int32_t group_min_rows = 1 << 14;            // smaller graphs run in the tile engine
+    Buf d_gctl, d_gstat;
     cudaStream_t s = nullptr;
     int device = 0, sms = 0;
     size_t budget = 0, used = 0;
@@ -953,7 +981,7 @@ struct ServerImpl {
         h.one_minus_c = 1.0 - q->c;
         h.eps = q->eps;
         h.xi = q->eps / (double)std::max(G.n_nd, 1);
-        h.pull_edges = 0.04 * (double)std::max<int64_t>(G.m - q->g->info.m_d, 1);
+        h.pull_edges = q->g->pull_ratio * (double)std::max<int64_t>(G.m - q->g->info.m_d, 1);
         h.pu = q->nnz < 0 ? 1.0 / (double)G.n : 0.0;
         h.p_dense = (q->prec == PR_FP32 && q->nnz >= 0) ? 1 : 0;
         h.algo = PR_IFP2;
@@ -1100,6 +1128,172 @@ struct ServerImpl {
         return PR_OK;
     }
 
+    bool any_active() const {
+        if (!act[0].empty() || !act[1].empty()) return true;
+        for (const Group *G : groups)
+            if (G->live()) return true;
+        return false;
+    }
+
+    // put a just-admitted request into a column group of its graph when the
+    // graph is large and has other requests in flight; false: tile engine
+    bool try_group(SReq *q) {
+        if (q->g->G.n_nd < group_min_rows) return false;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (inflight[q->g->uid] < 2) return false;
+        }
+        const int fmt = q->prec == PR_FP32 ? 0 : 1;
+        const int K = group_columns(fmt);
+        Group *G = nullptr;
+        int col = -1;
+        for (Group *gr : groups) {
+            if (gr->g != q->g || gr->fmt != fmt) continue;
+            for (int k = 0; k < K && col < 0; k++)
+                if (!gr->col[k]) col = k;
+            if (col >= 0) {
+                G = gr;
+                break;
+            }
+        }
+        if (!G) {
+            const size_t gb = group_bytes(q->g, fmt);
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                if (used + gb > budget) return false;
+                used += gb;
+            }
+            G = new (std::nothrow) Group();
+            void *mem = nullptr;
+            if (!G || cudaMallocAsync(&mem, gb, s) != cudaSuccess) {
+                cudaGetLastError();
+                delete G;
+                std::lock_guard<std::mutex> lock(mu);
+                used -= gb;
+                return false;
+            }
+            G->g = q->g;
+            G->fmt = fmt;
+            G->mem = mem;
+            G->bytes = gb;
+            group_layout(q->g, fmt, mem, G->D);
+            for (int k = 0; k < 8; k++) {
+                G->D.ctl[k] = nullptr;
+                G->D.join[k] = -1;
+            }
+            if (cudaMemsetAsync(G->D.ticket, 0, sizeof(uint32_t), s) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFreeAsync(mem, s);
+                delete G;
+                std::lock_guard<std::mutex> lock(mu);
+                used -= gb;
+                return false;
+            }
+            groups.push_back(G);
+            col = 0;
+        }
+        G->col[col] = q;
+        G->D.ctl[col] = q->at<Ctl>(q->off_ctl);
+        G->D.join[col] = G->next_launch;
+        if (group_load(q->g, G->D, fmt, col, q->at<char>(q->s_main.x), q->at<char>(q->s_main.r), s) != PR_OK) {
+            G->col[col] = nullptr;
+            G->D.ctl[col] = nullptr;
+            G->D.join[col] = -1;
+            return false;
+        }
+        q->group = G;
+        q->gcol = col;
+        return true;
+    }
+
+    void release_group_if_empty(Group *G) {
+        if (G->live()) return;
+        cudaFreeAsync(G->mem, s);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            used -= G->bytes;
+        }
+        groups.erase(std::find(groups.begin(), groups.end(), G));
+        delete G;
+    }
+
+    // a few rounds of every group, then its finished columns leave: FP32
+    // requests go on to the correction, double-float requests to the finish
+    pr_status step_groups(int phases) {
+        std::vector<std::pair<Group *, int>> cols;
+        std::vector<Ctl *> ptrs;
+        for (Group *G : groups) {
+            if (!G->live()) continue;
+            for (int k = 0; k < phases; k++) PR_TRY(group_round(G->g, G->D, G->fmt, G->next_launch++, s));
+            for (int k = 0; k < group_columns(G->fmt); k++)
+                if (G->col[k]) {
+                    cols.emplace_back(G, k);
+                    ptrs.push_back(G->D.ctl[k]);
+                }
+        }
+        if (cols.empty()) return PR_OK;
+        const int cnt = (int)cols.size();
+        if (d_gctl.bytes < sizeof(Ctl *) * cnt) PR_TRY(d_gctl.alloc(sizeof(Ctl *) * cnt * 2, s));
+        if (d_gstat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_gstat.alloc(sizeof(ReqStat) * cnt * 2, s));
+        PR_CK(cudaMemcpyAsync(d_gctl.p, ptrs.data(), sizeof(Ctl *) * cnt, cudaMemcpyHostToDevice, s));
+        k_gather_ctls<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_gctl.as<Ctl *>(), cnt,
+                                                                           d_gstat.as<ReqStat>());
+        std::vector<ReqStat> hs(cnt);
+        PR_CK(cudaMemcpyAsync(hs.data(), d_gstat.p, sizeof(ReqStat) * cnt, cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        PR_CK(cudaGetLastError());
+        std::vector<SReq *> to_correct, to_finish;
+        std::vector<int> fin_fmt;
+        std::vector<Group *> touched;
+        for (int i = 0; i < cnt; i++) {
+            if (!hs[i].done) continue;
+            Group *G = cols[i].first;
+            const int k = cols[i].second;
+            SReq *q = G->col[k];
+            PR_TRY(group_extract(G->g, G->D, G->fmt, k, q->at<char>(q->s_main.x), q->at<char>(q->s_main.r), s));
+            G->col[k] = nullptr;
+            G->D.ctl[k] = nullptr;
+            G->D.join[k] = -1;
+            q->group = nullptr;
+            q->gcol = -1;
+            touched.push_back(G);
+            if (q->prec == PR_FP32) {
+                q->rounds_first = hs[i].round;
+                to_correct.push_back(q);
+            } else {
+                to_finish.push_back(q);
+                fin_fmt.push_back(1);
+            }
+        }
+        if (!to_correct.empty()) {
+            PR_TRY(correct(to_correct));
+            for (SReq *q : to_correct) {
+                q->stage = 2;
+                act[1].push_back(q);
+            }
+            dirty[1] = true;
+        }
+        if (!to_finish.empty()) {
+            PR_TRY(finish(to_finish, fin_fmt));
+            complete(to_finish);
+        }
+        for (Group *G : touched)
+            if (std::find(groups.begin(), groups.end(), G) != groups.end()) release_group_if_empty(G);
+        return PR_OK;
+    }
+
+    // finished requests: results are on the host; free their budget share
+    void complete(const std::vector<SReq *> &done) {
+        std::lock_guard<std::mutex> lock(mu);
+        for (SReq *q : done) {
+            q->stage = 3;
+            used -= q->bytes;
+            auto it = inflight.find(q->g->uid);
+            if (it != inflight.end() && --it->second <= 0) inflight.erase(it);
+        }
+        cv.notify_all();
+    }
+
     pr_status step_once() {
         // admit
         std::vector<SReq *> adm;
@@ -1108,7 +1302,7 @@ struct ServerImpl {
             while (!queue.empty()) {
                 SReq *q = queue.front();
                 const size_t need = layout(*q);
-                if (used + need > budget && !(act[0].empty() && act[1].empty() && adm.empty())) break;
+                if (used + need > budget && (any_active() || !adm.empty())) break;
                 queue.pop_front();
                 used += need;
                 adm.push_back(q);
@@ -1117,13 +1311,15 @@ struct ServerImpl {
         for (SReq *q : adm) {
             PR_TRY(admit_one(q));
             q->stage = 1;
+            if (try_group(q)) continue;
             const int f = q->prec == PR_FP32 ? 0 : 1;
             act[f].push_back(q);
             dirty[f] = true;
         }
-        if (act[0].empty() && act[1].empty()) return PR_OK;
-        // a few round phases of every active request, per state format
+        // a few rounds of every request, per state format (groups first)
         constexpr int kPhases = 4;
+        PR_TRY(step_groups(kPhases));
+        if (act[0].empty() && act[1].empty()) return PR_OK;
         std::vector<BProb> hp;
         std::vector<Tile> ht;
         for (int f = 0; f < 2; f++) {
@@ -1187,12 +1383,7 @@ struct ServerImpl {
             }
             if (!to_finish.empty()) {
                 PR_TRY(finish(to_finish, fin_fmt));
-                std::lock_guard<std::mutex> lock(mu);
-                for (SReq *q : to_finish) {
-                    q->stage = 3;
-                    used -= q->bytes;
-                }
-                cv.notify_all();
+                complete(to_finish);
             }
         }
         return PR_OK;
@@ -1204,9 +1395,9 @@ struct ServerImpl {
             {
                 std::unique_lock<std::mutex> lock(mu);
                 cv.wait_for(lock, std::chrono::milliseconds(5),
-                            [&] { return stop || !queue.empty() || !act[0].empty() || !act[1].empty(); });
+                            [&] { return stop || !queue.empty() || any_active(); });
                 if (stop) return;
-                if (queue.empty() && act[0].empty() && act[1].empty()) continue;
+                if (queue.empty() && !any_active()) continue;
             }
             const pr_status st = step_once();
             if (st != PR_OK) {
@@ -1214,16 +1405,29 @@ struct ServerImpl {
                 loop_error = st;
                 loop_msg = pr_last_error();
                 // fail every pending request; the server stays usable for polling
+                std::vector<SReq *> failed;
                 for (int f = 0; f < 2; f++) {
-                    for (SReq *q : act[f]) {
-                        q->stage = 3;
-                        q->status = st;
-                        if (q->mem) cudaFreeAsync(q->mem, s);
-                        q->mem = nullptr;
-                        used -= q->bytes;
-                    }
+                    for (SReq *q : act[f]) failed.push_back(q);
                     act[f].clear();
                     dirty[f] = true;
+                }
+                for (Group *G : groups) {
+                    for (int k = 0; k < 8; k++)
+                        if (G->col[k]) failed.push_back(G->col[k]);
+                    cudaFreeAsync(G->mem, s);
+                    used -= G->bytes;
+                    delete G;
+                }
+                groups.clear();
+                for (SReq *q : failed) {
+                    q->stage = 3;
+                    q->status = st;
+                    q->group = nullptr;
+                    if (q->mem) cudaFreeAsync(q->mem, s);
+                    q->mem = nullptr;
+                    used -= q->bytes;
+                    auto it = inflight.find(q->g->uid);
+                    if (it != inflight.end() && --it->second <= 0) inflight.erase(it);
                 }
                 cv.notify_all();
             }
@@ -1315,6 +1519,7 @@ extern "C" pr_status pr_server_submit(pr_server *S, pr_graph *g, double c, doubl
     q->ticket = I.next_ticket++;
     I.reqs[q->ticket] = q;
     I.queue.push_back(q);
+    I.inflight[g->uid]++;
     *ticket = q->ticket;
     I.cv.notify_all();
     return PR_OK;
@@ -1350,6 +1555,11 @@ extern "C" void pr_server_destroy(pr_server *S) {
     I.cv.notify_all();
     if (I.th.joinable()) I.th.join();
     cudaStreamSynchronize(I.s);
+    for (ServerImpl::Group *G : I.groups) {
+        cudaFreeAsync(G->mem, I.s);
+        delete G;
+    }
+    I.groups.clear();
     for (auto &kv : I.reqs) {
         if (kv.second->mem) cudaFreeAsync(kv.second->mem, I.s);
         delete kv.second;

@@ -271,14 +271,17 @@ static __global__ void k_degree_facts(int32_t n, int32_t n_nd, const int32_t *pe
 }
 
 // bins[k] = number of rows in [lo, hi) (in-degree sorted descending) with indeg > thr[k]
-static __global__ void k_bin_bounds(const int32_t *indeg_int, int32_t lo, int32_t hi, const int32_t *thr,
-                                    int nthr, int32_t *bounds) {
+// first row in [lo, hi) whose in-degree (ref + unref segments) is <= thr[k]:
+// the rows of a class are sorted by in-degree, descending
+static __global__ void k_bin_bounds(const int32_t *inr_off, const int32_t *inu_off, int32_t lo, int32_t hi,
+                                    const int32_t *thr, int nthr, int32_t *bounds) {
     int k = threadIdx.x;
     if (k >= nthr) return;
-    int32_t a = lo, b = hi;  // first row with indeg <= thr
+    int32_t a = lo, b = hi;
     while (a < b) {
         int32_t mid = a + ((b - a) >> 1);
-        if (indeg_int[mid] > thr[k]) a = mid + 1;
+        const int32_t d = (inr_off[mid + 1] - inr_off[mid]) + (inu_off[mid + 1] - inu_off[mid]);
+        if (d > thr[k]) a = mid + 1;
         else b = mid;
     }
     bounds[k] = a;
@@ -385,6 +388,64 @@ void build_plans(pr_graph *g) {
     g->plan_nd = make_plan(nd, k1, g->block_budget);
     g->plan_d = make_plan(d, k2, g->block_budget);
     g->plan_all = make_plan(all, k1 + k2, g->block_budget);
+}
+
+pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t s) {
+    const int32_t n = g->G.n, n_nd = g->G.n_nd, n_ref = g->G.n_ref;
+    for (int k = 0; k < kNumThr; k++) {
+        if (thr[k] < 0 || (k > 0 && thr[k] > thr[k - 1]))
+            return fail(PR_EINVAL, "pull thresholds must be >= 0 and non-increasing");
+    }
+    if (budget < 1 || budget > kMaxBlocks / 2) return fail(PR_EINVAL, "block budget out of range");
+    Buf small;
+    PR_TRY(small.alloc(512, s));
+    int32_t *d_thr = small.as<int32_t>();                               // [6]
+    int32_t *d_bounds = d_thr + 8;                                      // [12]
+    int32_t *d_rows = d_thr + 24;                                       // [16]
+    long long *d_edges = reinterpret_cast<long long *>(d_thr + 48);     // [16]
+    PR_CK(cudaMemcpyAsync(d_thr, thr, sizeof(int32_t) * kNumThr, cudaMemcpyHostToDevice, s));
+    k_bin_bounds<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), 0, n_ref, d_thr, kNumThr,
+                                  d_bounds);
+    k_bin_bounds<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), n_nd, n, d_thr, kNumThr,
+                                  d_bounds + kNumThr);
+    int32_t b[2 * kNumThr];
+    PR_CK(cudaMemcpyAsync(b, d_bounds, sizeof(b), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaStreamSynchronize(s));
+    int32_t rows[2 * kNumThr + 4];
+    for (int k = 0; k < 2 * kNumThr; k++) rows[k] = b[k];
+    rows[12] = 0;
+    rows[13] = n_ref;
+    rows[14] = n_nd;
+    rows[15] = n;
+    long long edges[16];
+    PR_CK(cudaMemcpyAsync(d_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, s));
+    k_range_edges<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_rows, 16, d_edges);
+    PR_CK(cudaMemcpyAsync(edges, d_edges, sizeof(edges), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaStreamSynchronize(s));
+    PR_CK(cudaGetLastError());
+    pr_graph T = {};  // plans are built into a scratch copy first: the graph keeps its bins on failure
+    for (int k = 0; k < kNumThr; k++) {
+        T.thr[k] = thr[k];
+        T.bound_ref[k] = b[k];
+        T.bound_d[k] = b[kNumThr + k];
+    }
+    for (int k = 0; k < 16; k++) T.edges_at[k] = edges[k];
+    T.block_budget = budget;
+    T.G = g->G;
+    build_plans(&T);
+    if (T.plan_all.nblocks > kMaxBlocks || T.plan_nd.nblocks > kMaxBlocks)
+        return fail(PR_EINVAL, "pull plan exceeds the partial-sum slots");
+    for (int k = 0; k < kNumThr; k++) {
+        g->thr[k] = T.thr[k];
+        g->bound_ref[k] = T.bound_ref[k];
+        g->bound_d[k] = T.bound_d[k];
+    }
+    for (int k = 0; k < 16; k++) g->edges_at[k] = T.edges_at[k];
+    g->block_budget = budget;
+    g->plan_nd = T.plan_nd;
+    g->plan_d = T.plan_d;
+    g->plan_all = T.plan_all;
+    return PR_OK;
 }
 
 }  // namespace pr
@@ -605,37 +666,11 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
         k_vertex_arrays<<<grid_for(n_nd, sms), kThreads, 0, s>>>(
             n_nd, g->out_off.as<int32_t>(), g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
             g->inv_deg64.as<double>(), g->inv_deg32.as<float>(), g->inv_degdf.as<float2>());
-    Buf indeg_int, dev_small;
+    Buf indeg_int;
     PR_TRY(indeg_int.alloc(sizeof(int32_t) * n, s));
-    PR_TRY(dev_small.alloc(1024, s));
     k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, g->perm.as<int32_t>(), indeg.as<int32_t>(),
                                            g->out_off.as<int32_t>(), indeg_int.as<int32_t>(), fact_cnt, maxes,
                                            m_d);
-    // pull-bin boundaries: binary searches in the in-degree sorted classes
-    for (int k = 0; k < kNumThr; k++) g->thr[k] = kDefaultThr[k];
-    g->block_budget = sms * 16;
-    int32_t *d_thr = dev_small.as<int32_t>();            // [6]
-    int32_t *d_bounds = d_thr + 8;                      // [12]
-    int32_t *d_rows = d_thr + 24;                       // [16]
-    long long *d_edges = reinterpret_cast<long long *>(d_thr + 48);  // [16]
-    PR_CK(cudaMemcpyAsync(d_thr, g->thr, sizeof(g->thr), cudaMemcpyHostToDevice, s));
-    k_bin_bounds<<<1, 32, 0, s>>>(indeg_int.as<int32_t>(), 0, n_ref, d_thr, kNumThr, d_bounds);
-    k_bin_bounds<<<1, 32, 0, s>>>(indeg_int.as<int32_t>(), n_nd, n, d_thr, kNumThr, d_bounds + kNumThr);
-    PR_CK(cudaMemcpyAsync(g->bound_ref, d_bounds, sizeof(int32_t) * kNumThr, cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaMemcpyAsync(g->bound_d, d_bounds + kNumThr, sizeof(int32_t) * kNumThr, cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaStreamSynchronize(s));
-    int32_t rows[2 * kNumThr + 4];
-    for (int k = 0; k < kNumThr; k++) {
-        rows[k] = g->bound_ref[k];
-        rows[kNumThr + k] = g->bound_d[k];
-    }
-    rows[12] = 0;
-    rows[13] = n_ref;
-    rows[14] = n_nd;
-    rows[15] = n;
-    PR_CK(cudaMemcpyAsync(d_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, s));
-    k_range_edges<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_rows, 16, d_edges);
-    PR_CK(cudaMemcpyAsync(g->edges_at, d_edges, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
     int32_t hnd[2] = {0, 0};
     PR_CK(cudaMemcpyAsync(&hnd[0], g->inr_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(&hnd[1], g->inu_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -645,12 +680,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_CK(cudaMemcpyAsync(&hu, fact_cnt, sizeof(hu), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(&hmd, m_d, sizeof(hmd), cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaEventRecord(e1, s));
     PR_CK(cudaStreamSynchronize(s));
-    float ms = 0;
-    PR_CK(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
 
     DevGraph &G = g->G;
     G.n = n;
@@ -673,9 +703,14 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     G.inv = g->inv.as<int32_t>();
     g->scan_nd_ref = hnd[0];
     g->scan_nd_unref = hnd[1];
-    build_plans(g);
-    if (g->plan_all.nblocks > kMaxBlocks || g->plan_nd.nblocks > kMaxBlocks)
-        return fail(PR_ECUDA, "internal: pull plan exceeds the partial-sum slots");
+    g->pull_ratio = 0.04;
+    PR_TRY(set_bins(g, kDefaultThr, sms * 16, s));
+    PR_CK(cudaEventRecord(e1, s));
+    PR_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    PR_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 
     pr_graph_info &I = g->info;
     I.n = n;

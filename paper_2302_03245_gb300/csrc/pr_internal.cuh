@@ -120,6 +120,7 @@ struct pr_graph {
     int32_t bound_ref[pr::kNumThr] = {}, bound_d[pr::kNumThr] = {};
     long long edges_at[2 * pr::kNumThr + 4] = {};
     int32_t block_budget = 0;
+    double pull_ratio = 0.04;  // AUTO push/pull switch used when a solve passes 0
     int64_t scan_nd_ref = 0, scan_nd_unref = 0;  // in-list entries of the non-dangling rows, per segment
     pr::Plan plan_nd{}, plan_d{}, plan_all{};
     // solver workspace (lazily allocated, reused across solves)
@@ -128,5 +129,8 @@ struct pr_graph {
 
 namespace pr {
 void build_plans(pr_graph *g);
+// pull bins from in-degree thresholds (non-increasing) and a block budget;
+// rebuilds every plan of g (on error g keeps its bins)
+pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t s);
 void destroy_workspace(pr_graph *g);
 }  // namespace pr

@@ -141,12 +141,14 @@ template <> struct GT<double> {
     static __device__ __forceinline__ A zero() { return 0.0; }
     static __device__ __forceinline__ A add(A a, double v) { return a + v; }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
+    static __device__ __forceinline__ A shfl_xor(A a, int o, int w) { return __shfl_xor_sync(0xffffffffu, a, o, w); }
 };
 template <> struct GT<float> {
     using A = float;
     static __device__ __forceinline__ A zero() { return 0.f; }
     static __device__ __forceinline__ A add(A a, float v) { return a + v; }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) { return __shfl_down_sync(0xffffffffu, a, o, w); }
+    static __device__ __forceinline__ A shfl_xor(A a, int o, int w) { return __shfl_xor_sync(0xffffffffu, a, o, w); }
 };
 template <> struct GT<float2> {
     using A = float2;
@@ -154,6 +156,9 @@ template <> struct GT<float2> {
     static __device__ __forceinline__ A add(A a, float2 v) { return df_add(a, v); }
     static __device__ __forceinline__ A shfl_down(A a, int o, int w) {
         return make_float2(__shfl_down_sync(0xffffffffu, a.x, o, w), __shfl_down_sync(0xffffffffu, a.y, o, w));
+    }
+    static __device__ __forceinline__ A shfl_xor(A a, int o, int w) {
+        return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o, w), __shfl_xor_sync(0xffffffffu, a.y, o, w));
     }
 };
 

@@ -674,7 +674,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     pr_opts opt{};
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
-    if (opt.pull_ratio <= 0) opt.pull_ratio = 0.04;
+    if (opt.pull_ratio <= 0) opt.pull_ratio = g->pull_ratio;
     if (opt.mode < 0 || opt.mode > 2) return fail(PR_EINVAL, "unknown mode");
     if (opt.xi_act < 0) return fail(PR_EINVAL, "xi_act must be >= 0");
     const bool use_graph = opt.use_graph >= 0;  // 0 = default (on); -1 = host-driven rounds

@@ -30,7 +30,9 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("pr_graph_create", "pr_solve", "pr_solve_ex", "pr_destroy", "pr_last_error"):
+    for required in ("pr_graph_create", "pr_solve", "pr_solve_ex", "pr_solve_batch", "pr_server_create",
+                     "pr_server_submit", "pr_server_poll", "pr_server_destroy", "pr_graph_autotune",
+                     "pr_destroy", "pr_last_error"):
         assert required in names
 
 
@@ -58,6 +60,7 @@ def test_struct_layouts_match_binding(prlib):
 int main(void){
  printf("%zu %zu %zu %zu %zu\n", sizeof(pr_stats), sizeof(pr_opts), sizeof(pr_graph_info), sizeof(pr_pvec), sizeof(pr_kernel_profile));
  printf("%zu %zu %zu\n", offsetof(pr_stats, ms), offsetof(pr_opts, trace_mode), offsetof(pr_graph_info, device_bytes));
+ printf("%zu %zu %zu %zu\n", sizeof(pr_tuning), offsetof(pr_tuning, pull_ratio), offsetof(pr_tuning, bin_rows), offsetof(pr_tuning, pull_blocks));
  return 0;}'''
     exe = os.path.join(ROOT, "tests", ".layout_probe")
     r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-x", "c", "-", "-o", exe], input=src,
@@ -72,6 +75,9 @@ int main(void){
                      ctypes.sizeof(prlib.pr_kernel_profile)]
     assert offs == [prlib.pr_stats.ms.offset, prlib.pr_opts.trace_mode.offset,
                     prlib.pr_graph_info.device_bytes.offset]
+    T = prlib.pr_tuning
+    assert list(map(int, lines[2].split())) == [ctypes.sizeof(T), T.pull_ratio.offset, T.bin_rows.offset,
+                                                T.pull_blocks.offset]
 
 
 @pytest.mark.parametrize("case", ["dup_free_but_bad_offsets", "range", "negative_n", "off0", "offn"])

@@ -157,3 +157,48 @@ def test_server_destroy_with_requests_in_flight(graphs):
     with pr.Server(1 << 32) as S2:
         out, st, status = S2.wait(S2.submit(hs[1], 0.85, 1e-10, pr.PR_DF64))
         assert status == pr.PR_OK
+
+
+@pytest.fixture(scope="module")
+def big():
+    g = gg.rmat(16, 8, dangling=0.15, unref=0.10, seed=31)
+    h = pr.Graph(g.n, g.m, *g.csr32())
+    assert h.info["n_nd"] >= (1 << 14)  # large enough for column groups
+    yield g, h
+    h.close()
+
+
+@pytest.mark.parametrize("prec", [pr.PR_FP32, pr.PR_DF64])
+def test_server_column_groups_match_alone(big, prec):
+    """Many requests on one large graph share gathers in column groups (more
+    requests than one group holds, different seeds, damping factors and
+    arrival times); each result equals the same solve alone."""
+    g, h = big
+    rng = np.random.default_rng(5 + prec)
+    reqs = []
+    for j in range(19):
+        c = (0.85, 0.7, 0.9)[j % 3]
+        if j % 5 == 4:
+            reqs.append((c, None, None))  # full PageRank in the mix
+        else:
+            k = int(rng.integers(1, 65))
+            idx = rng.choice(g.n, size=k, replace=False).astype(np.int32)
+            reqs.append((c, rng.uniform(0.5, 1.5, size=k), idx))
+    eps = 1e-10 if prec == pr.PR_DF64 else 1e-8
+    with pr.Server(1 << 34) as S:
+        first = [S.submit(h, c, eps, prec, p, pi) for (c, p, pi) in reqs[:11]]
+        _ = S.wait(first[0])  # the rest arrive while the others run
+        later = [S.submit(h, c, eps, prec, p, pi) for (c, p, pi) in reqs[11:]]
+        results = [_] + [S.wait(t) for t in first[1:] + later]
+    for (c, p, pi), (out, st, status) in zip(reqs, results):
+        assert status == pr.PR_OK
+        assert abs(out.sum() - 1.0) < 1e-12
+        alone, st1, s1 = h.solve(c, eps, pr.PR_IFP2, prec, p=p, p_idx=pi)
+        assert l1(out, alone) <= st["err_bound"] + st1["err_bound"] + 1e-12
+        truth = truth_of(g, c, p, pi)
+        assert l1(out, truth) <= st["err_bound"] + 1e-12, (l1(out, truth), st["err_bound"])
+        if prec == pr.PR_DF64:
+            # the same arithmetic as a pull-only solve alone (up to the order of the sums)
+            alone_pull, st2, _ = h.solve(c, eps, pr.PR_IFP2, prec, p=p, p_idx=pi, opts=dict(mode=pr.PR_MODE_PULL))
+            assert l1(out, alone_pull) <= 1e-12
+            assert abs(st["rounds"] - st2["rounds"]) <= 1
