@@ -41,7 +41,8 @@ typedef enum {
     PR_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error) */
     PR_ENOTCONV = 4, /* round/iteration cap reached, or no vertex could be activated;
                         `out` still holds the best-effort result */
-    PR_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+    PR_ETIMEOUT = 5, /* a bounded device-side wait ran out (reserved: no kernel of this
+                        library waits on another block, rank or flag) */
     PR_EAGAIN = 6,   /* server: over the HBM budget and the queue is full */
     PR_EBUSY = 7     /* server: request not finished yet */
 } pr_status;
@@ -62,8 +63,9 @@ typedef enum {
                     residual from the reserve, and double-float rounds finish the
                     solve (not in the paper; the identity used is that of Eq. 4) */
     PR_DF64 = 2  /* residual, reserve and pushed mass as double-float pairs
-                    (hi + lo floats, 48-bit significand, FP32 instructions only);
-                    final sums and the output in FP64 */
+                    (hi + lo floats, 48-bit significand, FP32 instructions); push
+                    rounds add into an FP64 inbox with double atomics, folded into
+                    the pairs at the next activation; final sums and the output in FP64 */
 } pr_prec;
 
 typedef enum {
@@ -133,7 +135,7 @@ typedef struct {
     int32_t max_rounds;   /* 0 => 100000 */
     int32_t mode;         /* pr_mode */
     double pull_ratio;    /* AUTO: pull when the frontier's out-edges >= pull_ratio * m;
-                             0 => 0.04 */
+                             0 => the graph's pr_tuning value (0.04 unless set or autotuned) */
     int32_t use_graph;    /* 0 or 1 => rounds run inside a CUDA graph with a device-side
                              while loop (no host sync per round); -1 => host-driven rounds */
     int32_t trace_cap;    /* length of the host trace arrays below (may be 0) */
@@ -330,9 +332,10 @@ pr_status pr_solve_batch(pr_graph *const *gs, int32_t count, const double *c, co
  *   (arguments, p, a request larger than the whole budget), PR_EAGAIN
  *   (queue full: retry later), PR_ENOMEM.
  * pr_server_poll: PR_EBUSY while the request runs.  Once it has finished:
- *   out[g n] (host, may be NULL) receives the PageRank in the caller's ids
- *   (sum 1, FP64), st (may be NULL) the report (ms = submit to finish), and
- *   the ticket is released: PR_OK, or PR_ENOTCONV (round cap reached, or no
+ *   out[g n] (host or device pointer, may be NULL) receives the PageRank in
+ *   the caller's ids (sum 1, FP64) -- the result waits on the device until
+ *   this call copies it --, st (may be NULL) the report (ms = submit to
+ *   finish), and the ticket is released: PR_OK, or PR_ENOTCONV (round cap reached, or no
  *   vertex left above the activation threshold before R <= eps; out is
  *   written), or the error that stopped the server's thread (PR_ECUDA,
  *   PR_ENOMEM; out is not written).  PR_EINVAL for an unknown or released
@@ -345,6 +348,24 @@ pr_status pr_server_submit(pr_server *s, pr_graph *g, double c, double eps, pr_p
                            int64_t *ticket);
 pr_status pr_server_poll(pr_server *s, int64_t ticket, double *out, pr_stats *st);
 void pr_server_destroy(pr_server *s);
+
+/*
+ * Server counters since pr_server_create (thread-safe snapshot).  The ms_*
+ * fields are host wall time of the server thread per stage, launches and the
+ * synchronisations that end them included: admission (allocation, state
+ * init, joining a column group), rounds (round launches of groups and of the
+ * tile engine, and the stop-flag read), correction (FP32 form), finish
+ * (phase 2, normalisation, copy-out).
+ */
+typedef struct {
+    int64_t submitted, finished;      /* requests */
+    int64_t steps;                    /* loop iterations that had work */
+    int64_t group_launches;           /* column-group round kernels launched */
+    int64_t tile_launches;            /* tile-engine phase kernels launched */
+    int32_t groups, active;           /* live column groups; requests admitted, not finished */
+    double ms_admit, ms_rounds, ms_correct, ms_finish;
+} pr_server_stats;
+pr_status pr_server_get_stats(pr_server *s, pr_server_stats *st);
 
 /* Release a graph and its workspace (NULL is ignored). */
 void pr_destroy(pr_graph *g);

@@ -80,6 +80,16 @@ class pr_graph_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("finished", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("group_launches", ctypes.c_int64), ("tile_launches", ctypes.c_int64), ("groups", ctypes.c_int32),
+                ("active", ctypes.c_int32), ("ms_admit", ctypes.c_double), ("ms_rounds", ctypes.c_double),
+                ("ms_correct", ctypes.c_double), ("ms_finish", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class pr_tuning(ctypes.Structure):
     _fields_ = [("pull_thr", ctypes.c_int32 * 6), ("block_budget", ctypes.c_int32), ("pad0", ctypes.c_int32),
                 ("pull_ratio", ctypes.c_double), ("bin_rows", ctypes.c_int32 * 7), ("pull_blocks", ctypes.c_int32)]
@@ -139,6 +149,8 @@ def lib() -> ctypes.CDLL:
         L.pr_server_poll.restype = ctypes.c_int
         L.pr_server_destroy.argtypes = [P]
         L.pr_server_destroy.restype = None
+        L.pr_server_get_stats.argtypes = [P, ctypes.POINTER(pr_server_stats)]
+        L.pr_server_get_stats.restype = ctypes.c_int
         L.pr_last_error.restype = ctypes.c_char_p
         L.pr_version.restype = ctypes.c_char_p
         L.pr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
@@ -370,17 +382,26 @@ def pr_server_submit(server, g, c: float, eps: float, prec: int = PR_DF64, p=Non
     return t.value
 
 
-def pr_server_poll(server, ticket: int, n: int):
+def pr_server_poll(server, ticket: int, n: int, out=None):
     """Wraps pr_server_poll.  Returns None while the request runs (PR_EBUSY), else
-    (out, stats dict, status) with status PR_OK or PR_ENOTCONV; raises on errors."""
-    out = np.empty(n, dtype=np.float64)
+    (out, stats dict, status) with status PR_OK or PR_ENOTCONV; raises on errors.
+    out: None (a new host array), a float64 numpy array, or a float64 torch tensor
+    (host or CUDA)."""
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
     st = pr_stats()
-    status = lib().pr_server_poll(server, int(ticket), out.ctypes.data, ctypes.byref(st))
+    status = lib().pr_server_poll(server, int(ticket), _ptr(out), ctypes.byref(st))
     if status == PR_EBUSY:
         return None
     if status not in (PR_OK, PR_ENOTCONV):
         _check(status)
     return out, st.as_dict(), status
+
+
+def pr_server_get_stats(server) -> dict:
+    st = pr_server_stats()
+    _check(lib().pr_server_get_stats(server, ctypes.byref(st)))
+    return st.as_dict()
 
 
 def pr_server_destroy(server) -> None:
@@ -402,22 +423,25 @@ class Server:
         self._n[t] = pr_graph_get_info(h)["n"]
         return t
 
-    def poll(self, ticket):
-        r = pr_server_poll(self.h, ticket, self._n[ticket])
+    def poll(self, ticket, out=None):
+        r = pr_server_poll(self.h, ticket, self._n[ticket], out)
         if r is not None:
             self._n.pop(ticket, None)
         return r
 
-    def wait(self, ticket, timeout_s: float = 120.0, sleep_s: float = 0.0005):
+    def wait(self, ticket, timeout_s: float = 120.0, sleep_s: float = 0.0005, out=None):
         import time
         t0 = time.monotonic()
         while True:
-            r = self.poll(ticket)
+            r = self.poll(ticket, out)
             if r is not None:
                 return r
             if time.monotonic() - t0 > timeout_s:
                 raise TimeoutError(f"request {ticket} not finished after {timeout_s} s")
             time.sleep(sleep_s)
+
+    def stats(self) -> dict:
+        return pr_server_get_stats(self.h)
 
     def close(self):
         pr_server_destroy(self.h)

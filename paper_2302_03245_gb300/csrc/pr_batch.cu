@@ -112,7 +112,7 @@ __device__ __forceinline__ void push_worker(const DevGraph &G, const Ctl *ctl, c
                 const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
                 const int e0 = G.out_off[i];
                 const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-                for (int e = e0; e < e1; e++) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+                for (int e = e0; e < e1; e++) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
             }
         } else {  // a warp (bin 1) or the block (bin 2) per vertex
             const int lanes = b == 1 ? 32 : (int)blockDim.x;
@@ -126,7 +126,7 @@ __device__ __forceinline__ void push_worker(const DevGraph &G, const Ctl *ctl, c
                 const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
                 const int e0 = G.out_off[i];
                 const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-                for (int e = e0 + lane; e < e1; e += lanes) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+                for (int e = e0 + lane; e < e1; e += lanes) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
             }
         }
     }
@@ -228,9 +228,11 @@ __global__ void k_batch_init(const BProb *probs, const Tile *vt, int nvt) {
         const BProb &P = probs[tl.prob];
         T *x = static_cast<T *>(P.B.x);
         T *r = static_cast<T *>(P.B.r);
+        double *din = P.B.din;
         for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
             x[i] = ST<T>::zero();
             r[i] = ST<T>::p(P.ctl, P.pv, i);
+            if (din) din[i] = 0.0;
         }
     }
 }
@@ -277,10 +279,23 @@ __global__ void k_batch_64_to_df(const BProb *probs, const BProb *probs_df, cons
         const BProb &Q = probs_df[tl.prob];
         float2 *x = static_cast<float2 *>(Q.B.x);
         float2 *r = static_cast<float2 *>(Q.B.r);
+        double *din = Q.B.din;
         for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
             x[i] = df_from_d(P.x64[i]);
             r[i] = df_from_d(P.r64[i]);
+            din[i] = 0.0;
         }
+    }
+}
+
+// double-float inboxes folded into r (IFP1 dangling rows: pushed into, never activated)
+__global__ void k_batch_fold(const BProb *probs, const Tile *vt, int nvt) {
+    for (int k = blockIdx.x; k < nvt; k += gridDim.x) {
+        const Tile tl = vt[k];
+        const BProb &P = probs[tl.prob];
+        float2 *r = static_cast<float2 *>(P.B.r);
+        for (int i = max(tl.lo, P.G.n_nd) + (int)threadIdx.x; i < tl.hi; i += blockDim.x)
+            ST<float2>::fold(r, P.B.din, i);
     }
 }
 
@@ -416,10 +431,11 @@ struct Arena {  // bump allocator over one device buffer (256-byte aligned slice
 
 struct StateOffsets {
     size_t x, r, vbuf, w0, w1, bins, q;
+    size_t din;  // double-float state: push-round inbox (FP64); else unused
 };
 
-StateOffsets take_state(Arena &A, size_t n, size_t nnd, size_t t_bytes, size_t v_bytes) {
-    StateOffsets o;
+StateOffsets take_state(Arena &A, size_t n, size_t nnd, size_t t_bytes, size_t v_bytes, bool inbox) {
+    StateOffsets o{};
     o.x = A.take(t_bytes * n);
     o.r = A.take(t_bytes * n);
     o.vbuf = A.take(t_bytes * nnd);
@@ -427,12 +443,13 @@ StateOffsets take_state(Arena &A, size_t n, size_t nnd, size_t t_bytes, size_t v
     o.w1 = A.take(v_bytes * nnd);
     o.bins = A.take(sizeof(int32_t) * 3 * nnd);
     o.q = A.take(v_bytes * n);
+    o.din = inbox ? A.take(sizeof(double) * n) : 0;
     return o;
 }
 
 RoundBuf round_buf(const Arena &A, const StateOffsets &o) {
     return RoundBuf{A.at<char>(o.x), A.at<char>(o.r), A.at<char>(o.vbuf), {A.at<char>(o.w0), A.at<char>(o.w1)},
-                    A.at<int32_t>(o.bins)};
+                    A.at<int32_t>(o.bins), o.din ? A.at<double>(o.din) : nullptr};
 }
 
 template <typename T, bool IFP2>
@@ -537,9 +554,9 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     std::vector<size_t> off_out(count), off_x64(count), off_r64(count), off_q64(count);
     for (int k = 0; k < count; k++) {
         const size_t n = gs[k]->G.n, nnd = std::max(gs[k]->G.n_nd, 1);
-        so[k] = take_state(A, n, nnd, tb, vb);
+        so[k] = take_state(A, n, nnd, tb, vb, prec == PR_DF64);
         if (fp32) {
-            so_df[k] = take_state(A, n, nnd, sizeof(float2), sizeof(float2));
+            so_df[k] = take_state(A, n, nnd, sizeof(float2), sizeof(float2), true);
             off_x64[k] = A.take(sizeof(double) * n);
             off_r64[k] = A.take(sizeof(double) * n);
             off_q64[k] = A.take(sizeof(float2) * n);
@@ -667,6 +684,7 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
             k_batch_phase2_q<float2><<<sgrid, kThreads, 0, s>>>(d_fin, d_vt, nvt);
             k_batch_phase2<float2><<<dgrid, kThreads, 0, s>>>(d_fin, d_dt, ndt);
         }
+        if (!ifp2) k_batch_fold<<<sgrid, kThreads, 0, s>>>(d_fin, d_vt, nvt);
         k_batch_fin_sum<float2><<<sgrid, kThreads, 0, s>>>(d_fin, d_vt, nvt, kind, sl.R);
         k_batch_fin_write<float2><<<sgrid, kThreads, 0, s>>>(d_fin, d_vt, nvt, kind);
     }
@@ -812,7 +830,8 @@ struct SReq {
     int32_t rounds_first = 0;
     void *group = nullptr;          // column group holding the request's rounds (nullptr: tile engine)
     int gcol = -1;
-    std::vector<double> result;
+    double *dout = nullptr;         // normalised result (device, own allocation: outlives the state)
+    size_t out_bytes = 0;
     pr_stats st{};
     std::chrono::steady_clock::time_point t_submit;
     template <typename X> X *at(size_t off) const { return reinterpret_cast<X *>(static_cast<char *>(mem) + off); }
@@ -832,7 +851,7 @@ size_t layout(SReq &q) {
     const bool fp32 = q.prec == PR_FP32;
     const size_t tb = fp32 ? sizeof(float) : sizeof(float2), vb = fp32 ? sizeof(float) : sizeof(float2);
     auto state = [&](size_t t_bytes, size_t v_bytes) {
-        StateOffsets o;
+        StateOffsets o{};
         o.x = take(t_bytes * n);
         o.r = take(t_bytes * n);
         o.vbuf = take(t_bytes * nnd);
@@ -840,6 +859,7 @@ size_t layout(SReq &q) {
         o.w1 = take(v_bytes * nnd);
         o.bins = take(sizeof(int32_t) * 3 * nnd);
         o.q = take(v_bytes * n);
+        if (t_bytes == sizeof(float2)) o.din = take(sizeof(double) * n);  // double-float state only
         return o;
     };
     q.off_ctl = take(sizeof(Ctl));
@@ -851,7 +871,6 @@ size_t layout(SReq &q) {
         q.off_q64 = take(sizeof(float2) * n);
         q.off_p64 = take(sizeof(double) * n);
     }
-    q.off_out = take(sizeof(double) * n);
     q.off_sidx = take(sizeof(int32_t) * std::max(q.nnz, 1));
     q.off_sval = take(sizeof(double) * std::max(q.nnz, 1));
     return used;
@@ -859,7 +878,7 @@ size_t layout(SReq &q) {
 
 RoundBuf req_buf(const SReq &q, const StateOffsets &o) {
     return RoundBuf{q.at<char>(o.x), q.at<char>(o.r), q.at<char>(o.vbuf), {q.at<char>(o.w0), q.at<char>(o.w1)},
-                    q.at<int32_t>(o.bins)};
+                    q.at<int32_t>(o.bins), o.din ? q.at<double>(o.din) : nullptr};
 }
 
 }  // namespace
@@ -881,10 +900,18 @@ struct ServerImpl {
         }
     };
     std::vector<Group *> groups;
+    pr_server_stats stats{};  // written by the server thread under mu
+    using Clock = std::chrono::steady_clock;
+    void add_ms(double pr_server_stats::*field, Clock::time_point t0) {
+        const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+        std::lock_guard<std::mutex> lock(mu);
+        stats.*field += ms;
+    }
     std::unordered_map<uint64_t, int> inflight;  // requests per graph (uid), submitted and not finished
     int32_t group_min_rows = 1 << 14;            // smaller graphs run in the tile engine
     Buf d_gctl, d_gstat;
     cudaStream_t s = nullptr;
+    cudaStream_t ps = nullptr;  // copies of results to callers (pr_server_poll)
     int device = 0, sms = 0;
     size_t budget = 0, used = 0;
     std::mutex mu;
@@ -928,7 +955,7 @@ struct ServerImpl {
         const StateOffsets &o = (fmt == 1 && q->prec == PR_FP32) ? q->s_df : q->s_main;
         P.B = req_buf(*q, o);
         P.q = q->at<char>(o.q);
-        P.out = q->at<double>(q->off_out);
+        P.out = q->dout;
         if (q->prec == PR_FP32) {
             P.x64 = q->at<double>(q->off_x64);
             P.r64 = q->at<double>(q->off_r64);
@@ -965,8 +992,8 @@ struct ServerImpl {
             hp.push_back(P);
         }
         const size_t pb = sizeof(BProb) * std::max<size_t>(hp.size(), 1), tb = sizeof(Tile) * std::max<size_t>(ht.size(), 1);
-        if (dp.bytes < pb) PR_TRY(dp.alloc(pb * 2, s));
-        if (dt.bytes < tb) PR_TRY(dt.alloc(tb * 2, s));
+        if (dp.bytes < pb) PR_TRY(dp.alloc_async(pb * 2, s));
+        if (dt.bytes < tb) PR_TRY(dt.alloc_async(tb * 2, s));
         if (!hp.empty()) PR_CK(cudaMemcpyAsync(dp.p, hp.data(), sizeof(BProb) * hp.size(), cudaMemcpyHostToDevice, s));
         if (!ht.empty()) PR_CK(cudaMemcpyAsync(dt.p, ht.data(), sizeof(Tile) * ht.size(), cudaMemcpyHostToDevice, s));
         return PR_OK;
@@ -974,7 +1001,9 @@ struct ServerImpl {
 
     pr_status admit_one(SReq *q) {
         q->bytes = layout(*q);
+        q->out_bytes = sizeof(double) * (size_t)q->g->G.n;
         PR_CK(cudaMallocAsync(&q->mem, q->bytes, s));
+        PR_CK(cudaMallocAsync(reinterpret_cast<void **>(&q->dout), q->out_bytes, s));
         const DevGraph &G = q->g->G;
         Ctl h{};
         h.c = q->c;
@@ -994,6 +1023,8 @@ struct ServerImpl {
         h.unref_active = 1;
         fill_formats(h);
         PR_CK(cudaMemcpyAsync(q->at<Ctl>(q->off_ctl), &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        for (const StateOffsets *o : {&q->s_main, &q->s_df})  // double-float inboxes start empty
+            if (o->din) PR_CK(cudaMemsetAsync(q->at<char>(o->din), 0, sizeof(double) * G.n, s));
         double *p64 = q->prec == PR_FP32 ? q->at<double>(q->off_p64) : nullptr;
         const int grid = (int)std::min<int64_t>((G.n + kThreads - 1) / kThreads, (int64_t)sms * 8);
         const int32_t *sidx = q->at<int32_t>(q->off_sidx);
@@ -1038,7 +1069,7 @@ struct ServerImpl {
             hdf[k].q = set[k]->at<char>(set[k]->s_df.q);
         }
         Buf dfp;
-        PR_TRY(dfp.alloc(sizeof(BProb) * hdf.size(), s));
+        PR_TRY(dfp.alloc_async(sizeof(BProb) * hdf.size(), s));
         PR_CK(cudaMemcpyAsync(dfp.p, hdf.data(), sizeof(BProb) * hdf.size(), cudaMemcpyHostToDevice, s));
         const int nv = (int)hv.size(), nr = (int)hr.size();
         const int g1 = (int)std::min<int64_t>(std::max(nv, 1), (int64_t)sms * 16);
@@ -1048,7 +1079,7 @@ struct ServerImpl {
         k_batch_correct<<<g2, kThreads, 0, s>>>(dp, d_ftiles.as<Tile>(), nr);
         k_batch_64_to_df<<<g1, kThreads, 0, s>>>(dp, dfp.as<BProb>(), d_fvtiles.as<Tile>(), nv);
         Buf bcb;
-        PR_TRY(bcb.alloc(sizeof(BCtl), s));
+        PR_TRY(bcb.alloc_async(sizeof(BCtl), s));
         k_batch_reset<<<((int)set.size() + kThreads - 1) / kThreads, kThreads, 0, s>>>(dfp.as<BProb>(), (int)set.size(),
                                                                                      bcb.as<BCtl>());
         PR_CK(cudaStreamSynchronize(s));
@@ -1078,16 +1109,16 @@ struct ServerImpl {
             P.nd = (int)T.dang.size();
             hp.push_back(P);
         }
-        if (d_fprobs.bytes < sizeof(BProb) * hp.size()) PR_TRY(d_fprobs.alloc(sizeof(BProb) * hp.size() * 2, s));
+        if (d_fprobs.bytes < sizeof(BProb) * hp.size()) PR_TRY(d_fprobs.alloc_async(sizeof(BProb) * hp.size() * 2, s));
         if (d_fvtiles.bytes < sizeof(Tile) * std::max<size_t>(hv.size(), 1))
-            PR_TRY(d_fvtiles.alloc(sizeof(Tile) * std::max<size_t>(hv.size(), 1) * 2, s));
+            PR_TRY(d_fvtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hv.size(), 1) * 2, s));
         if (d_fdtiles.bytes < sizeof(Tile) * std::max<size_t>(hd.size(), 1))
-            PR_TRY(d_fdtiles.alloc(sizeof(Tile) * std::max<size_t>(hd.size(), 1) * 2, s));
+            PR_TRY(d_fdtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hd.size(), 1) * 2, s));
         PR_CK(cudaMemcpyAsync(d_fprobs.p, hp.data(), sizeof(BProb) * hp.size(), cudaMemcpyHostToDevice, s));
         PR_CK(cudaMemcpyAsync(d_fvtiles.p, hv.data(), sizeof(Tile) * hv.size(), cudaMemcpyHostToDevice, s));
         if (!hd.empty()) PR_CK(cudaMemcpyAsync(d_fdtiles.p, hd.data(), sizeof(Tile) * hd.size(), cudaMemcpyHostToDevice, s));
         const int nv = (int)hv.size(), nd = (int)hd.size();
-        if (d_slots.bytes < sizeof(double) * std::max(nv, 1)) PR_TRY(d_slots.alloc(sizeof(double) * std::max(nv, 1) * 2, s));
+        if (d_slots.bytes < sizeof(double) * std::max(nv, 1)) PR_TRY(d_slots.alloc_async(sizeof(double) * std::max(nv, 1) * 2, s));
         const int g1 = (int)std::min<int64_t>(std::max(nv, 1), (int64_t)sms * 16);
         const int g2 = (int)std::min<int64_t>(std::max(nd, 1), (int64_t)sms * 16);
         const BProb *dp = d_fprobs.as<BProb>();
@@ -1097,12 +1128,8 @@ struct ServerImpl {
         k_batch_fin_sum<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2, d_slots.as<double>());
         k_batch_fin_write<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2);
         std::vector<Ctl> hc(set.size());
-        for (size_t k = 0; k < set.size(); k++) {
-            set[k]->result.resize(set[k]->g->G.n);
-            PR_CK(cudaMemcpyAsync(set[k]->result.data(), set[k]->at<double>(set[k]->off_out),
-                                  sizeof(double) * set[k]->g->G.n, cudaMemcpyDeviceToHost, s));
+        for (size_t k = 0; k < set.size(); k++)  // results stay on the device until polled
             PR_CK(cudaMemcpyAsync(&hc[k], set[k]->at<Ctl>(set[k]->off_ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        }
         PR_CK(cudaStreamSynchronize(s));
         PR_CK(cudaGetLastError());
         const auto now = std::chrono::steady_clock::now();
@@ -1222,9 +1249,12 @@ struct ServerImpl {
     pr_status step_groups(int phases) {
         std::vector<std::pair<Group *, int>> cols;
         std::vector<Ctl *> ptrs;
+        const auto t_rounds = Clock::now();
+        int64_t launched = 0;
         for (Group *G : groups) {
             if (!G->live()) continue;
             for (int k = 0; k < phases; k++) PR_TRY(group_round(G->g, G->D, G->fmt, G->next_launch++, s));
+            launched += phases;
             for (int k = 0; k < group_columns(G->fmt); k++)
                 if (G->col[k]) {
                     cols.emplace_back(G, k);
@@ -1233,8 +1263,8 @@ struct ServerImpl {
         }
         if (cols.empty()) return PR_OK;
         const int cnt = (int)cols.size();
-        if (d_gctl.bytes < sizeof(Ctl *) * cnt) PR_TRY(d_gctl.alloc(sizeof(Ctl *) * cnt * 2, s));
-        if (d_gstat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_gstat.alloc(sizeof(ReqStat) * cnt * 2, s));
+        if (d_gctl.bytes < sizeof(Ctl *) * cnt) PR_TRY(d_gctl.alloc_async(sizeof(Ctl *) * cnt * 2, s));
+        if (d_gstat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_gstat.alloc_async(sizeof(ReqStat) * cnt * 2, s));
         PR_CK(cudaMemcpyAsync(d_gctl.p, ptrs.data(), sizeof(Ctl *) * cnt, cudaMemcpyHostToDevice, s));
         k_gather_ctls<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_gctl.as<Ctl *>(), cnt,
                                                                            d_gstat.as<ReqStat>());
@@ -1242,6 +1272,11 @@ struct ServerImpl {
         PR_CK(cudaMemcpyAsync(hs.data(), d_gstat.p, sizeof(ReqStat) * cnt, cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
         PR_CK(cudaGetLastError());
+        add_ms(&pr_server_stats::ms_rounds, t_rounds);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            stats.group_launches += launched;
+        }
         std::vector<SReq *> to_correct, to_finish;
         std::vector<int> fin_fmt;
         std::vector<Group *> touched;
@@ -1266,7 +1301,9 @@ struct ServerImpl {
             }
         }
         if (!to_correct.empty()) {
+            const auto t0 = Clock::now();
             PR_TRY(correct(to_correct));
+            add_ms(&pr_server_stats::ms_correct, t0);
             for (SReq *q : to_correct) {
                 q->stage = 2;
                 act[1].push_back(q);
@@ -1274,7 +1311,9 @@ struct ServerImpl {
             dirty[1] = true;
         }
         if (!to_finish.empty()) {
+            const auto t0 = Clock::now();
             PR_TRY(finish(to_finish, fin_fmt));
+            add_ms(&pr_server_stats::ms_finish, t0);
             complete(to_finish);
         }
         for (Group *G : touched)
@@ -1285,6 +1324,7 @@ struct ServerImpl {
     // finished requests: results are on the host; free their budget share
     void complete(const std::vector<SReq *> &done) {
         std::lock_guard<std::mutex> lock(mu);
+        stats.finished += (int64_t)done.size();
         for (SReq *q : done) {
             q->stage = 3;
             used -= q->bytes;
@@ -1301,13 +1341,14 @@ struct ServerImpl {
             std::lock_guard<std::mutex> lock(mu);
             while (!queue.empty()) {
                 SReq *q = queue.front();
-                const size_t need = layout(*q);
+                const size_t need = layout(*q) + sizeof(double) * (size_t)q->g->G.n;
                 if (used + need > budget && (any_active() || !adm.empty())) break;
                 queue.pop_front();
                 used += need;
                 adm.push_back(q);
             }
         }
+        const auto t_adm = Clock::now();
         for (SReq *q : adm) {
             PR_TRY(admit_one(q));
             q->stage = 1;
@@ -1315,6 +1356,11 @@ struct ServerImpl {
             const int f = q->prec == PR_FP32 ? 0 : 1;
             act[f].push_back(q);
             dirty[f] = true;
+        }
+        if (!adm.empty()) add_ms(&pr_server_stats::ms_admit, t_adm);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            stats.steps++;
         }
         // a few rounds of every request, per state format (groups first)
         constexpr int kPhases = 4;
@@ -1327,10 +1373,10 @@ struct ServerImpl {
             if (dirty[f]) {
                 PR_TRY(upload(act[f], f, 0, d_probs[f], d_tiles[f], hp, ht));
                 ntiles[f] = (int)ht.size();
-                if (!d_bc[f].p) PR_TRY(d_bc[f].alloc(sizeof(BCtl), s));
+                if (!d_bc[f].p) PR_TRY(d_bc[f].alloc_async(sizeof(BCtl), s));
                 PR_CK(cudaMemsetAsync(d_bc[f].p, 0, sizeof(BCtl), s));
                 const size_t sb = (sizeof(double) * 2 + sizeof(long long) * 2) * std::max(ntiles[f], 1);
-                if (d_slots.bytes < sb) PR_TRY(d_slots.alloc(sb * 2, s));
+                if (d_slots.bytes < sb) PR_TRY(d_slots.alloc_async(sb * 2, s));
                 dirty[f] = false;
             }
             const int nt = ntiles[f];
@@ -1338,6 +1384,11 @@ struct ServerImpl {
             BSlots sl{base, reinterpret_cast<long long *>(base + nt), reinterpret_cast<long long *>(base + 2 * nt),
                       reinterpret_cast<int *>(base + 3 * nt)};
             const int grid = sms * 6;
+            const auto t_tile = Clock::now();
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                stats.tile_launches += kPhases;
+            }
             for (int k = 0; k < kPhases; k++) {
                 if (f == 0)
                     k_batch_phase<float, true><<<grid, kThreads, 0, s>>>(d_probs[f].as<BProb>(), d_tiles[f].as<Tile>(),
@@ -1348,13 +1399,14 @@ struct ServerImpl {
             }
             // which requests stopped
             const int cnt = (int)act[f].size();
-            if (d_stat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_stat.alloc(sizeof(ReqStat) * cnt * 2, s));
+            if (d_stat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_stat.alloc_async(sizeof(ReqStat) * cnt * 2, s));
             k_gather_status<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_probs[f].as<BProb>(), cnt,
                                                                                  d_stat.as<ReqStat>());
             std::vector<ReqStat> hs(cnt);
             PR_CK(cudaMemcpyAsync(hs.data(), d_stat.p, sizeof(ReqStat) * cnt, cudaMemcpyDeviceToHost, s));
             PR_CK(cudaStreamSynchronize(s));
             PR_CK(cudaGetLastError());
+            add_ms(&pr_server_stats::ms_rounds, t_tile);
             std::vector<SReq *> keep, to_correct, to_finish;
             std::vector<int> fin_fmt;
             for (int k = 0; k < cnt; k++) {
@@ -1374,7 +1426,9 @@ struct ServerImpl {
                 dirty[f] = true;
             }
             if (!to_correct.empty()) {
+                const auto t0 = Clock::now();
                 PR_TRY(correct(to_correct));
+                add_ms(&pr_server_stats::ms_correct, t0);
                 for (SReq *q : to_correct) {
                     q->stage = 2;
                     act[1].push_back(q);
@@ -1382,7 +1436,9 @@ struct ServerImpl {
                 dirty[1] = true;
             }
             if (!to_finish.empty()) {
+                const auto t0 = Clock::now();
                 PR_TRY(finish(to_finish, fin_fmt));
+                add_ms(&pr_server_stats::ms_finish, t0);
                 complete(to_finish);
             }
         }
@@ -1424,8 +1480,11 @@ struct ServerImpl {
                     q->status = st;
                     q->group = nullptr;
                     if (q->mem) cudaFreeAsync(q->mem, s);
+                    if (q->dout) cudaFreeAsync(q->dout, s);
                     q->mem = nullptr;
-                    used -= q->bytes;
+                    q->dout = nullptr;
+                    used -= q->bytes + q->out_bytes;
+                    q->out_bytes = 0;
                     auto it = inflight.find(q->g->uid);
                     if (it != inflight.end() && --it->second <= 0) inflight.erase(it);
                 }
@@ -1457,6 +1516,11 @@ extern "C" pr_status pr_server_create(size_t hbm_budget_bytes, void *cuda_stream
     if (e != cudaSuccess) {
         delete S;
         return cuda_fail(e, "pr_server_create");
+    }
+    e = cudaStreamCreateWithFlags(&I.ps, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "pr_server_create (copy stream)");
     }
     I.th = std::thread([&I] { I.loop(); });
     *out = S;
@@ -1520,6 +1584,7 @@ extern "C" pr_status pr_server_submit(pr_server *S, pr_graph *g, double c, doubl
     I.reqs[q->ticket] = q;
     I.queue.push_back(q);
     I.inflight[g->uid]++;
+    I.stats.submitted++;
     *ticket = q->ticket;
     I.cv.notify_all();
     return PR_OK;
@@ -1528,20 +1593,51 @@ extern "C" pr_status pr_server_submit(pr_server *S, pr_graph *g, double c, doubl
 extern "C" pr_status pr_server_poll(pr_server *S, int64_t ticket, double *out, pr_stats *st) {
     if (!S) return fail(PR_EINVAL, "pr_server_poll: NULL server");
     ServerImpl &I = S->impl;
-    std::lock_guard<std::mutex> lock(I.mu);
-    auto it = I.reqs.find(ticket);
-    if (it == I.reqs.end()) return fail(PR_EINVAL, "pr_server_poll: unknown ticket");
-    SReq *q = it->second;
-    if (q->stage != 3) return PR_EBUSY;
-    const pr_status status = q->status;
-    if (status == PR_OK || status == PR_ENOTCONV) {
-        if (out) std::memcpy(out, q->result.data(), sizeof(double) * q->result.size());
-        if (st) *st = q->st;
+    SReq *q = nullptr;
+    std::string msg;
+    {
+        std::lock_guard<std::mutex> lock(I.mu);
+        auto it = I.reqs.find(ticket);
+        if (it == I.reqs.end()) return fail(PR_EINVAL, "pr_server_poll: unknown ticket");
+        if (it->second->stage != 3) return PR_EBUSY;
+        q = it->second;
+        I.reqs.erase(it);
+        msg = I.loop_msg;
     }
-    I.reqs.erase(it);
-    const std::string msg = I.loop_msg;
+    // the result was completed (and the server's stream synchronised) before
+    // the request was marked done: copy it on the copy stream, outside the lock
+    const pr_status status = q->status;
+    pr_status ret = status;
+    if (q->dout) {
+        int old = -1;
+        cudaGetDevice(&old);
+        if (old != I.device) cudaSetDevice(I.device);
+        cudaError_t e = cudaSuccess;
+        if (out && (status == PR_OK || status == PR_ENOTCONV))
+            e = cudaMemcpyAsync(out, q->dout, q->out_bytes, cudaMemcpyDefault, I.ps);
+        if (e == cudaSuccess) e = cudaFreeAsync(q->dout, I.ps);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(I.ps);
+        if (old >= 0 && old != I.device) cudaSetDevice(old);
+        if (e != cudaSuccess) ret = cuda_fail(e, "pr_server_poll (result copy)");
+        std::lock_guard<std::mutex> lock(I.mu);
+        I.used -= q->out_bytes;
+    }
+    if (st && (status == PR_OK || status == PR_ENOTCONV)) *st = q->st;
     delete q;
+    if (ret == PR_ECUDA) return ret;
     if (status != PR_OK) return fail(status, msg.empty() ? "request did not converge" : msg);
+    return PR_OK;
+}
+
+extern "C" pr_status pr_server_get_stats(pr_server *S, pr_server_stats *out) {
+    if (!S || !out) return fail(PR_EINVAL, "pr_server_get_stats: NULL argument");
+    ServerImpl &I = S->impl;
+    std::lock_guard<std::mutex> lock(I.mu);
+    *out = I.stats;
+    int live = 0;
+    for (const ServerImpl::Group *G : I.groups) live += G->live() > 0;
+    out->groups = live;
+    out->active = (int32_t)(I.stats.submitted - I.stats.finished - (int64_t)I.queue.size());
     return PR_OK;
 }
 
@@ -1562,8 +1658,10 @@ extern "C" void pr_server_destroy(pr_server *S) {
     I.groups.clear();
     for (auto &kv : I.reqs) {
         if (kv.second->mem) cudaFreeAsync(kv.second->mem, I.s);
+        if (kv.second->dout) cudaFreeAsync(kv.second->dout, I.s);
         delete kv.second;
     }
     cudaStreamSynchronize(I.s);
+    if (I.ps) cudaStreamDestroy(I.ps);
     delete S;
 }

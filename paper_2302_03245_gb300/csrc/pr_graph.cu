@@ -82,11 +82,29 @@ pr_status Buf::alloc(size_t nbytes, cudaStream_t stream) {
 
 void Buf::release() {
     if (p) {
-        if (ffn) ffn(p, bytes, (void *)s, fctx);
+        if (stream_ordered) cudaFreeAsync(p, s);
+        else if (ffn) ffn(p, bytes, (void *)s, fctx);
         else cudaFree(p);
     }
     p = nullptr;
     bytes = 0;
+    stream_ordered = false;
+}
+
+pr_status Buf::alloc_async(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    if (nbytes == 0) nbytes = 16;
+    if (cudaMallocAsync(&p, nbytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return fail(PR_ENOMEM, "device allocation of " + std::to_string(nbytes) + " bytes failed");
+    }
+    bytes = nbytes;
+    ffn = nullptr;
+    fctx = nullptr;
+    stream_ordered = true;
+    return PR_OK;
 }
 
 // ------------------------------------------------------------ kernels

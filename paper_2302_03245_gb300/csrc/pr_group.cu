@@ -4,9 +4,9 @@
 // Requests served on one resident graph (personalized PageRank with different
 // seeds, or different damping factors) run the same rounds over the same
 // in-lists.  A group keeps K of them side by side: x[i][k], r[i][k] and the
-// pending push w[i][k] of column k are contiguous for a vertex, so one 32-byte
-// load per in-list entry gathers the pushed mass of all K columns (K = 8 for
-// float state, 4 for double-float).  Each column keeps its own parameters,
+// pending push w[i][k] of column k are contiguous for a vertex, so the K
+// columns of one in-list entry's source are one 32-byte sector, read by two
+// lanes with 16-byte loads (K = 8 for float state, 4 for double-float).  Each column keeps its own parameters,
 // round counter and stopping decision; the arithmetic of a column is that of
 // a pull round of the single solve (Alg. 3, synchronous snapshot rounds):
 //   commit of round t-1 (x += (1-c) r, r = 0 where |r| > xi),
@@ -28,32 +28,39 @@ template <typename T> struct GK {
     static constexpr int K = 32 / (int)sizeof(typename ST<T>::V);
 };
 
-// K gathered values of one in-list entry (32 bytes, two 16-byte loads)
-template <typename V, int K> struct Vec {
-    V v[K];
-};
-template <typename V, int K> __device__ __forceinline__ Vec<V, K> load_vec(const V *__restrict__ w, int i) {
-    static_assert(sizeof(Vec<V, K>) == 32, "a gathered vector is 32 bytes");
-    const uint4 *p = reinterpret_cast<const uint4 *>(w + (size_t)i * K);
-    const uint4 a = __ldg(p), b = __ldg(p + 1);
-    Vec<V, K> out;
-    uint4 *o = reinterpret_cast<uint4 *>(&out);
-    o[0] = a;
-    o[1] = b;
-    return out;
-}
-
 // per-column parameters read once per block
 template <typename T, int K> struct ColParams {
     T c[K], om[K], xi[K];
     int act[K], fresh[K];
     int any;
+    int use_unref;  // some column's previous round was its first (see k_group_round)
 };
+
+// Thread layout: a vertex's K columns are 32 bytes; a lane loads 16 of them
+// (CPL = 16 / sizeof(V) columns), so a "slot" of LPE = K / CPL = 2 lanes reads
+// one in-list entry: both lanes load the source id (one broadcast) and one
+// 16-byte half each of the source's sector.  A row is served by max(LANES, 2)
+// lanes (LANES from the graph's pull bins), i.e. by one or more slots, whose
+// sums are combined by shuffles across slots.  A lane keeps the partial R, F,
+// E of its own CPL columns.
+template <typename V> struct Cols {
+    static constexpr int CPL = 16 / (int)sizeof(V);
+};
+template <typename V> struct Half {
+    V v[Cols<V>::CPL];
+};
+template <typename V> __device__ __forceinline__ Half<V> load_half(const V *__restrict__ w, size_t at) {
+    static_assert(sizeof(Half<V>) == 16, "half a vertex's columns is 16 bytes");
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(w + at));
+    Half<V> h;
+    memcpy(&h, &a, 16);
+    return h;
+}
 
 template <typename T, int K>
 __device__ __forceinline__ void column_epilogue(const DevGraph &G, const ColParams<T, K> &P, T *x, T *r,
                                                 typename ST<T>::V *wnext, int j, int k, T in,
-                                                typename ST<T>::R *Rk, int *Fk, int *Ek) {
+                                                typename ST<T>::R &Rl, int &Fl, int &El) {
     const size_t at = (size_t)j * K + k;
     const T v = r[at];
     T base = v;
@@ -63,35 +70,37 @@ __device__ __forceinline__ void column_epilogue(const DevGraph &G, const ColPara
     }
     const T rn = ST<T>::add(base, in);
     r[at] = rn;
-    Rk[k] = ST<T>::radd(Rk[k], ST<T>::rval(ST<T>::absv(rn)));
+    Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(rn)));
     const bool act = ST<T>::gt(ST<T>::absv(rn), P.xi[k]);
     wnext[at] = ST<T>::pack(act ? ST<T>::mul(rn, ST<T>::mul(P.c[k], ST<T>::invdeg(G, j))) : ST<T>::zero());
     if (act) {
-        Fk[k] += 1;
-        Ek[k] += G.ndeg[j];
+        Fl += 1;
+        El += G.ndeg[j];
     }
 }
 
-// sums of the K columns over the in-list entries of row j handled by this lane
+// this lane's CPL columns summed over the in-list entries e = off[j] + slot,
+// + nslots, ... of row j, U entries in flight, in entry order
 template <typename T, int K, int U>
-__device__ __forceinline__ void row_vec_sum(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int j,
-                                            const typename ST<T>::V *__restrict__ w, int start, int step,
-                                            typename GT<typename ST<T>::V>::A *acc) {
+__device__ __forceinline__ void slot_sum(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int j,
+                                         const typename ST<T>::V *__restrict__ w, int part, int slot, int nslots,
+                                         typename GT<typename ST<T>::V>::A *acc) {
     using V = typename ST<T>::V;
+    constexpr int CPL = Cols<V>::CPL;
     const int b = __ldg(&off[j + 1]);
-    for (int e = __ldg(&off[j]) + start; e < b; e += U * step) {
+    for (int e = __ldg(&off[j]) + slot; e < b; e += U * nslots) {
         int idx[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const int ee = e + u * step;
+            const int ee = e + u * nslots;
             idx[u] = ee < b ? __ldcs(&src[ee]) : -1;
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             if (idx[u] >= 0) {
-                const Vec<V, K> g = load_vec<V, K>(w, idx[u]);
+                const Half<V> h = load_half(w, (size_t)idx[u] * K + part * CPL);
 #pragma unroll
-                for (int k = 0; k < K; k++) acc[k] = GT<V>::add(acc[k], g.v[k]);
+                for (int c = 0; c < CPL; c++) acc[c] = GT<V>::add(acc[c], h.v[c]);
             }
         }
     }
@@ -100,44 +109,53 @@ __device__ __forceinline__ void row_vec_sum(const int32_t *__restrict__ off, con
 template <typename T, int K, int LANES>
 __device__ __forceinline__ void group_rows(const DevGraph &G, const Seg &S, int lb, const ColParams<T, K> &P, T *x,
                                            T *r, const typename ST<T>::V *wprev, typename ST<T>::V *wnext,
-                                           typename ST<T>::R *Rk, int *Fk, int *Ek) {
+                                           typename ST<T>::R *Rl, int *Fl, int *El) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    constexpr int GPB = kThreads / LANES;
-    constexpr int U = LANES >= 32 ? 4 : 2;
-    const int grp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
-    const int stride = S.nblk * GPB;
-    for (int base = S.lo + lb * GPB; base < S.hi; base += stride) {
+    constexpr int CPL = Cols<V>::CPL;
+    constexpr int LPE = K / CPL;                // lanes per in-list entry
+    constexpr int L = LANES > LPE ? LANES : LPE;  // lanes per row
+    constexpr int NS = L / LPE;                 // slots per row
+    constexpr int RPB = kThreads / L;           // rows per block pass
+    constexpr int U = LANES >= 2 && NS == 1 ? 8 : 4;
+    const int part = threadIdx.x % LPE;
+    const int slot = (threadIdx.x % L) / LPE;
+    const int grp = threadIdx.x / L;
+    // the plan sized this segment's blocks for LANES lanes per row: spread its
+    // rows over the same blocks with L lanes each
+    const int stride = S.nblk * RPB;
+    for (int base = S.lo + lb * RPB; base < S.hi; base += stride) {
         const int j = base + grp;
-        A acc[K];
+        A acc[CPL];
 #pragma unroll
-        for (int k = 0; k < K; k++) acc[k] = GT<V>::zero();
+        for (int c = 0; c < CPL; c++) acc[c] = GT<V>::zero();
         if (j < S.hi) {
-            row_vec_sum<T, K, U>(G.inr_off, G.inr_src, j, wprev, lane, LANES, acc);
-            row_vec_sum<T, K, U>(G.inu_off, G.inu_src, j, wprev, lane, LANES, acc);
+            slot_sum<T, K, U>(G.inr_off, G.inr_src, j, wprev, part, slot, NS, acc);
+            if (P.use_unref) slot_sum<T, K, U>(G.inu_off, G.inu_src, j, wprev, part, slot, NS, acc);
         }
-        // every lane of the group gets the K sums (butterfly)
 #pragma unroll
-        for (int o = LANES / 2; o > 0; o >>= 1)
+        for (int o = L / 2; o >= LPE; o >>= 1)
 #pragma unroll
-            for (int k = 0; k < K; k++) {
-                acc[k] = GT<V>::add(acc[k], GT<V>::shfl_xor(acc[k], o, LANES));
+            for (int c = 0; c < CPL; c++) acc[c] = GT<V>::add(acc[c], GT<V>::shfl_xor(acc[c], o, L));
+        if (j < S.hi && slot == 0) {
+#pragma unroll
+            for (int c = 0; c < CPL; c++) {
+                const int k = part * CPL + c;
+                if (P.act[k])
+                    column_epilogue<T, K>(G, P, x, r, wnext, j, k, ST<T>::from_acc(acc[c]), Rl[c], Fl[c], El[c]);
             }
-        if (j < S.hi) {
-            // lane l takes the columns k = l, l + LANES, ...
-#pragma unroll
-            for (int k = 0; k < K; k++)
-                if (k % LANES == lane && P.act[k])
-                    column_epilogue<T, K>(G, P, x, r, wnext, j, k, ST<T>::from_acc(acc[k]), Rk, Fk, Ek);
         }
     }
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) k_group_round(DevGraph G, Plan PL, GroupDev D, int32_t launch_id) {
+__global__ void __launch_bounds__(kThreads, 5) k_group_round(DevGraph G, Plan PL, GroupDev D, int32_t launch_id) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
     using R = typename ST<T>::R;
+    constexpr int CPL = Cols<V>::CPL;
+    constexpr int LPE = K / CPL;
+    static_assert(K * sizeof(V) == 32 && LPE * CPL == K, "one 32-byte sector per vertex, 16 bytes per lane");
     __shared__ ColParams<T, K> P;
     if (threadIdx.x < K) {
         const int k = threadIdx.x;
@@ -153,9 +171,17 @@ __global__ void __launch_bounds__(kThreads) k_group_round(DevGraph G, Plan PL, G
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int any = 0;
-        for (int k = 0; k < K; k++) any |= P.act[k];
+        // Unreferenced sources (no in-edges) push only in a column's first
+        // round: their residual is never refilled.  Their in-list segment is
+        // read in the round after some column's first round, and skipped in
+        // every other round (it holds zeros there).
+        int any = 0, unref = 0;
+        for (int k = 0; k < K; k++) {
+            any |= P.act[k];
+            unref |= P.act[k] && D.join[k] == launch_id - 1;
+        }
         P.any = any;
+        P.use_unref = unref;
     }
     __syncthreads();
     if (!P.any) return;  // every block returns: no column is running
@@ -167,69 +193,74 @@ __global__ void __launch_bounds__(kThreads) k_group_round(DevGraph G, Plan PL, G
     while (s + 1 < PL.nseg && (int)blockIdx.x >= PL.seg[s + 1].blk0) s++;
     const Seg S = PL.seg[s];
     const int lb = blockIdx.x - S.blk0;
-    R Rk[K];
-    int Fk[K], Ek[K];
+    const int part = threadIdx.x % LPE;  // this lane's columns: part * CPL + c
+    R Rl[CPL];
+    int Fl[CPL], El[CPL];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        Rk[k] = ST<T>::rzero();
-        Fk[k] = 0;
-        Ek[k] = 0;
+    for (int c = 0; c < CPL; c++) {
+        Rl[c] = ST<T>::rzero();
+        Fl[c] = 0;
+        El[c] = 0;
     }
     switch (S.lanes) {
-        case 1: group_rows<T, K, 1>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        case 2: group_rows<T, K, 2>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        case 4: group_rows<T, K, 4>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        case 8: group_rows<T, K, 8>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        case 16: group_rows<T, K, 16>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        case 32: group_rows<T, K, 32>(G, S, lb, P, x, r, wprev, wnext, Rk, Fk, Ek); break;
-        default: {  // one block per row
+        case 1: group_rows<T, K, 1>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        case 2: group_rows<T, K, 2>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        case 4: group_rows<T, K, 4>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        case 8: group_rows<T, K, 8>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        case 16: group_rows<T, K, 16>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        case 32: group_rows<T, K, 32>(G, S, lb, P, x, r, wprev, wnext, Rl, Fl, El); break;
+        default: {  // one block per row: kThreads / LPE slots
             __shared__ A sha[kThreads / 32][K];
+            const int slot = threadIdx.x / LPE;
             for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
-                A acc[K];
+                A acc[CPL];
 #pragma unroll
-                for (int k = 0; k < K; k++) acc[k] = GT<V>::zero();
-                row_vec_sum<T, K, 4>(G.inr_off, G.inr_src, j, wprev, threadIdx.x, blockDim.x, acc);
-                row_vec_sum<T, K, 4>(G.inu_off, G.inu_src, j, wprev, threadIdx.x, blockDim.x, acc);
+                for (int c = 0; c < CPL; c++) acc[c] = GT<V>::zero();
+                slot_sum<T, K, 4>(G.inr_off, G.inr_src, j, wprev, part, slot, kThreads / LPE, acc);
+                if (P.use_unref)
+                    slot_sum<T, K, 4>(G.inu_off, G.inu_src, j, wprev, part, slot, kThreads / LPE, acc);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int o = 16; o >= LPE; o >>= 1)
 #pragma unroll
-                    for (int k = 0; k < K; k++) acc[k] = GT<V>::add(acc[k], GT<V>::shfl_xor(acc[k], o, 32));
+                    for (int c = 0; c < CPL; c++) acc[c] = GT<V>::add(acc[c], GT<V>::shfl_xor(acc[c], o, 32));
                 __syncthreads();
-                if ((threadIdx.x & 31) == 0)
+                if ((threadIdx.x & 31) < LPE)
 #pragma unroll
-                    for (int k = 0; k < K; k++) sha[threadIdx.x >> 5][k] = acc[k];
+                    for (int c = 0; c < CPL; c++) sha[threadIdx.x >> 5][part * CPL + c] = acc[c];
                 __syncthreads();
+                if ((int)threadIdx.x < LPE) {
 #pragma unroll
-                for (int k = 0; k < K; k++) {  // thread k takes column k (static indices keep Rk/Fk/Ek in registers)
-                    if ((int)threadIdx.x == k && P.act[k]) {
+                    for (int c = 0; c < CPL; c++) {
+                        const int k = part * CPL + c;
+                        if (!P.act[k]) continue;
                         A t = GT<V>::zero();
                         for (int w = 0; w < kThreads / 32; w++) t = GT<V>::add(t, sha[w][k]);
-                        column_epilogue<T, K>(G, P, x, r, wnext, j, k, ST<T>::from_acc(t), Rk, Fk, Ek);
+                        column_epilogue<T, K>(G, P, x, r, wnext, j, k, ST<T>::from_acc(t), Rl[c], Fl[c], El[c]);
                     }
                 }
             }
         }
     }
-    // block partials per column: warp shuffles, then one slot per warp in shared memory
+    // block partials per column: a column's lanes are LPE apart; fold the higher
+    // lanes of each warp, then one slot per warp in shared memory
     __shared__ R shr[kThreads / 32][K];
     __shared__ int shf[kThreads / 32][K], she[kThreads / 32][K];
+#pragma unroll
+    for (int o = 16; o >= LPE; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < CPL; c++) {
+            Rl[c] = ST<T>::radd(Rl[c], ST<T>::rshfl(Rl[c], o));
+            Fl[c] += __shfl_down_sync(0xffffffffu, Fl[c], o);
+            El[c] += __shfl_down_sync(0xffffffffu, El[c], o);
+        }
     const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln < LPE)
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        R rv = Rk[k];
-        int fv = Fk[k], ev = Ek[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rv = ST<T>::radd(rv, ST<T>::rshfl(rv, o));
-            fv += __shfl_down_sync(0xffffffffu, fv, o);
-            ev += __shfl_down_sync(0xffffffffu, ev, o);
+        for (int c = 0; c < CPL; c++) {
+            shr[wid][part * CPL + c] = Rl[c];
+            shf[wid][part * CPL + c] = Fl[c];
+            she[wid][part * CPL + c] = El[c];
         }
-        if (ln == 0) {
-            shr[wid][k] = rv;
-            shf[wid][k] = fv;
-            she[wid][k] = ev;
-        }
-    }
     __syncthreads();
     if (threadIdx.x < K) {
         const int k = threadIdx.x;

@@ -39,7 +39,11 @@ struct Buf {
     cudaStream_t s = nullptr;
     pr_free_fn ffn = nullptr;  // allocator hook that made p (nullptr: cudaMalloc)
     void *fctx = nullptr;
+    bool stream_ordered = false;  // made by alloc_async: freed with cudaFreeAsync on s
     pr_status alloc(size_t nbytes, cudaStream_t stream);
+    // cudaMallocAsync on `stream`, never the allocator hook: for the server's
+    // own thread, which must not call back into the host program
+    pr_status alloc_async(size_t nbytes, cudaStream_t stream);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
     ~Buf() { release(); }

@@ -193,6 +193,11 @@ template <> struct ST<double> {
     static __device__ __forceinline__ R rshfl(R a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
     static __device__ __forceinline__ double r_to_d(R a) { return a; }
     static __device__ __forceinline__ void atomic_add(double *a, double v) { atomicAdd(a, v); }
+    // push-round delivery, the pushing vertex's own subtraction, and the read of
+    // r_i at the activation that follows a push round (see ST<float2>)
+    static __device__ __forceinline__ void push_to(double *r, double *, int j, double w) { atomicAdd(&r[j], w); }
+    static __device__ __forceinline__ void commit_sub(double *r, int i, double v) { atomicAdd(&r[i], -v); }
+    static __device__ __forceinline__ double fold(double *r, double *, int i) { return r[i]; }
 };
 template <> struct ST<float> {
     using V = float;
@@ -222,6 +227,9 @@ template <> struct ST<float> {
     static __device__ __forceinline__ R rshfl(R a, int o) { return GT<float2>::shfl_down(a, o, 32); }
     static __device__ __forceinline__ double r_to_d(R a) { return df_to_d(a); }
     static __device__ __forceinline__ void atomic_add(float *a, float v) { atomicAdd(a, v); }
+    static __device__ __forceinline__ void push_to(float *r, double *, int j, float w) { atomicAdd(&r[j], w); }
+    static __device__ __forceinline__ void commit_sub(float *r, int i, float v) { atomicAdd(&r[i], -v); }
+    static __device__ __forceinline__ float fold(float *r, double *, int i) { return r[i]; }
 };
 template <> struct ST<float2> {
     using V = float2;
@@ -251,6 +259,24 @@ template <> struct ST<float2> {
     static __device__ __forceinline__ R rshfl(R a, int o) { return GT<float2>::shfl_down(a, o, 32); }
     static __device__ __forceinline__ double r_to_d(R a) { return df_to_d(a); }
     static __device__ __forceinline__ void atomic_add(float2 *a, float2 v) { df_atomic_add(a, v); }
+    // A push round adds into an FP64 inbox with the L2's native double atomics:
+    // a double-float compare-and-swap loop serialises on vertices that many
+    // frontier vertices push into.  The double sum keeps more than the pair's
+    // 48 significant bits.  Nothing else writes r during a push round, so the
+    // pushing vertex subtracts its snapshot from r directly, and the activation
+    // that follows every push round folds the inbox into r.
+    static __device__ __forceinline__ void push_to(float2 *, double *din, int j, float2 w) {
+        atomicAdd(&din[j], df_to_d(w));
+    }
+    static __device__ __forceinline__ void commit_sub(float2 *r, int i, float2 v) { r[i] = df_add(r[i], df_neg(v)); }
+    static __device__ __forceinline__ float2 fold(float2 *r, double *din, int i) {
+        const double d = din[i];
+        if (d == 0.0) return r[i];
+        const float2 v = df_add(r[i], df_from_d(d));
+        r[i] = v;
+        din[i] = 0.0;
+        return v;
+    }
 };
 
 // |v| > xi_act, evaluated identically wherever an activation is decided.
@@ -494,6 +520,7 @@ struct RoundBuf {
     void *x, *r, *vbuf;  // T arrays
     void *w[2];          // ST<T>::V arrays; w[t & 1] written by the activation of round t
     int32_t *bins;
+    double *din;         // [n] push-round inbox of double-float state (zero between rounds); else unused
 };
 
 // activation of one non-dangling vertex i with residual v (round t):
@@ -534,7 +561,7 @@ __device__ __forceinline__ void bins_append(bool act, int pd, int i, uint32_t *b
 template <typename T>
 __device__ __forceinline__ void push_commit(const Ctl *ctl, T *x, T *r, int i, T v) {
     x[i] = ST<T>::add(x[i], ST<T>::mul(ST<T>::om(ctl), v));
-    ST<T>::atomic_add(&r[i], ST<T>::neg(v));
+    ST<T>::commit_sub(r, i, v);
 }
 
 template <typename T, bool IFP2>
@@ -558,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0; e < e1; e++) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+            for (int e = e0; e < e1; e++) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
         }
     } else if (b < nb_thread + nb_warp) {
         const uint32_t c1 = cnt[1];
@@ -571,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + lane; e < e1; e += 32) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+            for (int e = e0 + lane; e < e1; e += 32) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
         }
     } else {
         const uint32_t c2 = cnt[2];
@@ -583,7 +610,7 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) ST<T>::atomic_add(&r[G.out_dst[e]], wi);
+            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
         }
     }
 }
@@ -700,14 +727,14 @@ __device__ __forceinline__ void activate_range(const DevGraph &G, const Ctl *ctl
                                                typename ST<T>::V *w, int lo, int hi, int first, int step, int want,
                                                uint32_t *bcnt, typename ST<T>::R &Rl, long long &Fl, long long &El,
                                                int &ul) {
-    const T *r = static_cast<const T *>(B.r);
+    T *r = static_cast<T *>(B.r);
     T *vbuf = static_cast<T *>(B.vbuf);
     for (int base = lo + first; base < hi; base += step) {
         const int i = base + (int)threadIdx.x;
         bool act = false;
         int pd = 0;
         if (i < hi) {
-            const T v = r[i];
+            const T v = ST<T>::fold(r, B.din, i);  // the previous round was a push round
             Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(v)));
             act = activate_one<T, IFP2>(G, ctl, i, v, want, w, vbuf, pd, Fl, El, ul);
         }
@@ -960,6 +987,13 @@ __device__ __forceinline__ T zval(const DevGraph &G, const Ctl *ctl, int kind, c
     return x[i];
 }
 
+
+// inbox of double-float state folded into r over rows [lo, hi) (IFP1 dangling
+// rows receive pushes and no activation reads them)
+static __global__ void k_fold_inbox(float2 *r, double *din, int32_t lo, int32_t hi) {
+    for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x)
+        ST<float2>::fold(r, din, i);
+}
 
 // host-side conversions of the scalar parameters
 inline float float_at_most(double v) {  // largest float <= v

@@ -262,6 +262,7 @@ struct Prof {
 // ------------------------------------------------------------ workspace
 struct StateBufs {
     Buf x, r, vbuf, w[2], q;  // round state of one format; q: phase-2 / correction gather values
+    Buf din;                  // double-float state: push-round inbox (FP64, zero between rounds)
 };
 
 struct Workspace {
@@ -318,14 +319,20 @@ static PVals pvals_of(Workspace &W) { return PVals{W.p64.as<double>(), W.p32.as<
 
 // state buffers of one format: x, r (n), vbuf (n_nd), w[2] (n_nd), q (n)
 static pr_status alloc_state(StateBufs &S, size_t t_bytes, size_t v_bytes, size_t n, size_t nnd, cudaStream_t s) {
-    if (S.x.p) return PR_OK;
-    PR_TRY(S.x.alloc(t_bytes * n, s));
-    PR_TRY(S.r.alloc(t_bytes * n, s));
-    PR_TRY(S.vbuf.alloc(t_bytes * nnd, s));
-    PR_TRY(S.w[0].alloc(v_bytes * nnd, s));
-    PR_TRY(S.w[1].alloc(v_bytes * nnd, s));
-    PR_TRY(S.q.alloc(v_bytes * n, s));
-    return PR_OK;
+    if (S.q.p) return PR_OK;  // allocated last: present only when all are
+    const pr_status st = [&]() -> pr_status {
+        PR_TRY(S.x.alloc(t_bytes * n, s));
+        PR_TRY(S.r.alloc(t_bytes * n, s));
+        PR_TRY(S.vbuf.alloc(t_bytes * nnd, s));
+        PR_TRY(S.w[0].alloc(v_bytes * nnd, s));
+        PR_TRY(S.w[1].alloc(v_bytes * nnd, s));
+        PR_TRY(S.q.alloc(v_bytes * n, s));
+        return PR_OK;
+    }();
+    if (st != PR_OK) {  // leave nothing half-built for the next solve
+        for (Buf *b : {&S.x, &S.r, &S.vbuf, &S.w[0], &S.w[1], &S.q}) b->release();
+    }
+    return st;
 }
 
 static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
@@ -334,17 +341,25 @@ static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
     if (!g->ws) {
         Workspace *W = new (std::nothrow) Workspace();
         if (!W) return fail(PR_ENOMEM, "host allocation failed");
+        const pr_status st = [&]() -> pr_status {
+            PR_TRY(W->ctl.alloc(sizeof(Ctl), s));
+            PR_TRY(W->part.alloc(sizeof(double) * kMaxBlocks * 6, s));
+            PR_TRY(W->p64.alloc(sizeof(double) * n, s));
+            PR_TRY(W->p32.alloc(sizeof(float) * n, s));
+            PR_TRY(W->pdf.alloc(sizeof(float2) * n, s));
+            PR_TRY(W->outbuf.alloc(sizeof(double) * n, s));
+            PR_TRY(W->bins.alloc(sizeof(int32_t) * 3 * nnd, s));
+            PR_CK(cudaMallocHost(&W->hctl, sizeof(Ctl)));
+            PR_CK(cudaMemsetAsync(W->ctl.p, 0, sizeof(Ctl), s));
+            PR_CK(cudaMemsetAsync(W->part.p, 0, W->part.bytes, s));
+            return PR_OK;
+        }();
+        if (st != PR_OK) {  // the next solve starts over
+            g->ws = W;
+            destroy_workspace(g);
+            return st;
+        }
         g->ws = W;
-        PR_TRY(W->ctl.alloc(sizeof(Ctl), s));
-        PR_TRY(W->part.alloc(sizeof(double) * kMaxBlocks * 6, s));
-        PR_TRY(W->p64.alloc(sizeof(double) * n, s));
-        PR_TRY(W->p32.alloc(sizeof(float) * n, s));
-        PR_TRY(W->pdf.alloc(sizeof(float2) * n, s));
-        PR_TRY(W->outbuf.alloc(sizeof(double) * n, s));
-        PR_TRY(W->bins.alloc(sizeof(int32_t) * 3 * nnd, s));
-        PR_CK(cudaMallocHost(&W->hctl, sizeof(Ctl)));
-        PR_CK(cudaMemsetAsync(W->ctl.p, 0, sizeof(Ctl), s));
-        PR_CK(cudaMemsetAsync(W->part.p, 0, W->part.bytes, s));
     }
     Workspace &W = *static_cast<Workspace *>(g->ws);
     if (prec == PR_FP64) PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(float2), n, nnd, s));
@@ -352,7 +367,10 @@ static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
         PR_TRY(alloc_state(W.s32, sizeof(float), sizeof(float), n, nnd, s));
         PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(float2), n, nnd, s));  // correction sweep
     }
-    if (prec == PR_FP32 || prec == PR_DF64) PR_TRY(alloc_state(W.sdf, sizeof(float2), sizeof(float2), n, nnd, s));
+    if (prec == PR_FP32 || prec == PR_DF64) {
+        if (!W.sdf.din.p) PR_TRY(W.sdf.din.alloc(sizeof(double) * n, s));
+        PR_TRY(alloc_state(W.sdf, sizeof(float2), sizeof(float2), n, nnd, s));
+    }
     if (trace_len > W.trace_len) {
         W.drop_graphs();  // the traces are kernel arguments of the captured graphs
         PR_TRY(W.tR.alloc(sizeof(double) * trace_len, s));
@@ -376,7 +394,7 @@ template <> StateBufs &state_of<float2>(Workspace &W) { return W.sdf; }
 
 template <typename T> static RoundBuf round_bufs(Workspace &W) {
     StateBufs &S = state_of<T>(W);
-    return RoundBuf{S.x.p, S.r.p, S.vbuf.p, {S.w[0].p, S.w[1].p}, W.bins.as<int32_t>()};
+    return RoundBuf{S.x.p, S.r.p, S.vbuf.p, {S.w[0].p, S.w[1].p}, W.bins.as<int32_t>(), S.din.as<double>()};
 }
 
 // graph-cache keys: 2 per round format (IFP1, IFP2) and one per Power format
@@ -740,9 +758,12 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         finish_ifp<double>(g, W, algo, dout, launches);
         launches += 1;
     } else if (prec == PR_DF64) {
+        PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
         k_init_state<float2><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
         PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
         PR_TRY(count_rounds(0));
+        if (algo == PR_IFP1 && G.n > G.n_nd)  // pushes into dangling rows still in the inbox
+            k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
         finish_ifp<float2>(g, W, algo, dout, launches);
         launches += 1;
     } else {  // FP32 rounds, FP64 correction sweep, double-float rounds to the end
@@ -762,9 +783,12 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         k_reset_run<<<1, 1, 0, s>>>(ctl);
         k_sweep<double, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
         k_64_to_df<<<gn, kThreads, 0, s>>>(G.n, x64, r64, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
+        PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
         PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
         PR_TRY(count_rounds(r32_rounds));
         fp64_rounds = W.hctl->round - r32_rounds;
+        if (algo == PR_IFP1 && G.n > G.n_nd)
+            k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
         finish_ifp<float2>(g, W, algo, dout, launches);
         launches += 5;
     }

@@ -61,6 +61,7 @@ int main(void){
  printf("%zu %zu %zu %zu %zu\n", sizeof(pr_stats), sizeof(pr_opts), sizeof(pr_graph_info), sizeof(pr_pvec), sizeof(pr_kernel_profile));
  printf("%zu %zu %zu\n", offsetof(pr_stats, ms), offsetof(pr_opts, trace_mode), offsetof(pr_graph_info, device_bytes));
  printf("%zu %zu %zu %zu\n", sizeof(pr_tuning), offsetof(pr_tuning, pull_ratio), offsetof(pr_tuning, bin_rows), offsetof(pr_tuning, pull_blocks));
+ printf("%zu %zu %zu\n", sizeof(pr_server_stats), offsetof(pr_server_stats, groups), offsetof(pr_server_stats, ms_finish));
  return 0;}'''
     exe = os.path.join(ROOT, "tests", ".layout_probe")
     r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-x", "c", "-", "-o", exe], input=src,
@@ -78,6 +79,8 @@ int main(void){
     T = prlib.pr_tuning
     assert list(map(int, lines[2].split())) == [ctypes.sizeof(T), T.pull_ratio.offset, T.bin_rows.offset,
                                                 T.pull_blocks.offset]
+    S = prlib.pr_server_stats
+    assert list(map(int, lines[3].split())) == [ctypes.sizeof(S), S.groups.offset, S.ms_finish.offset]
 
 
 @pytest.mark.parametrize("case", ["dup_free_but_bad_offsets", "range", "negative_n", "off0", "offn"])
