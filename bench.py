@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the benchmark workload)")
     ap.add_argument("--eps", type=float, default=1e-9)
+    ap.add_argument("--serve-scale", type=int, default=23, help="R-MAT scale of the resident serving graph")
+    ap.add_argument("--serve-rates", default="100,300,1000,3000,10000,20000", help="arrival rates (requests/s)")
+    ap.add_argument("--serve-max", type=int, default=400, help="requests per rate at most")
+    ap.add_argument("--algo", default="ifp2", choices=["ifp2", "ifp1", "power"],
+                    help="algorithm of the timed steps (ifp2 = the headline)")
     ap.add_argument("--skip-extras", action="store_true", help="only the timed IFP2 steps")
     ap.add_argument("--host-rounds", action="store_true",
                     help="launch rounds from the host instead of the CUDA-graph while loop (same kernels; "
@@ -55,17 +60,18 @@ def parse():
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch parameters (read if it has this graph, else written)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters")
-    ap.add_argument("--legs", default="dag,batch,serve",
+    ap.add_argument("--legs", default="dag,batch,serve,sweep",
                     help="extra configurations after the headline: dag (scale-24 DAG-heavy, FP32 form), "
-                         "batch (512 graphs in one batch), serve (continuous batching); '' for none")
+                         "batch (512 graphs in one batch), serve (continuous batching), sweep (time and "
+                         "error against eps); '' for none")
     return ap.parse_args()
 
 
-def workload(scale):
-    return dict(workload=f"rmat{scale}_ifp2_df64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
+def workload(scale, algo="ifp2"):
+    return dict(workload=f"rmat{scale}_{algo}_df64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
                 vertices=1 << scale, edge_factor=16, sampled_edges=16 << scale, dangling_deleted=0.20,
                 unref_deleted=0.10, relabel="seeded random permutation", seed=1, c=C, p="uniform",
-                algo="IFP2", precision="df64", eps=1e-9)
+                algo=algo.upper() if algo != "power" else "Power", precision="df64", eps=1e-9)
 
 
 def make_graph(scale):
@@ -164,6 +170,27 @@ def recorded_traffic(kernel, workload_name):
     if not e or e.get("source_hash") != source_hash():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def run_legs(args, line, pr, torch, stream, flush, hbm_peak, peak_src):
+    """The extra configurations named by --legs, each reported in its own key."""
+    legs = [x for x in args.legs.split(",") if x]
+    extra = {}
+    for leg in legs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            extra[leg] = LEGS[leg](pr, torch, stream, flush, hbm_peak, peak_src)
+        except Exception as e:  # a failed leg is reported, the headline line still prints
+            extra[leg] = {"error": f"{type(e).__name__}: {e}"}
+        extra[leg]["leg_wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    keys = {"dag": "dag24", "batch": "batch512", "sweep": "eps_sweep", "serve": "serving"}
+    for leg, res in extra.items():
+        line[keys.get(leg, leg)] = res
+    sv = extra.get("serve", {})
+    if "rates" in sv:
+        line["served_p50_p99_ms"] = {str(r["rate"]): [r["p50_ms"], r["p99_ms"]] for r in sv["rates"]}
 
 
 def reduce_ranks(seconds, edges, dist, device):
@@ -366,7 +393,7 @@ def leg_serve(pr, torch, stream, flush, hbm_peak, peak_src):
     import numpy as np
     from graphgen import torchgen as tg
     t0 = time.perf_counter()
-    gd = tg.rmat(23, 16, dangling=0.20, unref=0.10, seed=3, device="cuda")
+    gd = tg.rmat(ARGS.serve_scale, 16, dangling=0.20, unref=0.10, seed=3, device="cuda")
     off, dst = gd.csr32()
     R = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream)
     del gd, off, dst
@@ -383,7 +410,7 @@ def leg_serve(pr, torch, stream, flush, hbm_peak, peak_src):
         del gd, off, dst
     torch.cuda.synchronize()
     n_res = R.info["n"]
-    res = {"workload": "serve_rmat23_ppr90_fp32", "graph_s": time.perf_counter() - t0,
+    res = {"workload": f"serve_rmat{ARGS.serve_scale}_ppr90_fp32", "graph_s": time.perf_counter() - t0,
            "resident": {k: R.info[k] for k in ("n", "m", "n_nd")}, "pool_n": [h.info["n"] for h in pool]}
 
     def request(rr):
@@ -420,8 +447,8 @@ def leg_serve(pr, torch, stream, flush, hbm_peak, peak_src):
         for _ in range(8):  # warm-up: the server's tables and the per-graph tiles
             h, pv, pi = request(rr)
             S.wait(S.submit(h, C, 1e-6, pr.PR_FP32, pv, pi))
-        for rate in (100, 300, 1000, 3000, 10000, 20000):
-            N = min(int(rate * 2.0), 400)
+        for rate in [int(v) for v in ARGS.serve_rates.split(",") if v]:
+            N = min(int(rate * 2.0), ARGS.serve_max)
             arr = np.cumsum(rng.exponential(1.0 / rate, N))
             reqs = [request(rr) for _ in range(N)]
             lat, server_ms, pending = [], [], {}
@@ -458,7 +485,30 @@ def leg_serve(pr, torch, stream, flush, hbm_peak, peak_src):
     return res
 
 
-LEGS = {"dag": leg_dag, "batch": leg_batch, "serve": leg_serve}
+def leg_sweep(pr, torch, stream, flush, hbm_peak, peak_src):
+    """Time and accuracy against eps (the paper's Fig. 1 / Fig. 2 analogue) on
+    the headline graph: IFP1 and IFP2 (DF64) stopped at eps, the Power method
+    (DF64) stopped at ||delta||_1 <= eps; L1 and max relative error (the
+    paper's ERR, Sec. 4) against a Power solution to 1e-14."""
+    g = make_graph_device(22)
+    off, dst = g.csr32()
+    G = pr.Graph(g.n, g.m, off, dst, mem_is_device=True, stream=stream)
+    del g, off, dst
+    out = torch.empty(G.info["n"], dtype=torch.float64, device="cuda")
+    truth = torch.empty_like(out)
+    G.solve(C, 1e-14, pr.PR_POWER, pr.PR_FP64, out=truth)
+    rows = []
+    for name, algo in (("IFP1", pr.PR_IFP1), ("IFP2", pr.PR_IFP2), ("Power", pr.PR_POWER)):
+        for eps in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11, 1e-12):
+            ms, st = median_solve(G, flush, 2, C, eps, algo, pr.PR_DF64, out=out)
+            err = (out - truth).abs()
+            rows.append(dict(algo=name, eps=eps, ms=ms, rounds=st["rounds"], l1=float(err.sum()),
+                             err_max_rel=float((err / truth).max()), err_bound=st["err_bound"]))
+    G.close()
+    return {"workload": "rmat22 sweep over eps, DF64", "rows": rows}
+
+
+LEGS = {"dag": leg_dag, "batch": leg_batch, "serve": leg_serve, "sweep": leg_sweep}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -505,8 +555,12 @@ def emit(line, args):
 
 
 # ------------------------------------------------------------------ GPU arm
+ARGS = None  # parsed command line (the legs read their options from it)
+
+
 def main():
-    args = parse()
+    global ARGS
+    args = ARGS = parse()
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -551,7 +605,9 @@ def main():
     out = torch.empty(n_v, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
-    def solve(algo=pr.PR_IFP2, prec=pr.PR_DF64, eps=args.eps, opts=None):
+    step_algo = {"ifp2": pr.PR_IFP2, "ifp1": pr.PR_IFP1, "power": pr.PR_POWER}[args.algo]
+
+    def solve(algo=step_algo, prec=pr.PR_DF64, eps=args.eps, opts=None):
         opts = dict(opts or {})
         if args.host_rounds:
             opts.setdefault("use_graph", -1)
@@ -593,7 +649,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "df64 (fp32 hi+lo pairs; fp64 final sums and output)",
             "data": "synthetic",
-            "config": dict(workload(args.scale), l2="512 MB buffer written between timed steps",
+            "config": dict(workload(args.scale, args.algo), l2="512 MB buffer written between timed steps",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "gpu_launches": int(launches), "clocks": clk,
             "graph": {k: info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_outdeg",
@@ -601,16 +657,17 @@ def main():
             "rounds": rounds[0], "edges_pushed_per_step": edges[0], "wall_s_timed": wall,
             "tuning": dict(tuning, autotune_s=tune_s, source=tune_report.splitlines()[-1] if tune_report else ""),
             "graph_generation_s": gen_s}
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
     if rank != 0 or args.skip_extras:
         if rank == 0:
+            G.close()
+            run_legs(args, line, pr, torch, stream, flush, hbm_peak, peak_src)
             emit(line, args)
         if dist:
             dist.destroy_process_group()
         return
-
-    peaks = measured_peaks()
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
-    peak_src = "measured" if peaks else "fallback"
 
     # ---- per-kernel CUDA-event timing (instrumented pass of the same solve)
     prof_runs = 2
@@ -651,7 +708,7 @@ def main():
     line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (copy bandwidth)",
                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
-                        "traffic": recorded_traffic(dom, workload(args.scale)["workload"]),
+                        "traffic": recorded_traffic(dom, workload(args.scale, args.algo)["workload"]),
                         "timing": "CUDA events around every launch on the graph's stream, instrumented pass"}
     line["kernels"] = kernels
 
@@ -754,26 +811,7 @@ def main():
         line["tuning"]["default_params_ms"] = statistics.median(tms)
         line["tuning"]["tuned_ms"] = t_step
     G.close()
-    legs = [x for x in args.legs.split(",") if x]
-    extra = {}
-    for leg in legs:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        try:
-            extra[leg] = LEGS[leg](pr, torch, stream, flush, hbm_peak, peak_src)
-        except Exception as e:  # a failed leg is reported, the headline line still prints
-            extra[leg] = {"error": f"{type(e).__name__}: {e}"}
-        extra[leg]["leg_wall_s"] = time.perf_counter() - t0
-        torch.cuda.empty_cache()
-    if "dag" in extra:
-        line["dag24"] = extra["dag"]
-    if "batch" in extra:
-        line["batch512"] = extra["batch"]
-    if "serve" in extra:
-        line["serving"] = extra["serve"]
-        sv = extra["serve"]
-        if "rates" in sv:
-            line["served_p50_p99_ms"] = {str(r["rate"]): [r["p50_ms"], r["p99_ms"]] for r in sv["rates"]}
+    run_legs(args, line, pr, torch, stream, flush, hbm_peak, peak_src)
     emit(line, args)
     if dist:
         dist.destroy_process_group()

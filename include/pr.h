@@ -59,9 +59,10 @@ typedef enum {
                     FP64 pipe runs at 1/64 of FP32: the reference form, slow) */
     PR_FP32 = 1, /* residual, reserve and pushed mass in float; sums of the
                     residual L1 and dangling mass in double-float with a final
-                    FP64 sum; at the end an FP64 correction sweep recomputes the
-                    residual from the reserve, and double-float rounds finish the
-                    solve (not in the paper; the identity used is that of Eq. 4) */
+                    FP64 sum; at the end a correction sweep recomputes the
+                    residual from the reserve in double-float arithmetic, and
+                    double-float rounds finish the solve (not in the paper; the
+                    identity used is that of Eq. 4) */
     PR_DF64 = 2  /* residual, reserve and pushed mass as double-float pairs
                     (hi + lo floats, 48-bit significand, FP32 instructions); push
                     rounds add into an FP64 inbox with double atomics, folded into

@@ -36,8 +36,7 @@ struct BProb {
     int32_t v0, nv;              // vertex tiles
     int32_t d0, nd;              // dangling-row tiles
     PVals pv;
-    double *x64, *r64;           // FP32 form: the FP64 correction state
-    float2 *q64;
+    float2 *qc;                  // FP32 form: gather values x_u / ((1-c) deg u) of the correction
     void *q;                     // phase-2 gather values
     double *out;                 // normalised result (device)
 };
@@ -237,54 +236,44 @@ __global__ void k_batch_init(const BProb *probs, const Tile *vt, int nvt) {
     }
 }
 
-// FP32 reserve -> FP64 state and packed gather values for the correction sweep
+// FP32 reserve -> double-float state (exactly) with an empty push inbox, and the
+// gather values q_u = x_u / ((1-c) deg(u)) of the correction sweep; IFP2's
+// dangling residual is p (phase 1 never touches it), IFP1's comes from the sweep
 template <bool IFP2>
-__global__ void k_batch_to64(const BProb *probs, const Tile *vt, int nvt) {
-    for (int k = blockIdx.x; k < nvt; k += gridDim.x) {
-        const Tile tl = vt[k];
-        const BProb &P = probs[tl.prob];
-        const float *x32 = static_cast<const float *>(P.B.x);
-        for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
-            const double xv = (double)x32[i];
-            P.x64[i] = xv;
-            if (i < P.G.n_nd) P.q64[i] = df_from_d(xv * P.ctl->inv_om * P.G.inv_deg64[i]);
-            else if (IFP2) P.r64[i] = P.ctl->p_dense ? P.pv.p64[i] : P.ctl->pu;
-        }
-    }
-}
-
-// FP64 correction sweep r = p + c P~ s - s over the round tiles
-__global__ void __launch_bounds__(kThreads) k_batch_correct(const BProb *probs, const Tile *tiles, int ntiles) {
-    using A = typename GT<float2>::A;
-    __shared__ A sha[32];
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const Tile tl = tiles[k];
-        const BProb &P = probs[tl.prob];
-        SweepArgs<double> a{};
-        a.val = P.q64;
-        a.r = P.r64;
-        a.x = P.x64;
-        a.pv = P.pv;
-        double s1 = 0, s2 = 0, s3 = 0;
-        const Seg S{tl.lo, tl.hi, tl.lanes, 0, 1};
-        sweep_segment<double, OP_CORRECT>(P.G, S, 0, P.ctl, a, s1, s2, s3, sha);
-    }
-}
-
-// corrected FP64 state -> the double-float round state, and a fresh run
-__global__ void k_batch_64_to_df(const BProb *probs, const BProb *probs_df, const Tile *vt, int nvt) {
+__global__ void k_batch_to_df(const BProb *probs, const BProb *probs_df, const Tile *vt, int nvt) {
     for (int k = blockIdx.x; k < nvt; k += gridDim.x) {
         const Tile tl = vt[k];
         const BProb &P = probs[tl.prob];
         const BProb &Q = probs_df[tl.prob];
+        const float *x32 = static_cast<const float *>(P.B.x);
         float2 *x = static_cast<float2 *>(Q.B.x);
         float2 *r = static_cast<float2 *>(Q.B.r);
-        double *din = Q.B.din;
         for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
-            x[i] = df_from_d(P.x64[i]);
-            r[i] = df_from_d(P.r64[i]);
-            din[i] = 0.0;
+            const float2 xv = make_float2(x32[i], 0.f);
+            x[i] = xv;
+            Q.B.din[i] = 0.0;
+            if (i < P.G.n_nd) Q.qc[i] = df_mul(xv, df_mul(P.G.inv_degdf[i], P.ctl->inv_om_df));
+            else if (IFP2) r[i] = P.ctl->p_dense ? df_from_d(P.pv.p64[i]) : P.ctl->pu_df;
         }
+    }
+}
+
+// correction sweep r = p + c P~ s - s (double-float) over the round tiles, into
+// the double-float state
+__global__ void __launch_bounds__(kThreads) k_batch_correct(const BProb *probs_df, const Tile *tiles, int ntiles) {
+    using A = typename GT<float2>::A;
+    __shared__ A sha[32];
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = tiles[k];
+        const BProb &Q = probs_df[tl.prob];
+        SweepArgs<float2> a{};
+        a.val = Q.qc;
+        a.r = static_cast<float2 *>(Q.B.r);
+        a.x = static_cast<const float2 *>(Q.B.x);
+        a.pv = Q.pv;
+        float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+        const Seg S{tl.lo, tl.hi, tl.lanes, 0, 1};
+        sweep_segment<float2, OP_CORRECT>(Q.G, S, 0, Q.ctl, a, s1, s2, s3, sha);
     }
 }
 
@@ -551,15 +540,13 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     const size_t off_ctl = A.take(sizeof(Ctl) * count);
     const size_t off_bc = A.take(sizeof(BCtl));
     std::vector<StateOffsets> so(count), so_df(fp32 ? count : 0);
-    std::vector<size_t> off_out(count), off_x64(count), off_r64(count), off_q64(count);
+    std::vector<size_t> off_out(count), off_qc(count);
     for (int k = 0; k < count; k++) {
         const size_t n = gs[k]->G.n, nnd = std::max(gs[k]->G.n_nd, 1);
         so[k] = take_state(A, n, nnd, tb, vb, prec == PR_DF64);
         if (fp32) {
             so_df[k] = take_state(A, n, nnd, sizeof(float2), sizeof(float2), true);
-            off_x64[k] = A.take(sizeof(double) * n);
-            off_r64[k] = A.take(sizeof(double) * n);
-            off_q64[k] = A.take(sizeof(float2) * n);
+            off_qc[k] = A.take(sizeof(float2) * n);
         }
         off_out[k] = outs_are_device ? 0 : A.take(sizeof(double) * n);
     }
@@ -607,9 +594,7 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
         P.q = A.at<char>(so[k].q);
         P.out = outs_are_device ? outs[k] : A.at<double>(off_out[k]);
         if (fp32) {
-            P.x64 = A.at<double>(off_x64[k]);
-            P.r64 = A.at<double>(off_r64[k]);
-            P.q64 = A.at<float2>(off_q64[k]);
+            P.qc = A.at<float2>(off_qc[k]);
         }
     }
     if (fp32) {
@@ -662,10 +647,9 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
         PR_CK(cudaMemcpyAsync(mid.data(), d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
         for (int k = 0; k < count; k++) r32_rounds[k] = mid[k].round;
-        if (ifp2) k_batch_to64<true><<<sgrid, kThreads, 0, s>>>(d_probs, d_vt, nvt);
-        else k_batch_to64<false><<<sgrid, kThreads, 0, s>>>(d_probs, d_vt, nvt);
-        k_batch_correct<<<(int)std::min<int64_t>(nrt, (int64_t)sms * 16), kThreads, 0, s>>>(d_probs, d_rt, nrt);
-        k_batch_64_to_df<<<sgrid, kThreads, 0, s>>>(d_probs, d_probs_df, d_vt, nvt);
+        if (ifp2) k_batch_to_df<true><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs_df, d_vt, nvt);
+        else k_batch_to_df<false><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs_df, d_vt, nvt);
+        k_batch_correct<<<(int)std::min<int64_t>(nrt, (int64_t)sms * 16), kThreads, 0, s>>>(d_probs_df, d_rt, nrt);
         k_batch_reset<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_probs_df, count, bc);
         PR_TRY(batch_rounds<float2>(ifp2, s, cap, d_probs_df, d_rt, nrt, bc, sl, grid));
     }
@@ -826,7 +810,7 @@ struct SReq {
     size_t bytes = 0;
     void *mem = nullptr;            // one stream-ordered allocation
     StateOffsets s_main{}, s_df{};
-    size_t off_ctl = 0, off_out = 0, off_x64 = 0, off_r64 = 0, off_q64 = 0, off_p64 = 0, off_sidx = 0, off_sval = 0;
+    size_t off_ctl = 0, off_out = 0, off_qc = 0, off_p64 = 0, off_sidx = 0, off_sval = 0;
     int32_t rounds_first = 0;
     void *group = nullptr;          // column group holding the request's rounds (nullptr: tile engine)
     int gcol = -1;
@@ -866,9 +850,7 @@ size_t layout(SReq &q) {
     q.s_main = state(tb, vb);
     if (fp32) {
         q.s_df = state(sizeof(float2), sizeof(float2));
-        q.off_x64 = take(sizeof(double) * n);
-        q.off_r64 = take(sizeof(double) * n);
-        q.off_q64 = take(sizeof(float2) * n);
+        q.off_qc = take(sizeof(float2) * n);
         q.off_p64 = take(sizeof(double) * n);
     }
     q.off_sidx = take(sizeof(int32_t) * std::max(q.nnz, 1));
@@ -957,9 +939,7 @@ struct ServerImpl {
         P.q = q->at<char>(o.q);
         P.out = q->dout;
         if (q->prec == PR_FP32) {
-            P.x64 = q->at<double>(q->off_x64);
-            P.r64 = q->at<double>(q->off_r64);
-            P.q64 = q->at<float2>(q->off_q64);
+            P.qc = q->at<float2>(q->off_qc);
             P.pv = PVals{q->at<double>(q->off_p64), nullptr, nullptr};
         }
         return P;
@@ -1075,9 +1055,8 @@ struct ServerImpl {
         const int g1 = (int)std::min<int64_t>(std::max(nv, 1), (int64_t)sms * 16);
         const int g2 = (int)std::min<int64_t>(std::max(nr, 1), (int64_t)sms * 16);
         const BProb *dp = d_fprobs.as<BProb>();
-        k_batch_to64<true><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv);
-        k_batch_correct<<<g2, kThreads, 0, s>>>(dp, d_ftiles.as<Tile>(), nr);
-        k_batch_64_to_df<<<g1, kThreads, 0, s>>>(dp, dfp.as<BProb>(), d_fvtiles.as<Tile>(), nv);
+        k_batch_to_df<true><<<g1, kThreads, 0, s>>>(dp, dfp.as<BProb>(), d_fvtiles.as<Tile>(), nv);
+        k_batch_correct<<<g2, kThreads, 0, s>>>(dfp.as<BProb>(), d_ftiles.as<Tile>(), nr);
         Buf bcb;
         PR_TRY(bcb.alloc_async(sizeof(BCtl), s));
         k_batch_reset<<<((int)set.size() + kThreads - 1) / kThreads, kThreads, 0, s>>>(dfp.as<BProb>(), (int)set.size(),

@@ -110,21 +110,16 @@ __global__ void k_power_init(DevGraph G, Ctl *ctl, Partials P, PVals pv, T *pi, 
 
 // FP32 reserve -> FP64: x64 = x32, q_u = x_u / ((1-c) deg(u)) packed for the
 // correction gather; IFP2: r64_d = p_d (dangling residual untouched in phase 1)
-__global__ void k_to64(DevGraph G, const Ctl *ctl, const float *x32, double *x64, double *r64, float2 *q,
-                       PVals pv, int ifp2) {
+// FP32 reserve -> double-float state (exactly) and the gather values
+// q_u = x_u / ((1-c) deg(u)) of the correction sweep; IFP2's dangling residual
+// is p (phase 1 never touches it), IFP1's comes from the sweep
+__global__ void k_to_df(DevGraph G, const Ctl *ctl, const float *x32, float2 *x, float2 *r, float2 *q, PVals pv,
+                        int ifp2) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n; i += gridDim.x * blockDim.x) {
-        const double xv = (double)x32[i];
-        x64[i] = xv;
-        if (i < G.n_nd) q[i] = df_from_d(xv * ctl->inv_om * G.inv_deg64[i]);
-        else if (ifp2) r64[i] = ctl->p_dense ? pv.p64[i] : ctl->pu;
-    }
-}
-
-// corrected FP64 state -> double-float state for the remaining rounds
-__global__ void k_64_to_df(int32_t n, const double *x64, const double *r64, float2 *x, float2 *r) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        x[i] = df_from_d(x64[i]);
-        r[i] = df_from_d(r64[i]);
+        const float2 xv = make_float2(x32[i], 0.f);
+        x[i] = xv;
+        if (i < G.n_nd) q[i] = df_mul(xv, df_mul(G.inv_degdf[i], ctl->inv_om_df));
+        else if (ifp2) r[i] = ctl->p_dense ? df_from_d(pv.p64[i]) : ctl->pu_df;
     }
 }
 
@@ -365,7 +360,6 @@ static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
     if (prec == PR_FP64) PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(float2), n, nnd, s));
     if (prec == PR_FP32) {
         PR_TRY(alloc_state(W.s32, sizeof(float), sizeof(float), n, nnd, s));
-        PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(float2), n, nnd, s));  // correction sweep
     }
     if (prec == PR_FP32 || prec == PR_DF64) {
         if (!W.sdf.din.p) PR_TRY(W.sdf.din.alloc(sizeof(double) * n, s));
@@ -762,8 +756,10 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         k_init_state<float2><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
         PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
         PR_TRY(count_rounds(0));
-        if (algo == PR_IFP1 && G.n > G.n_nd)  // pushes into dangling rows still in the inbox
+        if (algo == PR_IFP1 && G.n > G.n_nd) {  // pushes into dangling rows still in the inbox
             k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
+            launches += 1;
+        }
         finish_ifp<float2>(g, W, algo, dout, launches);
         launches += 1;
     } else {  // FP32 rounds, FP64 correction sweep, double-float rounds to the end
@@ -771,26 +767,27 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         PR_TRY(ifp_phase1<float>(g, W, algo, use_graph, prof));
         PR_TRY(count_rounds(0));
         const int32_t r32_rounds = W.hctl->round;
-        double *x64 = W.s64.x.as<double>(), *r64 = W.s64.r.as<double>();
-        k_to64<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), x64, r64, W.s64.q.as<float2>(), pv,
-                                        algo == PR_IFP2);
-        SweepArgs<double> a{};
-        a.val = W.s64.q.as<float2>();
-        a.r = r64;
-        a.x = x64;
+        float2 *xdf = W.sdf.x.as<float2>(), *rdf = W.sdf.r.as<float2>();
+        k_to_df<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), xdf, rdf, W.sdf.q.as<float2>(), pv,
+                                         algo == PR_IFP2);
+        SweepArgs<float2> a{};
+        a.val = W.sdf.q.as<float2>();
+        a.r = rdf;
+        a.x = xdf;
         a.pv = pv;
         const Plan &PL = algo == PR_IFP2 ? g->plan_nd : g->plan_all;
         k_reset_run<<<1, 1, 0, s>>>(ctl);
-        k_sweep<double, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
-        k_64_to_df<<<gn, kThreads, 0, s>>>(G.n, x64, r64, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
+        k_sweep<float2, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
         PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
         PR_TRY(count_rounds(r32_rounds));
         fp64_rounds = W.hctl->round - r32_rounds;
-        if (algo == PR_IFP1 && G.n > G.n_nd)
+        if (algo == PR_IFP1 && G.n > G.n_nd) {
             k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
+            launches += 1;
+        }
         finish_ifp<float2>(g, W, algo, dout, launches);
-        launches += 5;
+        launches += 4;  // init, to double-float, reset, correction sweep
     }
     PR_CK(cudaEventRecord(e1, s));
     if (!out_is_device) PR_CK(cudaMemcpyAsync(out, dout, sizeof(double) * G.n, cudaMemcpyDeviceToHost, s));
