@@ -81,6 +81,8 @@ def _bind(lib):
     lib.orc_ifp_sequential.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, P, i32, P, P, P, P]
     lib.orc_ifp_rounds.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32,
                                    P, P, P, P, P, P, P, P]
+    lib.orc_ifp2_levels.argtypes = [i32, P, P, dbl, dbl, dbl, P, P, i32, i32,
+                                    P, P, P, P, P, P, P, P]
     return lib
 
 
@@ -160,6 +162,55 @@ class Oracle:
         return out
 
 
+    def ifp2_levels(self, g, c, eps, p, levels, L, xi_act=None, max_rounds=100000, trace=True):
+        """IFP2 in level-ordered rounds (orc_ifp2_levels).  levels[i] in [0, L]
+        for non-dangling i (gs_levels gives the library's assignment rule).
+        Returns dict(pi, x, r, r_pending, rounds, status, R, F, E): R, F, E are
+        indexed by round (R has the decision residual of each round taken)."""
+        off, dst = _csr(g)
+        p = _f64(p)
+        n = g.n
+        if xi_act is None:
+            n_nd = int((np.diff(off) > 0).sum())
+            xi_act = eps / max(n_nd, 1)
+        lv = np.ascontiguousarray(levels, dtype=np.int32)
+        x, r, rp, pi = np.empty(n), np.empty(n), np.empty(n), np.empty(n)
+        T = max_rounds + 2
+        tR = np.zeros(T) if trace else None
+        tF = np.zeros(T, np.int64) if trace else None
+        tE = np.zeros(T, np.int64) if trace else None
+        rounds = ctypes.c_int32()
+        st = self.L.orc_ifp2_levels(n, _p(off), _p(dst), c, eps, xi_act, _p(p), _p(lv), int(L), max_rounds,
+                                    _p(x), _p(r), _p(rp), _p(pi), ctypes.byref(rounds), _p(tR), _p(tF), _p(tE))
+        k = rounds.value
+        out = dict(pi=pi, x=x, r=r, r_pending=rp, rounds=k, status=st, xi_act=xi_act)
+        if trace:
+            # decisions taken: rounds 0..k-1 and, when the stop came at the start
+            # of a synchronous round (k < 2 or status != 0 there), round k itself
+            nd = k + 1 if (k < 2 or st != 0) else k
+            out.update(R=tR[:nd].copy(), F=tF[:k].copy(), E=tE[:k].copy())
+        return out
+
+
+def gs_levels(g, L: int) -> np.ndarray:
+    """Level of every vertex for level-ordered rounds, from its degrees alone:
+    non-dangling vertices with in-edges are ranked by the integer key
+    floor(2^31 (indeg + 1) / (indeg + outdeg + 2)), ascending (vertices that
+    mostly send come first), ties by id; rank q of n_ref gets level
+    floor(q L / n_ref).  Non-dangling vertices without in-edges get level L;
+    dangling vertices -1 (never scanned in IFP2's phase 1)."""
+    outdeg = np.diff(g.out_off).astype(np.int64)
+    indeg = np.diff(g.in_off).astype(np.int64)
+    lv = np.full(g.n, -1, np.int32)
+    ref = np.nonzero((outdeg > 0) & (indeg > 0))[0]
+    key = ((indeg[ref] + 1) << 31) // (indeg[ref] + outdeg[ref] + 2)
+    order = ref[np.lexsort((ref, key))]
+    q = np.arange(order.size, dtype=np.int64)
+    lv[order] = (q * L // max(order.size, 1)).astype(np.int32)
+    lv[(outdeg > 0) & (indeg == 0)] = L
+    return lv
+
+
 _default = None
 
 
@@ -190,6 +241,10 @@ def ifp_sequential(*a, **k):
 
 def ifp_rounds(*a, **k):
     return default().ifp_rounds(*a, **k)
+
+
+def ifp2_levels(*a, **k):
+    return default().ifp2_levels(*a, **k)
 
 
 def certified_l1_bound(algo: int, c: float, R: float) -> float:

@@ -21,6 +21,9 @@
  *   orc_ifp_rounds      IFP1 / IFP2 in synchronous snapshot rounds with a
  *                       (1-c) reserve: the round semantics the GPU library
  *                       implements (reading of Sec. 3.3.1's "iteration").
+ *   orc_ifp2_levels     IFP2 in level-ordered rounds: the in-round
+ *                       propagation of Sec. 3.2's asynchronous scans, with
+ *                       levels scanned in a fixed order.
  *
  * Arrays: out_off[n+1] (int64), out_dst[m] (int32), vertex ids 0..n-1.
  * Every loop is the textbook one; nothing is blocked, fused or reordered.
@@ -252,6 +255,146 @@ int orc_ifp_sequential(int algo, int32_t n, const int64_t *out_off, const int32_
     if (scans_out) *scans_out = scans;
     if (pushes_out) *pushes_out = pushes;
     if (edges_out) *edges_out = edges;
+    return status;
+}
+
+/*
+ * IFP2 with level-ordered rounds: the asynchronous propagation of Sec. 3.2
+ * (a vertex pushes, within the same scan, mass it received earlier in that
+ * scan), made deterministic by scanning blocks of vertices ("levels") in a
+ * fixed order.  level[i] in [0, L] for every non-dangling i; dangling
+ * vertices are not scanned in phase 1 (IFP2).
+ *
+ * Rounds 0 and 1 are the synchronous rounds of orc_ifp_rounds.  A push made
+ * in any round is delivered to its target the first time the target is
+ * scanned after the push.  From round 2 on, a round scans levels 0, 1, ..., L
+ * in order; every vertex j of the level being scanned
+ *   receives its undelivered pushes;
+ *   if |r_j| > xi_act: v = r_j, x_j += (1-c) v, r_j = 0, and c v / deg(j) is
+ *   pushed to each non-dangling out-neighbour (F += 1, E += 1 per edge).
+ * A push to a vertex of a higher level arrives in the same round; one to a
+ * vertex of the same or a lower level arrives in the next round.
+ *
+ * Decisions: R_0, R_1 are the synchronous residuals at the start of rounds 0
+ * and 1.  For a round t >= 2, R_t is the residual after the round: sum over
+ * non-dangling |r| plus the pushed mass not yet delivered.  Stop when
+ * R_t <= eps (after round t >= 2 the round's pushes stand: rounds = t + 1);
+ * status 1 when max_rounds rounds ran, 2 when F_t was empty while R_t > eps.
+ * On return, r holds the delivered residual and r_pending (if not NULL) the
+ * undelivered pushes per target, so r + r_pending is the state's residual
+ * (the identity (I - cP~)(x/(1-c)) = p - (r + r_pending) holds).  Phase 2 and
+ * the finalisation are those of orc_ifp_rounds (IFP2).
+ * Traces (length >= max_rounds + 2): R_t, F_t, E_t as above.
+ */
+int orc_ifp2_levels(int32_t n, const int64_t *out_off, const int32_t *out_dst, double c, double eps,
+                    double xi_act, const double *p, const int32_t *level, int32_t L, int32_t max_rounds,
+                    double *x, double *r, double *r_pending, double *pi, int32_t *rounds_out, double *trace_R,
+                    int64_t *trace_F, int64_t *trace_E) {
+    size_t N = (size_t)(n > 0 ? n : 1);
+    double *pend = (double *)calloc(N, sizeof(double)); /* undelivered pushes per target */
+    double *v = (double *)calloc(N, sizeof(double));
+    unsigned char *active = (unsigned char *)calloc(N, 1);
+    for (int32_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = p[i]; }
+    int32_t t = 0, rounds = 0;
+    int status = 1;
+    for (;;) {
+        if (t < 2) { /* synchronous round: deliver, measure, snapshot, push into pend */
+            for (int32_t i = 0; i < n; i++) { r[i] += pend[i]; pend[i] = 0.0; }
+            double R = 0.0;
+            for (int32_t i = 0; i < n; i++)
+                if (outdeg(out_off, i) != 0) R += fabs(r[i]);
+            if (trace_R) trace_R[t] = R;
+            if (R <= eps) { status = 0; rounds = t; break; }
+            if (t >= max_rounds) { status = 1; rounds = t; break; }
+            int64_t nF = 0, nE = 0;
+            for (int32_t i = 0; i < n; i++) {
+                active[i] = outdeg(out_off, i) > 0 && fabs(r[i]) > xi_act;
+                if (!active[i]) continue;
+                v[i] = r[i];
+                x[i] += (1.0 - c) * v[i];
+                r[i] = 0.0;
+                nF++;
+            }
+            if (nF == 0) { status = 2; rounds = t; break; }
+            for (int32_t i = 0; i < n; i++) {
+                if (!active[i]) continue;
+                int64_t deg = outdeg(out_off, i);
+                for (int64_t e = out_off[i]; e < out_off[i + 1]; e++) {
+                    int32_t j = out_dst[e];
+                    if (outdeg(out_off, j) == 0) continue;
+                    pend[j] += c * v[i] / (double)deg;
+                    nE++;
+                }
+            }
+            if (trace_F) trace_F[t] = nF;
+            if (trace_E) trace_E[t] = nE;
+            t++;
+            continue;
+        }
+        if (t >= max_rounds) { status = 1; rounds = t; break; }
+        int64_t nF = 0, nE = 0;
+        for (int32_t l = 0; l <= L; l++) {
+            for (int32_t j = 0; j < n; j++) { /* the level's vertices receive (all at once) */
+                if (outdeg(out_off, j) == 0 || level[j] != l) continue;
+                r[j] += pend[j];
+                pend[j] = 0.0;
+            }
+            for (int32_t j = 0; j < n; j++) { /* and activate together */
+                active[j] = outdeg(out_off, j) > 0 && level[j] == l && fabs(r[j]) > xi_act;
+                if (!active[j]) continue;
+                v[j] = r[j];
+                x[j] += (1.0 - c) * v[j];
+                r[j] = 0.0;
+                nF++;
+            }
+            for (int32_t j = 0; j < n; j++) {
+                if (!active[j]) continue;
+                int64_t deg = outdeg(out_off, j);
+                for (int64_t e = out_off[j]; e < out_off[j + 1]; e++) {
+                    int32_t k = out_dst[e];
+                    if (outdeg(out_off, k) == 0) continue;
+                    pend[k] += c * v[j] / (double)deg;
+                    nE++;
+                }
+            }
+        }
+        double R = 0.0;
+        for (int32_t i = 0; i < n; i++)
+            if (outdeg(out_off, i) > 0) R += fabs(r[i]) + fabs(pend[i]);
+        if (trace_R) trace_R[t] = R;
+        if (trace_F) trace_F[t] = nF;
+        if (trace_E) trace_E[t] = nE;
+        if (R <= eps) { status = 0; rounds = t + 1; break; }
+        if (nF == 0) { status = 2; rounds = t + 1; break; }
+        t++;
+    }
+    if (rounds_out) *rounds_out = rounds;
+    if (r_pending)
+        for (int32_t i = 0; i < n; i++) r_pending[i] = pend[i];
+    /* IFP2 phase 2 and finalisation (as in orc_ifp_rounds) */
+    int64_t *in_off;
+    int32_t *in_src;
+    build_in_lists(n, out_off, out_dst, &in_off, &in_src);
+    for (int32_t d = 0; d < n; d++) {
+        if (outdeg(out_off, d) != 0) continue;
+        double sd = p[d];
+        for (int64_t e = in_off[d]; e < in_off[d + 1]; e++) {
+            int32_t u = in_src[e];
+            sd += c * x[u] / ((1.0 - c) * (double)outdeg(out_off, u));
+        }
+        r[d] = sd;
+    }
+    free(in_off);
+    free(in_src);
+    double total = 0.0;
+    for (int32_t i = 0; i < n; i++) {
+        pi[i] = outdeg(out_off, i) > 0 ? x[i] : (1.0 - c) * r[i];
+        total += pi[i];
+    }
+    for (int32_t i = 0; i < n; i++) pi[i] /= total;
+    free(pend);
+    free(v);
+    free(active);
     return status;
 }
 

@@ -53,6 +53,15 @@ MUTANTS = {
     "residual_wrong_sign": (
         "y[out_dst[e]] -= c * pi[i] / (double)deg;",
         "y[out_dst[e]] += c * pi[i] / (double)deg;"),
+    "levels_scanned_in_reverse": (
+        "for (int32_t l = 0; l <= L; l++) {",
+        "for (int32_t l = L; l >= 0; l--) {"),
+    "levels_push_into_dangling": (
+        "if (outdeg(out_off, k) == 0) continue;",
+        ";"),
+    "levels_residual_without_pending": (
+        "if (outdeg(out_off, i) > 0) R += fabs(r[i]) + fabs(pend[i]);",
+        "if (outdeg(out_off, i) > 0) R += fabs(r[i]);"),
     "power_off_by_one_degree": (
         "next[out_dst[e]] += c * pi[i] / (double)deg;",
         "next[out_dst[e]] += c * pi[i] / (double)(deg + 1);"),

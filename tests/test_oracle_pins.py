@@ -343,3 +343,72 @@ def test_not_converged_and_stall_status(orc):
     assert out["status"] == 1 and out["rounds"] == 4
     out = orc.ifp_rounds(IFP1, g, C, 1e-12, gg.p_uniform(5), xi_act=1.0)
     assert out["status"] == 2 and out["rounds"] == 0
+
+
+# ------------------------------------------------- level-ordered IFP2 rounds
+@pytest.mark.parametrize("n", [2, 3, 4, 9, 40])
+def test_levels_drain_a_chain_in_three_rounds(orc, n):
+    """Path 0->...->n-1 with one level per vertex (the chain's vertices tie on
+    the level key and fall in id order): two synchronous rounds, then one
+    level-ordered round carries every residual to the end, where synchronous
+    rounds need n-1 (the asynchronous scans of Sec. 3.2 on a DAG)."""
+    g = gg.chain(n)
+    p = gg.p_uniform(n)
+    y = (1 - C ** (np.arange(n) + 1)) / (n * (1 - C))
+    truth = y / y.sum()
+    L = max(n - 2, 1)
+    lv = oracle.gs_levels(g, L)
+    if n > 2:
+        assert list(lv[1:n - 1]) == list(range(n - 2)) and lv[0] == L and lv[n - 1] == -1
+    out = orc.ifp2_levels(g, C, 1e-300, p, lv, L, xi_act=0.0)
+    assert out["status"] == 0
+    assert out["rounds"] == (1 if n == 2 else 3)
+    assert l1(out["pi"], truth) < 1e-14
+    if n >= 4:  # IFP2 never pushes into the dangling end: n-2, n-3, n-4 valid edges pushed
+        assert list(out["E"]) == [n - 2, n - 3, n - 4]
+        assert list(out["F"]) == [n - 1, n - 2, n - 3]
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("L", [1, 3, 16])
+def test_levels_identity_and_bound(orc, seed, L):
+    """The state after any level-ordered round satisfies
+    r + r_pending = p + c P~ s - s on the non-dangling vertices (s = x/(1-c)),
+    and the result is within 2R/(1-c) of the exact PageRank."""
+    g = gg.random_small(200, avg_deg=5.0, dangling=0.2, unref=0.1, seed=seed)
+    p = gg.p_uniform(g.n)
+    P = sparse_P(g)
+    nd = (g.outdeg > 0).astype(float)
+    Pt = sp.diags(nd) @ P
+    lv = oracle.gs_levels(g, L)
+    truth = eig_pagerank(g, C, p)
+    for max_rounds in (2, 3, 7):
+        o = orc.ifp2_levels(g, C, 1e-30, p, lv, L, max_rounds=max_rounds)
+        assert o["status"] == 1
+        s = o["x"] / (1 - C)
+        assert l1((o["r"] + o["r_pending"]) * nd, (p + C * (Pt @ s) - s) * nd) < 1e-13
+    o = orc.ifp2_levels(g, C, 1e-10, p, lv, L)
+    assert o["status"] == 0
+    assert l1(o["pi"], truth) <= 2 * o["R"][-1] / (1 - C) + 1e-14
+    # the stop test saw the whole residual of the state: delivered and in flight
+    assert abs(o["R"][-1] - float(((np.abs(o["r"]) + np.abs(o["r_pending"])) * nd).sum())) < 1e-20
+
+
+def test_levels_assignment_rule():
+    """Ranks by floor(2^31 (in+1)/(in+out+2)), ties by id; unreferenced get L."""
+    g = gg.from_edges(6, np.array([0, 0, 0, 1, 2, 3, 4], np.int32), np.array([1, 2, 3, 2, 3, 4, 1], np.int32))
+    # in/out: v0 0/3 (unreferenced), v1 2/1, v2 2/1, v3 2/1, v4 1/1, v5 dangling, isolated
+    lv = oracle.gs_levels(g, 4)
+    assert lv[0] == 4 and lv[5] == -1
+    # keys: v4: 2/4 -> 2^30 ; v1, v2, v3: 3/5 -> floor(0.6 * 2^31): v4 first, then 1, 2, 3
+    assert list(lv[[4, 1, 2, 3]]) == [0, 1, 2, 3]
+
+
+def test_levels_fewer_rounds_than_synchronous(orc):
+    g = gg.rmat(12, 8, dangling=0.2, unref=0.1, seed=1)
+    p = gg.p_uniform(g.n)
+    sync = orc.ifp_rounds(IFP2, g, C, 1e-10, p)
+    lv = oracle.gs_levels(g, 16)
+    gs = orc.ifp2_levels(g, C, 1e-10, p, lv, 16)
+    assert gs["rounds"] < 0.75 * sync["rounds"]
+    assert l1(gs["pi"], sync["pi"]) < 2e-9
