@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--legs", default="dag,batch,serve,sweep",
                     help="extra configurations after the headline: dag (scale-24 DAG-heavy, FP32 form), "
                          "batch (512 graphs in one batch), serve (continuous batching), sweep (time and "
-                         "error against eps); '' for none")
+                         "error against eps), undirected (symmetric scale-22 graph), threads (CTA-count "
+                         "sweep); '' for none")
     return ap.parse_args()
 
 
@@ -185,7 +186,8 @@ def run_legs(args, line, pr, torch, stream, flush, hbm_peak, peak_src):
             extra[leg] = {"error": f"{type(e).__name__}: {e}"}
         extra[leg]["leg_wall_s"] = time.perf_counter() - t0
         torch.cuda.empty_cache()
-    keys = {"dag": "dag24", "batch": "batch512", "sweep": "eps_sweep", "serve": "serving"}
+    keys = {"dag": "dag24", "batch": "batch512", "sweep": "eps_sweep", "serve": "serving",
+            "undirected": "undirected22", "threads": "parallelism_sweep"}
     for leg, res in extra.items():
         line[keys.get(leg, leg)] = res
     sv = extra.get("serve", {})
@@ -508,7 +510,74 @@ def leg_sweep(pr, torch, stream, flush, hbm_peak, peak_src):
     return {"workload": "rmat22 sweep over eps, DF64", "rows": rows}
 
 
-LEGS = {"dag": leg_dag, "batch": leg_batch, "serve": leg_serve, "sweep": leg_sweep}
+def equal_l1_power(G, flush, out, truth, target, prec, pr, ref_ms):
+    """Power stopped at the first ||delta||_1 tolerance whose L1 error meets target."""
+    ladder = []
+    for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11):
+        ms, st = median_solve(G, flush, 2, C, tol, pr.PR_POWER, prec, out=out)
+        ladder.append(dict(tol=tol, ms=ms, iters=st["rounds"], l1=float((out - truth).abs().sum())))
+        if ladder[-1]["l1"] <= target:
+            return dict(ladder[-1], speedup_ifp2=ladder[-1]["ms"] / ref_ms), ladder
+    return None, ladder
+
+
+def leg_undirected(pr, torch, stream, flush, hbm_peak, peak_src):
+    """The case the paper expects to lose (a graph with no DAG structure): R-MAT
+    scale 22, edge factor 16, every sampled edge also taken reversed, no
+    deletions (no dangling or unreferenced vertex but the isolated ones);
+    IFP2 in DF64 (synchronous rounds, AUTO delivery, and level-ordered rounds
+    with 16 levels) against Power DF64 at equal L1, eps 1e-9."""
+    from graphgen import torchgen as tg
+    gd = tg.rmat(22, 16, dangling=0.0, unref=0.0, seed=1, undirected=True, device="cuda")
+    off, dst = gd.csr32()
+    G = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream, levels=16)
+    del gd, off, dst
+    torch.cuda.synchronize()
+    res = {"workload": "rmat22_undirected_ifp2_df64",
+           "graph": {k: G.info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_indeg")}}
+    G.autotune(pr.PR_DF64, max_ms=1500.0)
+    out = torch.empty(G.info["n"], dtype=torch.float64, device="cuda")
+    truth = torch.empty_like(out)
+    G.solve(C, 1e-14, pr.PR_POWER, pr.PR_FP64, out=truth)
+    for name, mode in (("auto", pr.PR_MODE_AUTO), ("levels16", pr.PR_MODE_LEVELS)):
+        ms, st = median_solve(G, flush, 3, C, 1e-9, pr.PR_IFP2, pr.PR_DF64, out=out, opts=dict(mode=mode))
+        l1 = float((out - truth).abs().sum())
+        eq, ladder = equal_l1_power(G, flush, out, truth, l1, pr.PR_DF64, pr, ms)
+        res[f"ifp2_df64_{name}"] = dict(ms=ms, rounds=st["rounds"], l1=l1, err_bound=st["err_bound"],
+                                        gedges_s=st["edges_pushed"] / ms / 1e6, power_df64_at_equal_l1=eq)
+    res["power_df64_ladder"] = ladder
+    G.close()
+    return res
+
+
+def leg_threads(pr, torch, stream, flush, hbm_peak, peak_src):
+    """The parallelism study (the paper's Fig. 3 analogue): on the headline graph,
+    the pull rounds and Power sweeps capped at B resident CTAs of 256 threads
+    (block_budget B), B from 19 to 1216; IFP2 DF64 (synchronous and 16-level
+    rounds) and Power DF64 to eps 1e-9.  The cap applies to the dominant
+    kernels; the short activation, phase-2 and finishing kernels keep their
+    grids."""
+    g = make_graph_device(22)
+    off, dst = g.csr32()
+    G = pr.Graph(g.n, g.m, off, dst, mem_is_device=True, stream=stream, levels=16)
+    del g, off, dst
+    out = torch.empty(G.info["n"], dtype=torch.float64, device="cuda")
+    rows = []
+    for budget in (19, 38, 76, 152, 304, 608, 1216):
+        G.set_tuning(block_budget=budget)
+        row = dict(ctas=budget, threads=budget * 256)
+        for name, algo, mode in (("ifp2", pr.PR_IFP2, pr.PR_MODE_AUTO), ("ifp2_levels16", pr.PR_IFP2, pr.PR_MODE_LEVELS),
+                                 ("power", pr.PR_POWER, pr.PR_MODE_AUTO)):
+            ms, st = median_solve(G, flush, 2, C, 1e-9, algo, pr.PR_DF64, out=out, opts=dict(mode=mode))
+            row[f"{name}_ms"] = ms
+            row[f"{name}_rounds"] = st["rounds"]
+        rows.append(row)
+    G.close()
+    return {"workload": "rmat22, DF64, eps 1e-9, block budget sweep", "rows": rows}
+
+
+LEGS = {"dag": leg_dag, "batch": leg_batch, "serve": leg_serve, "sweep": leg_sweep, "undirected": leg_undirected,
+        "threads": leg_threads}
 
 
 # ------------------------------------------------------------------ reference arm

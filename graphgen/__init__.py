@@ -158,12 +158,15 @@ def _finish(n, src, dst, m, seed, dangling, unref, permute, name, recipe):
 
 def rmat(scale: int, edge_factor: float = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
          dangling: float = 0.15, unref: float = 0.10, seed: int = 1, permute: bool = True,
-         dag_frac: float | None = None, nverts: int | None = None, edges: int | None = None) -> Graph:
+         dag_frac: float | None = None, nverts: int | None = None, edges: int | None = None,
+         undirected: bool = False) -> Graph:
     """Directed R-MAT graph on 2**scale vertices.
 
     `edge_factor * 2**scale` edges are sampled (or `edges` exactly); with
     `dag_frac` set, that share of edges is oriented forward in a seeded random
-    order first.  Self-loops and repeated edges are removed, then all out-edges
+    order first; with `undirected`, every sampled edge is also taken reversed
+    (a symmetric graph: no DAG structure before the deletions below).
+    Self-loops and repeated edges are removed, then all out-edges
     of a seeded `dangling` share of vertices and all in-edges of an independent
     `unref` share are deleted, and the ids are randomly relabelled.  With
     `nverts` < 2**scale, vertices >= nverts and their edges are dropped.
@@ -182,9 +185,12 @@ def rmat(scale: int, edge_factor: float = 16, a: float = 0.57, b: float = 0.19, 
         keep = (src < nverts) & (dst < nverts)
         src, dst = np.ascontiguousarray(src[keep]), np.ascontiguousarray(dst[keep])
         m, n = int(src.size), int(nverts)
+    if undirected:
+        src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
+        m = int(src.size)
     recipe = dict(kind="rmat", scale=scale, edge_factor=edge_factor, abcd=(a, b, c, 1 - a - b - c),
                   dangling=dangling, unref=unref, seed=seed, permute=permute, dag_frac=dag_frac,
-                  sampled_edges=int(m), nverts=n)
+                  sampled_edges=int(m), nverts=n, undirected=bool(undirected))
     return _finish(n, src, dst, m, seed, dangling, unref, permute, f"rmat{scale}", recipe)
 
 

@@ -194,7 +194,7 @@ def _finish(n, src, dst, seed, dangling, unref, permute, name, recipe):
 def rmat(scale: int, edge_factor: float = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
          dangling: float = 0.15, unref: float = 0.10, seed: int = 1, permute: bool = True,
          dag_frac: float | None = None, nverts: int | None = None, edges: int | None = None,
-         device="cuda") -> TGraph:
+         undirected: bool = False, device="cuda") -> TGraph:
     """graphgen.rmat on a torch device (same arguments, same graph)."""
     n = 1 << scale
     m = int(edges if edges is not None else round(edge_factor * n))
@@ -206,9 +206,12 @@ def rmat(scale: int, edge_factor: float = 16, a: float = 0.57, b: float = 0.19, 
         keep = (src < nverts) & (dst < nverts)
         src, dst = src[keep], dst[keep]
         m, n = int(src.numel()), int(nverts)
+    if undirected:
+        src, dst = torch.cat([src, dst]), torch.cat([dst, src])
+        m = int(src.numel())
     recipe = dict(kind="rmat", scale=scale, edge_factor=edge_factor, abcd=(a, b, c, 1 - a - b - c),
                   dangling=dangling, unref=unref, seed=seed, permute=permute, dag_frac=dag_frac,
-                  sampled_edges=int(m), nverts=n)
+                  sampled_edges=int(m), nverts=n, undirected=bool(undirected))
     return _finish(n, src, dst, seed, dangling, unref, permute, f"rmat{scale}", recipe)
 
 

@@ -72,7 +72,16 @@ typedef enum {
 typedef enum {
     PR_MODE_AUTO = 0, /* per round: atomic push when the frontier is small, else CSC pull */
     PR_MODE_PUSH = 1, /* always atomic push over the frontier's out-lists */
-    PR_MODE_PULL = 2  /* always deterministic gather over in-lists */
+    PR_MODE_PULL = 2, /* always deterministic gather over in-lists */
+    PR_MODE_LEVELS = 3 /* IFP2 on a graph created with levels: after two synchronous
+                          rounds, every round scans the levels in order and a push
+                          reaches a higher level in the same round -- the in-round
+                          propagation of the asynchronous scans of Sec. 3.2, made
+                          deterministic.  The round's residual R counts the pushes
+                          still in flight; the stopping rule and the certified bound
+                          are those of the other modes.  PR_EINVAL with another
+                          algorithm, on a graph without levels, and in
+                          pr_solve_batch and the server */
 } pr_mode;
 
 /*
@@ -117,6 +126,7 @@ enum {
     PR_K_PULL = 3,     /* pull rounds: gather along in-lists + next activation */
     PR_K_POWER = 4,    /* Power method iteration */
     PR_K_OTHER = 5,    /* init, correction, phase 2, finalize */
+    PR_K_LEVELS = 6,   /* level-ordered rounds (PR_MODE_LEVELS): one round's level launches together */
     PR_K_KINDS = 8
 };
 
@@ -156,6 +166,8 @@ typedef struct {
     int32_t max_outdeg, max_indeg;
     double ms_preprocess;             /* device time of pr_graph_create (Table 2 analogue) */
     size_t device_bytes;              /* graph storage held on the device */
+    int32_t levels;                   /* pr_graph_opts.levels the graph was created with */
+    int32_t pad0;
 } pr_graph_info;
 
 /*
@@ -191,6 +203,22 @@ pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
 pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                           const int32_t *in_off, const int32_t *in_src, int mem_is_device,
                           void *cuda_stream, pr_graph **g);
+
+/*
+ * Graph options (pr_graph_create_ex; NULL or zero-initialised = defaults).
+ *  levels: 0, or L in [1, 16] to prepare level-ordered rounds (PR_MODE_LEVELS):
+ *          the non-dangling vertices with in-edges are ranked by
+ *          q = floor(2^31 (indeg + 1) / (indeg + outdeg + 2)), ascending (ties
+ *          by id), and rank r of n_ref gets level floor(r L / n_ref).  Every
+ *          solve works on such a graph; only PR_MODE_LEVELS needs it.
+ */
+typedef struct {
+    int32_t levels;
+    int32_t reserved[7];
+} pr_graph_opts;
+pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
+                             const int32_t *in_off, const int32_t *in_src, int mem_is_device, void *cuda_stream,
+                             const pr_graph_opts *opts, pr_graph **g);
 
 /* Fill *info for a created graph. */
 pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);

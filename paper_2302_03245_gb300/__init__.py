@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libpr.so")
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY = range(8)
 PR_POWER, PR_IFP1, PR_IFP2 = 0, 1, 2
 PR_FP64, PR_FP32, PR_DF64 = 0, 1, 2
-PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL = 0, 1, 2
+PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL, PR_MODE_LEVELS = 0, 1, 2, 3
 STATUS_NAMES = ["PR_OK", "PR_EINVAL", "PR_ENOMEM", "PR_ECUDA", "PR_ENOTCONV", "PR_ETIMEOUT", "PR_EAGAIN",
                 "PR_EBUSY"]
 
@@ -49,10 +49,11 @@ class pr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PR_K_ACTIVATE, PR_K_COMMIT, PR_K_PUSH, PR_K_PULL, PR_K_POWER, PR_K_OTHER = range(6)
+PR_K_ACTIVATE, PR_K_COMMIT, PR_K_PUSH, PR_K_PULL, PR_K_POWER, PR_K_OTHER, PR_K_LEVELS = range(7)
 PR_K_KINDS = 8
 KERNEL_NAMES = {PR_K_ACTIVATE: "k_activate", PR_K_COMMIT: "k_commit", PR_K_PUSH: "k_push",
-                PR_K_PULL: "k_round_pull", PR_K_POWER: "k_sweep<OP_POWER>", PR_K_OTHER: "other"}
+                PR_K_PULL: "k_round_pull", PR_K_POWER: "k_sweep<OP_POWER>", PR_K_OTHER: "other",
+                PR_K_LEVELS: "k_round_levels"}
 
 
 class pr_kernel_profile(ctypes.Structure):
@@ -70,11 +71,15 @@ class pr_opts(ctypes.Structure):
                 ("trace_mode", ctypes.c_void_p), ("profile", ctypes.POINTER(pr_kernel_profile))]
 
 
+class pr_graph_opts(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
 class pr_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_nd", ctypes.c_int32), ("n_ref", ctypes.c_int32),
                 ("n_d", ctypes.c_int32), ("n_u", ctypes.c_int32), ("m", ctypes.c_int64), ("m_d", ctypes.c_int64),
                 ("max_outdeg", ctypes.c_int32), ("max_indeg", ctypes.c_int32), ("ms_preprocess", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("levels", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +125,9 @@ def lib() -> ctypes.CDLL:
         P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.pr_graph_create.argtypes = [i32, i64, P, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.pr_graph_create.restype = ctypes.c_int
+        L.pr_graph_create_ex.argtypes = [i32, i64, P, P, P, P, ctypes.c_int, P, ctypes.POINTER(pr_graph_opts),
+                                         ctypes.POINTER(P)]
+        L.pr_graph_create_ex.restype = ctypes.c_int
         L.pr_graph_get_info.argtypes = [P, ctypes.POINTER(pr_graph_info)]
         L.pr_graph_get_info.restype = ctypes.c_int
         L.pr_graph_get_tuning.argtypes = [P, ctypes.POINTER(pr_tuning)]
@@ -190,14 +198,18 @@ def pr_version() -> str:
 
 
 def pr_graph_create(n: int, m: int, out_off, out_dst, in_off=None, in_src=None, mem_is_device: bool = False,
-                    stream=None) -> ctypes.c_void_p:
-    """Wraps pr_graph_create.  Arrays are int32 numpy (host) or torch (device)."""
+                    stream=None, levels: int = 0) -> ctypes.c_void_p:
+    """Wraps pr_graph_create_ex.  Arrays are int32 numpy (host) or torch (device);
+    levels > 0 prepares level-ordered rounds (PR_MODE_LEVELS)."""
     for a in (out_off, out_dst, in_off, in_src):
         if isinstance(a, np.ndarray) and (a.dtype != np.int32 or not a.flags.c_contiguous):
             raise TypeError("graph arrays must be contiguous int32")
     g = ctypes.c_void_p()
-    _check(lib().pr_graph_create(int(n), int(m), _ptr(out_off), _ptr(out_dst), _ptr(in_off), _ptr(in_src),
-                                 1 if mem_is_device else 0, _stream_handle(stream), ctypes.byref(g)))
+    o = pr_graph_opts()
+    o.levels = int(levels)
+    _check(lib().pr_graph_create_ex(int(n), int(m), _ptr(out_off), _ptr(out_dst), _ptr(in_off), _ptr(in_src),
+                                    1 if mem_is_device else 0, _stream_handle(stream), ctypes.byref(o),
+                                    ctypes.byref(g)))
     return g
 
 
@@ -483,8 +495,9 @@ def use_torch_allocator(enable: bool = True) -> None:
 class Graph:
     """RAII wrapper: pr_graph_create on construction, pr_destroy on close."""
 
-    def __init__(self, n, m, out_off, out_dst, in_off=None, in_src=None, mem_is_device=False, stream=None):
-        self.h = pr_graph_create(n, m, out_off, out_dst, in_off, in_src, mem_is_device, stream)
+    def __init__(self, n, m, out_off, out_dst, in_off=None, in_src=None, mem_is_device=False, stream=None,
+                 levels=0):
+        self.h = pr_graph_create(n, m, out_off, out_dst, in_off, in_src, mem_is_device, stream, levels)
         self.info = pr_graph_get_info(self.h)
 
     def solve(self, c, eps, algo, prec=PR_FP64, **kw):

@@ -131,8 +131,65 @@ static __global__ void k_indeg(int64_t m, const int32_t *dst, int32_t *indeg) {
         atomicAdd(&indeg[dst[e]], 1);
 }
 
+// Level of every non-dangling vertex with in-edges (level-ordered rounds):
+// ranked by q = floor(2^31 (indeg + 1) / (indeg + outdeg + 2)), ascending,
+// ties by id (the key packs both); the others sort after them.
+static __global__ void k_level_keys(int32_t n, const int32_t *off, const int32_t *indeg, uint64_t *keys,
+                                    unsigned int *n_ref) {
+    __shared__ unsigned int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    unsigned int c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int64_t deg = off[i + 1] - off[i], id = indeg[i];
+        if (deg > 0 && id > 0) {
+            const uint64_t q = ((uint64_t)(id + 1) << 31) / (uint64_t)(id + deg + 2);
+            keys[i] = (q << 32) | (uint64_t)(uint32_t)i;
+            c++;
+        } else {
+            keys[i] = ~0ULL;
+        }
+    }
+    if (c) atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt) atomicAdd(n_ref, cnt);
+}
+
+// rank r of n_ref (sorted keys) -> level floor(r L / n_ref)
+static __global__ void k_assign_levels(const uint64_t *sorted, int32_t n_ref, int32_t L, int32_t *level) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_ref; r += gridDim.x * blockDim.x)
+        level[(int32_t)(sorted[r] & 0xFFFFFFFFu)] = (int32_t)(((int64_t)r * L) / n_ref);
+}
+
+// valid out-edges of each non-dangling row into its own or a lower level (the
+// pushes a level-ordered round leaves for the next round); rows without
+// in-edges are scanned last, so all their pushes wait
+static __global__ void k_level_back(int32_t n_ref, int32_t n_nd, const int32_t *out_off, const int32_t *out_dst,
+                                    const int32_t *ndeg, const int32_t *lo, int32_t L, int32_t *back) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nd; j += gridDim.x * blockDim.x) {
+        if (j >= n_ref) {
+            back[j] = ndeg[j];
+            continue;
+        }
+        int a = 0, b = L - 1;  // the level of row j: the last l with lo[l] <= j
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (lo[mid] <= j) a = mid;
+            else b = mid - 1;
+        }
+        const int32_t end = lo[a + 1];
+        int32_t x = out_off[j], y = out_off[j] + ndeg[j];  // valid targets, ascending
+        while (x < y) {
+            const int32_t mid = x + ((y - x) >> 1);
+            if (out_dst[mid] < end) x = mid + 1;
+            else y = mid;
+        }
+        back[j] = x - out_off[j];
+    }
+}
+
 // class 0: deg>0 & indeg>0, class 1: deg>0 & indeg==0, class 2: deg==0
-static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_t *indeg,
+static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_t *indeg, const int32_t *level,
                                      uint64_t *keys, int32_t *vals, unsigned int *class_cnt) {
     __shared__ unsigned int cnt[3];
     if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
@@ -143,7 +200,8 @@ static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_
         int32_t deg = off[i + 1] - off[i];
         int32_t id = indeg[i];
         uint32_t cls = deg == 0 ? 2u : (id == 0 ? 1u : 0u);
-        keys[i] = ((uint64_t)cls << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
+        const uint64_t lev = (cls == 0 && level) ? (uint64_t)level[i] : 0;  // level-ordered graphs
+        keys[i] = ((uint64_t)cls << 40) | (lev << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
         vals[i] = i;
         local[cls]++;
     }
@@ -289,26 +347,26 @@ static __global__ void k_degree_facts(int32_t n, int32_t n_nd, const int32_t *pe
 }
 
 // bins[k] = number of rows in [lo, hi) (in-degree sorted descending) with indeg > thr[k]
-// first row in [lo, hi) whose in-degree (ref + unref segments) is <= thr[k]:
-// the rows of a class are sorted by in-degree, descending
-static __global__ void k_bin_bounds(const int32_t *inr_off, const int32_t *inu_off, int32_t lo, int32_t hi,
-                                    const int32_t *thr, int nthr, int32_t *bounds) {
-    int k = threadIdx.x;
+// range blockIdx.x [lo, hi): the first row whose in-degree (ref + unref
+// segments) is <= thr[k]; the rows of a range are sorted by in-degree, descending
+static __global__ void k_bin_bounds(const int32_t *inr_off, const int32_t *inu_off, const int32_t *lo,
+                                    const int32_t *hi, const int32_t *thr, int nthr, int32_t *bounds) {
+    const int k = threadIdx.x;
     if (k >= nthr) return;
-    int32_t a = lo, b = hi;
+    int32_t a = lo[blockIdx.x], b = hi[blockIdx.x];
     while (a < b) {
         int32_t mid = a + ((b - a) >> 1);
         const int32_t d = (inr_off[mid + 1] - inr_off[mid]) + (inu_off[mid + 1] - inu_off[mid]);
         if (d > thr[k]) a = mid + 1;
         else b = mid;
     }
-    bounds[k] = a;
+    bounds[blockIdx.x * nthr + k] = a;
 }
 
 // edges of the ref+unref in-list segments in [lo, hi) of rows (for block budgets)
 static __global__ void k_range_edges(const int32_t *inr_off, const int32_t *inu_off, const int32_t *rows,
                                      int nrows, long long *edges) {
-    int k = threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nrows) return;
     edges[k] = (long long)inr_off[rows[k]] + inu_off[rows[k]];
 }
@@ -394,18 +452,45 @@ static int class_ranges(int32_t lo, int32_t hi, const int32_t *bounds, const lon
 }
 
 void build_plans(pr_graph *g) {
-    const int32_t n = g->G.n, n_nd = g->G.n_nd, n_ref = g->G.n_ref;
-    // edges_at layout: [0..5] at bound_ref, [6..11] at bound_d, [12] row 0, [13] n_ref, [14] n_nd, [15] n
-    const long long *E = g->edges_at;
-    RangeSpec nd[kNumThr + 2], d[kNumThr + 1], all[2 * kNumThr + 3];
-    int k1 = class_ranges(0, n_ref, g->bound_ref, &E[12], &E[0], E[13], nd);
-    nd[k1++] = RangeSpec{n_ref, n_nd, 1, E[14] - E[13]};
-    int k2 = class_ranges(n_nd, n, g->bound_d, &E[14], &E[6], E[15], d);
-    for (int k = 0; k < k1; k++) all[k] = nd[k];
-    for (int k = 0; k < k2; k++) all[k1 + k] = d[k];
-    g->plan_nd = make_plan(nd, k1, g->block_budget);
-    g->plan_d = make_plan(d, k2, g->block_budget);
-    g->plan_all = make_plan(all, k1 + k2, g->block_budget);
+    const int32_t n_nd = g->G.n_nd, n_ref = g->G.n_ref;
+    const int nr = g->nranges;  // referenced ranges (levels), then the dangling range
+    std::vector<RangeSpec> ref, d, lvl[kMaxLevels];
+    for (int k = 0; k < nr; k++) {
+        const long long *E = &g->range_edges[(size_t)k * (kNumThr + 2)];
+        RangeSpec rs[kNumThr + 1];
+        class_ranges(g->range_lo[k], g->range_hi[k], &g->bounds[(size_t)k * kNumThr], &E[0], &E[1], E[kNumThr + 1],
+                     rs);
+        for (const RangeSpec &r : rs) {
+            if (k < nr - 1) {
+                ref.push_back(r);
+                if (g->levels) lvl[k].push_back(r);
+            } else {
+                d.push_back(r);
+            }
+        }
+    }
+    // unreferenced rows (no in-edges): one lane each; their in-lists are empty
+    const long long e_ref_end = g->range_edges[(size_t)(nr - 2) * (kNumThr + 2) + kNumThr + 1];
+    const long long e_nd = g->range_edges[(size_t)(nr - 1) * (kNumThr + 2)];
+    const RangeSpec unref{n_ref, n_nd, 1, e_nd - e_ref_end};
+    std::vector<RangeSpec> nd = ref, all = ref;
+    nd.push_back(unref);
+    all.push_back(unref);
+    all.insert(all.end(), d.begin(), d.end());
+    g->plan_nd = make_plan(nd.data(), (int)nd.size(), g->block_budget);
+    g->plan_d = make_plan(d.data(), (int)d.size(), g->block_budget);
+    g->plan_all = make_plan(all.data(), (int)all.size(), g->block_budget);
+    // level-ordered rounds launch one level at a time, and a latency-bound
+    // gather needs the whole GPU's resident warps: every level gets the full
+    // block budget (capped so the round's launches fit the partial-sum slots);
+    // a small level is limited by its row groups in make_plan
+    if (g->levels) {
+        const int cap = std::max(32, kMaxBlocks / (g->levels + 1) - kNumThr - 2);  // make_plan adds <= 1 per segment
+        const int b = std::min(g->block_budget, cap);
+        for (int l = 0; l < g->levels; l++) g->plan_lvl[l] = make_plan(lvl[l].data(), (int)lvl[l].size(), b);
+        const std::vector<RangeSpec> u{unref};
+        g->plan_unref = make_plan(u.data(), 1, b);
+    }
 }
 
 pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t s) {
@@ -415,54 +500,90 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
             return fail(PR_EINVAL, "pull thresholds must be >= 0 and non-increasing");
     }
     if (budget < 1 || budget > kMaxBlocks / 2) return fail(PR_EINVAL, "block budget out of range");
-    Buf small;
-    PR_TRY(small.alloc(512, s));
-    int32_t *d_thr = small.as<int32_t>();                               // [6]
-    int32_t *d_bounds = d_thr + 8;                                      // [12]
-    int32_t *d_rows = d_thr + 24;                                       // [16]
-    long long *d_edges = reinterpret_cast<long long *>(d_thr + 48);     // [16]
+    // the ranges: the referenced class (or its levels), then the dangling class
+    int32_t lo[kMaxLevels + 1], hi[kMaxLevels + 1];
+    int nr = 0;
+    if (g->levels) {
+        for (int l = 0; l < g->levels; l++) {
+            lo[nr] = g->level_lo[l];
+            hi[nr++] = g->level_lo[l + 1];
+        }
+    } else {
+        lo[nr] = 0;
+        hi[nr++] = n_ref;
+    }
+    lo[nr] = n_nd;
+    hi[nr++] = n;
+    Buf small, ebuf;
+    const size_t rows_n = (size_t)nr * (kNumThr + 2);
+    PR_TRY(small.alloc(sizeof(int32_t) * (8 + 2 * (kMaxLevels + 1) + nr * kNumThr + rows_n), s));
+    PR_TRY(ebuf.alloc(sizeof(long long) * rows_n, s));
+    int32_t *d_thr = small.as<int32_t>();           // [6]
+    int32_t *d_lo = d_thr + 8;                      // [nr]
+    int32_t *d_hi = d_lo + (kMaxLevels + 1);        // [nr]
+    int32_t *d_bounds = d_hi + (kMaxLevels + 1);    // [nr * 6]
+    int32_t *d_rows = d_bounds + nr * kNumThr;      // [nr * 8]
+    long long *d_edges = ebuf.as<long long>();      // [nr * 8]
     PR_CK(cudaMemcpyAsync(d_thr, thr, sizeof(int32_t) * kNumThr, cudaMemcpyHostToDevice, s));
-    k_bin_bounds<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), 0, n_ref, d_thr, kNumThr,
-                                  d_bounds);
-    k_bin_bounds<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), n_nd, n, d_thr, kNumThr,
-                                  d_bounds + kNumThr);
-    int32_t b[2 * kNumThr];
-    PR_CK(cudaMemcpyAsync(b, d_bounds, sizeof(b), cudaMemcpyDeviceToHost, s));
+    PR_CK(cudaMemcpyAsync(d_lo, lo, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+    PR_CK(cudaMemcpyAsync(d_hi, hi, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+    k_bin_bounds<<<nr, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_lo, d_hi, d_thr, kNumThr,
+                                   d_bounds);
+    std::vector<int32_t> b((size_t)nr * kNumThr);
+    PR_CK(cudaMemcpyAsync(b.data(), d_bounds, sizeof(int32_t) * b.size(), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaStreamSynchronize(s));
-    int32_t rows[2 * kNumThr + 4];
-    for (int k = 0; k < 2 * kNumThr; k++) rows[k] = b[k];
-    rows[12] = 0;
-    rows[13] = n_ref;
-    rows[14] = n_nd;
-    rows[15] = n;
-    long long edges[16];
-    PR_CK(cudaMemcpyAsync(d_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, s));
-    k_range_edges<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_rows, 16, d_edges);
-    PR_CK(cudaMemcpyAsync(edges, d_edges, sizeof(edges), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> rows(rows_n);
+    for (int k = 0; k < nr; k++) {
+        rows[(size_t)k * (kNumThr + 2)] = lo[k];
+        for (int t = 0; t < kNumThr; t++) rows[(size_t)k * (kNumThr + 2) + 1 + t] = b[(size_t)k * kNumThr + t];
+        rows[(size_t)k * (kNumThr + 2) + kNumThr + 1] = hi[k];
+    }
+    std::vector<long long> edges(rows_n);
+    PR_CK(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * rows_n, cudaMemcpyHostToDevice, s));
+    k_range_edges<<<(int)((rows_n + 31) / 32), 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(),
+                                                           d_rows, (int)rows_n, d_edges);
+    PR_CK(cudaMemcpyAsync(edges.data(), d_edges, sizeof(long long) * rows_n, cudaMemcpyDeviceToHost, s));
     PR_CK(cudaStreamSynchronize(s));
     PR_CK(cudaGetLastError());
-    pr_graph T = {};  // plans are built into a scratch copy first: the graph keeps its bins on failure
-    for (int k = 0; k < kNumThr; k++) {
-        T.thr[k] = thr[k];
-        T.bound_ref[k] = b[k];
-        T.bound_d[k] = b[kNumThr + k];
+    // plans are built into a scratch copy first: the graph keeps its bins on failure
+    pr_graph *T = new (std::nothrow) pr_graph();
+    if (!T) return fail(PR_ENOMEM, "host allocation failed");
+    T->G = g->G;
+    T->levels = g->levels;
+    for (int l = 0; l <= kMaxLevels; l++) T->level_lo[l] = g->level_lo[l];
+    T->nranges = nr;
+    for (int k = 0; k < nr; k++) {
+        T->range_lo[k] = lo[k];
+        T->range_hi[k] = hi[k];
     }
-    for (int k = 0; k < 16; k++) T.edges_at[k] = edges[k];
-    T.block_budget = budget;
-    T.G = g->G;
-    build_plans(&T);
-    if (T.plan_all.nblocks > kMaxBlocks || T.plan_nd.nblocks > kMaxBlocks)
+    for (size_t k = 0; k < b.size(); k++) T->bounds[k] = b[k];
+    for (size_t k = 0; k < rows_n; k++) T->range_edges[k] = edges[k];
+    T->block_budget = budget;
+    build_plans(T);
+    bool ok = T->plan_all.nblocks <= kMaxBlocks && T->plan_nd.nblocks <= kMaxBlocks;
+    int lvl_blocks = T->plan_unref.nblocks;
+    for (int l = 0; l < T->levels; l++) lvl_blocks += T->plan_lvl[l].nblocks;
+    ok = ok && lvl_blocks <= kMaxBlocks;
+    if (!ok) {
+        delete T;
         return fail(PR_EINVAL, "pull plan exceeds the partial-sum slots");
-    for (int k = 0; k < kNumThr; k++) {
-        g->thr[k] = T.thr[k];
-        g->bound_ref[k] = T.bound_ref[k];
-        g->bound_d[k] = T.bound_d[k];
     }
-    for (int k = 0; k < 16; k++) g->edges_at[k] = T.edges_at[k];
+    for (int k = 0; k < kNumThr; k++) g->thr[k] = thr[k];
+    g->nranges = nr;
+    for (int k = 0; k <= kMaxLevels; k++) {
+        g->range_lo[k] = T->range_lo[k];
+        g->range_hi[k] = T->range_hi[k];
+    }
+    for (size_t k = 0; k < sizeof(g->bounds) / sizeof(g->bounds[0]); k++) g->bounds[k] = T->bounds[k];
+    for (size_t k = 0; k < sizeof(g->range_edges) / sizeof(g->range_edges[0]); k++)
+        g->range_edges[k] = T->range_edges[k];
     g->block_budget = budget;
-    g->plan_nd = T.plan_nd;
-    g->plan_d = T.plan_d;
-    g->plan_all = T.plan_all;
+    g->plan_nd = T->plan_nd;
+    g->plan_d = T->plan_d;
+    g->plan_all = T->plan_all;
+    for (int l = 0; l < kMaxLevels; l++) g->plan_lvl[l] = T->plan_lvl[l];
+    g->plan_unref = T->plan_unref;
+    delete T;
     return PR_OK;
 }
 
@@ -533,7 +654,7 @@ pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int e
 
 pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                       const int32_t *in_off, const int32_t *in_src, int mem_is_device,
-                      cudaStream_t s, pr_graph *g) {
+                      cudaStream_t s, int32_t levels, pr_graph *g) {
     int dev = 0;
     PR_CK(cudaGetDevice(&dev));
     int sms = 0;
@@ -598,16 +719,32 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_TRY(vk2.alloc(sizeof(uint64_t) * n, s));
     PR_TRY(vv.alloc(sizeof(int32_t) * n, s));
     PR_TRY(vv2.alloc(sizeof(int32_t) * n, s));
-    k_vertex_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), vk.as<uint64_t>(),
-                                          vv.as<int32_t>(), class_cnt);
     Temp tmp;
+    Buf level;
+    if (levels > 0) {  // levels of the referenced class (level-ordered rounds)
+        PR_TRY(level.alloc(sizeof(int32_t) * n, s));
+        unsigned int *lvl_cnt = class_cnt + 3;
+        k_level_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), vk.as<uint64_t>(), lvl_cnt);
+        size_t bytes = 0;
+        PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, vk.as<uint64_t>(), vk2.as<uint64_t>(), n, 0, 64, s));
+        PR_TRY(tmp.need(bytes, s));
+        PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, vk.as<uint64_t>(), vk2.as<uint64_t>(), n, 0, 64, s));
+        unsigned int h_ref = 0;
+        PR_CK(cudaMemcpyAsync(&h_ref, lvl_cnt, sizeof(h_ref), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        if (h_ref)
+            k_assign_levels<<<grid_for(h_ref, sms), kThreads, 0, s>>>(vk2.as<uint64_t>(), (int32_t)h_ref, levels,
+                                                                    level.as<int32_t>());
+    }
+    k_vertex_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), levels > 0 ? level.as<int32_t>() : nullptr,
+                                          vk.as<uint64_t>(), vv.as<int32_t>(), class_cnt);
     {
         cub::DoubleBuffer<uint64_t> dk(vk.as<uint64_t>(), vk2.as<uint64_t>());
         cub::DoubleBuffer<int32_t> dv(vv.as<int32_t>(), vv2.as<int32_t>());
         size_t bytes = 0;
-        PR_CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, dk, dv, n, 0, 34, s));
+        PR_CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, dk, dv, n, 0, 42, s));
         PR_TRY(tmp.need(bytes, s));
-        PR_CK(cub::DeviceRadixSort::SortPairs(tmp.b.p, bytes, dk, dv, n, 0, 34, s));
+        PR_CK(cub::DeviceRadixSort::SortPairs(tmp.b.p, bytes, dk, dv, n, 0, 42, s));
         PR_TRY(g->perm.alloc(sizeof(int32_t) * n, s));
         PR_CK(cudaMemcpyAsync(g->perm.p, dv.Current(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
@@ -621,6 +758,9 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_CK(cudaMemcpyAsync(hc, class_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaStreamSynchronize(s));
     const int32_t n_ref = (int32_t)hc[0], n_nd = (int32_t)(hc[0] + hc[1]);
+    g->levels = levels;
+    for (int l = 0; l <= levels; l++)  // level l holds the ranks [ceil(l n_ref / L), ceil((l+1) n_ref / L))
+        g->level_lo[l] = (int32_t)(((int64_t)l * n_ref + levels - 1) / levels);
 
     // out-lists in internal ids
     Buf ek, ek2;
@@ -684,6 +824,18 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
         k_vertex_arrays<<<grid_for(n_nd, sms), kThreads, 0, s>>>(
             n_nd, g->out_off.as<int32_t>(), g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
             g->inv_deg64.as<double>(), g->inv_deg32.as<float>(), g->inv_degdf.as<float2>());
+    if (levels > 0) {
+        Buf d_lo;
+        PR_TRY(d_lo.alloc(sizeof(int32_t) * (kMaxLevels + 1), s));
+        PR_CK(cudaMemcpyAsync(d_lo.p, g->level_lo, sizeof(int32_t) * (levels + 1), cudaMemcpyHostToDevice, s));
+        PR_TRY(g->gs_back.alloc(sizeof(int32_t) * std::max(n_nd, 1), s));
+        if (n_nd)
+            k_level_back<<<grid_for(n_nd, sms), kThreads, 0, s>>>(n_ref, n_nd, g->out_off.as<int32_t>(),
+                                                                  g->out_dst.as<int32_t>(), g->ndeg.as<int32_t>(),
+                                                                  d_lo.as<int32_t>(), levels,
+                                                                  g->gs_back.as<int32_t>());
+        PR_CK(cudaStreamSynchronize(s));  // d_lo is freed at the end of this scope
+    }
     Buf indeg_int;
     PR_TRY(indeg_int.alloc(sizeof(int32_t) * n, s));
     k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, g->perm.as<int32_t>(), indeg.as<int32_t>(),
@@ -719,6 +871,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     G.inu_src = g->inu_src.as<int32_t>();
     G.perm = g->perm.as<int32_t>();
     G.inv = g->inv.as<int32_t>();
+    G.gs_back = levels > 0 ? g->gs_back.as<int32_t>() : nullptr;
     g->scan_nd_ref = hnd[0];
     g->scan_nd_unref = hnd[1];
     g->pull_ratio = 0.04;
@@ -741,17 +894,18 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     I.max_outdeg = hm[0];
     I.max_indeg = hm[1];
     I.ms_preprocess = ms;
+    I.levels = levels;
     I.device_bytes = g->out_off.bytes + g->out_dst.bytes + g->ndeg.bytes + g->inv_deg64.bytes +
                      g->inv_deg32.bytes + g->inv_degdf.bytes + g->inr_off.bytes + g->inr_src.bytes + g->inu_off.bytes +
-                     g->inu_src.bytes + g->perm.bytes + g->inv.bytes;
+                     g->inu_src.bytes + g->perm.bytes + g->inv.bytes + g->gs_back.bytes;
     return PR_OK;
 }
 }  // namespace
 
-extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off,
+extern "C" pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out_off,
                                      const int32_t *out_dst, const int32_t *in_off,
                                      const int32_t *in_src, int mem_is_device, void *cuda_stream,
-                                     pr_graph **g) {
+                                     const pr_graph_opts *opts, pr_graph **g) {
     if (!g) return fail(PR_EINVAL, "pr_graph_create: g is NULL");
     *g = nullptr;
     if (n < 1) return fail(PR_EINVAL, "n must be >= 1");
@@ -759,6 +913,8 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_of
     if (!out_off || (m > 0 && !out_dst)) return fail(PR_EINVAL, "out_off/out_dst missing");
     if (!in_off && in_src) return fail(PR_EINVAL, "in_src given without in_off");
     if (in_off && m > 0 && !in_src) return fail(PR_EINVAL, "in_off given without in_src");
+    const int32_t levels = opts ? opts->levels : 0;
+    if (levels < 0 || levels > kMaxLevels) return fail(PR_EINVAL, "levels must be in [0, 16]");
     if (!mem_is_device) {  // host arrays are checked before any CUDA call
         PR_TRY(validate_host(n, m, out_off, out_dst));
         if (in_off) PR_TRY(validate_host(n, m, in_off, in_src));
@@ -768,7 +924,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_of
     static std::atomic<uint64_t> serial{0};
     G->uid = ++serial;
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
-                               (cudaStream_t)cuda_stream, G);
+                               (cudaStream_t)cuda_stream, levels, G);
     if (st != PR_OK) {
         std::string msg = pr_last_error();
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
@@ -779,4 +935,10 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_of
     }
     *g = G;
     return PR_OK;
+}
+
+extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
+                                     const int32_t *in_off, const int32_t *in_src, int mem_is_device,
+                                     void *cuda_stream, pr_graph **g) {
+    return pr_graph_create_ex(n, m, out_off, out_dst, in_off, in_src, mem_is_device, cuda_stream, nullptr, g);
 }

@@ -77,6 +77,7 @@ struct DevGraph {
     const int32_t *inu_src;   // [m_unref]
     const int32_t *perm;      // [n] internal -> caller id
     const int32_t *inv;       // [n] caller id -> internal
+    const int32_t *gs_back;   // [n_nd] level-ordered graphs: valid out-edges into the row's own or a lower level
 };
 
 // Row ranges of a gather kernel, by work-group size.  Rows inside each
@@ -89,7 +90,8 @@ struct Seg {
     int32_t blk0;     // first block of this segment
     int32_t nblk;     // blocks assigned
 };
-constexpr int kMaxSeg = 16;
+constexpr int kMaxSeg = 128;   // levels x 7 bins + the unreferenced rows + 7 dangling bins
+constexpr int kMaxLevels = 16;  // levels of level-ordered rounds
 struct Plan {
     Seg seg[kMaxSeg];
     int32_t nseg;
@@ -121,9 +123,20 @@ struct pr_graph {
     // pull bins: row boundaries of the in-degree sorted classes and the in-list
     // entries in front of each boundary (ref + unref segments)
     int32_t thr[pr::kNumThr] = {};
-    int32_t bound_ref[pr::kNumThr] = {}, bound_d[pr::kNumThr] = {};
-    long long edges_at[2 * pr::kNumThr + 4] = {};
+    // Bin ranges: the referenced class (one range, or one per level), then the
+    // dangling class; each range sorted by in-degree, split at 6 bounds.
+    // ranges[k] = {lo, hi}; bounds[6k..6k+5]; edges at lo, bounds, hi.
+    int32_t nranges = 0;
+    int32_t range_lo[pr::kMaxLevels + 1] = {}, range_hi[pr::kMaxLevels + 1] = {};
+    int32_t bounds[(pr::kMaxLevels + 1) * pr::kNumThr] = {};
+    long long range_edges[(pr::kMaxLevels + 1) * (pr::kNumThr + 2)] = {};
     int32_t block_budget = 0;
+    // level-ordered rounds (pr_graph_opts.levels): the referenced class is cut
+    // into `levels` contiguous row ranges [level_lo[l], level_lo[l+1])
+    int32_t levels = 0;
+    int32_t level_lo[pr::kMaxLevels + 1] = {};
+    pr::Buf gs_back;  // [n_nd] valid out-edges of a row into its own or a lower level
+    pr::Plan plan_lvl[pr::kMaxLevels]{}, plan_unref{};
     double pull_ratio = 0.04;  // AUTO push/pull switch used when a solve passes 0
     int64_t scan_nd_ref = 0, scan_nd_unref = 0;  // in-list entries of the non-dangling rows, per segment
     pr::Plan plan_nd{}, plan_d{}, plan_all{};

@@ -49,6 +49,7 @@
 namespace pr {
 
 enum { MODE_ACT = 0, MODE_PUSH = 1, MODE_PULL = 2 };
+constexpr int POLICY_LEVELS = 3;  // PR_MODE_LEVELS: level-ordered pull rounds
 
 struct Ctl {
     // parameters (host-written per solve), in every format the kernels use
@@ -73,6 +74,10 @@ struct Ctl {
     float gamma_f, pad4;
     float2 gamma_df, zinv_df;
     int32_t iter, pad2;
+    // level-ordered rounds: the kind of the next pull round (0 synchronous,
+    // 1 the first level-ordered round, 2 level-ordered, 3 commit only: the
+    // round cap stops the run at the start of the first level-ordered round)
+    int32_t gs_phase, pad6;
 };
 
 struct Partials {
@@ -495,7 +500,7 @@ __device__ __forceinline__ void round_decision(Ctl *ctl, int t, double R, long l
     }
     int mode;
     if (ctl->policy == MODE_PUSH) mode = MODE_PUSH;
-    else if (ctl->policy == MODE_PULL) mode = MODE_PULL;
+    else if (ctl->policy == MODE_PULL || ctl->policy == POLICY_LEVELS) mode = MODE_PULL;
     else mode = (want && (double)E < ctl->pull_edges) ? MODE_PUSH : MODE_PULL;
     ctl->mode = mode;
     ctl->cur = t;
@@ -843,6 +848,301 @@ __global__ void __launch_bounds__(kThreads, PR_PULL_MIN_BLOCKS) k_round_pull(Dev
     E = block_sum(E, shl);
     u = __syncthreads_or(u);
     if (threadIdx.x == 0) round_decision(ctl, t, Rsum, F, E, u, want, tr);
+}
+
+// ------------------------------------------------------------ level-ordered rounds (IFP2)
+// One launch serves one level's rows (plan of the level); the launches of a
+// round run in level order, the rows without in-edges last, and the last
+// launch takes the round's decision over the partial slots of all of them.
+struct LevelLaunch {
+    int32_t split;       // sources below this id belong to lower levels
+    int32_t slot_base;   // this launch's first partial slot
+    int32_t slot_total;  // slots of the whole round (read by the deciding launch)
+    int32_t decide;      // the round's last launch
+};
+
+// sums of a row's pending pushes: sources of lower levels pushed in this round
+// (wcur; in the first level-ordered round also in the previous one, which was
+// synchronous and delivered nothing in-round), the others in the previous
+// round (wprev).  Each lane adds its entries in order; ROWS rows and U entries
+// per row are in flight at once, as in row_sums.
+template <typename V, int ROWS, int U>
+__device__ __forceinline__ void level_row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
+                                               const int *js, const bool *valid, const V *__restrict__ wcur,
+                                               const V *__restrict__ wprev, int split, bool both, int start,
+                                               int step, typename GT<V>::A *acc) {
+    int e[ROWS], b[ROWS];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        e[r] = 0;
+        b[r] = 0;
+        if (valid[r]) {
+            e[r] = __ldg(&off[js[r]]) + start;
+            b[r] = __ldg(&off[js[r] + 1]);
+        }
+        any |= e[r] < b[r];
+    }
+    while (any) {
+        int idx[ROWS][U];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++)
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int ee = e[r] + u * step;
+                idx[r][u] = ee < b[r] ? __ldcs(&src[ee]) : -1;
+            }
+        any = false;
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int i = idx[r][u];
+                if (i < 0) continue;
+                if (i < split) {
+                    acc[r] = GT<V>::add(acc[r], __ldg(&wcur[i]));
+                    if (both) acc[r] = GT<V>::add(acc[r], __ldg(&wprev[i]));
+                } else {
+                    acc[r] = GT<V>::add(acc[r], __ldg(&wprev[i]));
+                }
+            }
+            e[r] += U * step;
+            any |= e[r] < b[r];
+        }
+    }
+}
+
+// a level-ordered row: [deferred commit of the synchronous round before] +
+// delivery + activation committed at once; R counts the residual left and the
+// pushes into the row's own or lower levels (in flight until the next round)
+template <typename T>
+__device__ __forceinline__ void level_row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                                   typename ST<T>::V *wcur, int j, T in, bool deferred,
+                                                   typename ST<T>::R &Rl, long long &Fl, long long &El) {
+    T *x = static_cast<T *>(B.x);
+    T *r = static_cast<T *>(B.r);
+    T v = r[j];
+    if (deferred && is_active(v, ctl)) {  // commit of the synchronous round's activation
+        x[j] = ST<T>::add(x[j], ST<T>::mul(ST<T>::om(ctl), v));
+        v = ST<T>::zero();
+    }
+    const T rn = ST<T>::add(v, in);
+    if (is_active(rn, ctl)) {
+        x[j] = ST<T>::add(x[j], ST<T>::mul(ST<T>::om(ctl), rn));
+        r[j] = ST<T>::zero();
+        const T w = ST<T>::mul(rn, ST<T>::mul(ST<T>::c(ctl), ST<T>::invdeg(G, j)));
+        wcur[j] = ST<T>::pack(w);
+        Fl++;
+        El += G.ndeg[j];
+        Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::mul(ST<T>::absv(w), ST<T>::pack_from_d((double)G.gs_back[j]))));
+    } else {
+        r[j] = rn;
+        wcur[j] = ST<T>::pack(ST<T>::zero());
+        Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(rn)));
+    }
+}
+
+// Rows of one level's plan segment, LANES threads per row, ROWS rows per lane
+// group at a time (as round_rows).  Phase 0: a synchronous round (deferred
+// commit); phases 1 and 2: level-ordered.  The segment of unreferenced
+// sources is read only in the synchronous round: from the level-ordered
+// rounds on, those sources have nothing left to push.
+template <typename T, int LANES>
+__device__ __forceinline__ void level_rows(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                           const RoundBuf &B, const typename ST<T>::V *wprev,
+                                           typename ST<T>::V *wcur, int phase, int split,
+                                           typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    constexpr int GPB = kThreads / LANES;
+    constexpr int ROWS = RowsInFlight<LANES>::value;
+    constexpr int U = EntriesInFlight<LANES>::value;
+    const int grp = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    const int stride = S.nblk * GPB;
+    const bool both = phase == 1;
+    for (int base = S.lo + lb * GPB; base < S.hi; base += ROWS * stride) {
+        int js[ROWS];
+        bool valid[ROWS];
+        A acc[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            js[r] = base + r * stride + grp;
+            valid[r] = js[r] < S.hi;
+            acc[r] = GT<V>::zero();
+        }
+        level_row_sums<V, ROWS, U>(G.inr_off, G.inr_src, js, valid, wcur, wprev, split, both, lane, LANES, acc);
+        if (phase == 0)
+            level_row_sums<V, ROWS, U>(G.inu_off, G.inu_src, js, valid, wcur, wprev, split, both, lane, LANES, acc);
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+#pragma unroll
+            for (int o = LANES / 2; o > 0; o >>= 1) acc[r] = GT<V>::add(acc[r], GT<V>::shfl_down(acc[r], o, LANES));
+            if (valid[r] && lane == 0) {
+                if (phase == 0) {
+                    int pd = 0;
+                    pull_row_epilogue<T, true>(G, ctl, B, wcur, js[r], ST<T>::from_acc(acc[r]), 0, pd, Rl, Fl, El,
+                                               ul);
+                } else {
+                    level_row_epilogue<T>(G, ctl, B, wcur, js[r], ST<T>::from_acc(acc[r]), phase == 1, Rl, Fl, El);
+                }
+            }
+        }
+    }
+}
+
+// the decision after a round of level launches (t = the round just run)
+__device__ __forceinline__ void level_decision(Ctl *ctl, int t, int phase, double R, long long F, long long E,
+                                               int u, const Trace &tr) {
+    if (phase == 0) {  // a synchronous round: R is its start-of-round residual
+        round_decision(ctl, t, R, F, E, u, 0, tr);
+        // a cap at round t + 1 stops at its start: that round only commits
+        if (!ctl->done) ctl->gs_phase = t + 1 >= ctl->max_rounds ? 3 : 1;
+        return;
+    }
+    if (phase == 3) {
+        ctl->ticket = 0;
+        ctl->done = 1;
+        ctl->status = 1;
+        return;
+    }
+    // a level-ordered round ran whole: its pushes stand, R is the residual
+    // left after it (in flight included)
+    ctl->ticket = 0;
+    ctl->R = R;
+    ctl->F = F;
+    ctl->E = E;
+    if (t < ctl->trace_cap) {
+        tr.R[t] = R;
+        tr.F[t] = F;
+        tr.E[t] = E;
+        tr.mode[t] = (int8_t)MODE_PULL;
+    }
+    ctl->pushes += F;
+    ctl->edges_pushed += E;
+    ctl->edges_scanned += ctl->scan_ref + ctl->scan_unref;
+    ctl->rounds_pull++;
+    ctl->round = t + 1;
+    ctl->cur = t;
+    if (R <= ctl->eps) {
+        ctl->done = 1;
+        ctl->status = 0;
+    } else if (F == 0) {
+        ctl->done = 1;
+        ctl->status = 2;
+    } else if (t + 1 >= ctl->max_rounds) {
+        ctl->done = 1;
+        ctl->status = 1;
+    } else {
+        ctl->gs_phase = 2;
+        ctl->unref_active = 0;
+    }
+}
+
+// the level kernel reads two pending-push arrays per row: at 6 blocks per SM
+// (40 registers) it spills, at 5 (48 registers) it does not
+#ifndef PR_LEVEL_MIN_BLOCKS
+#define PR_LEVEL_MIN_BLOCKS 5
+#endif
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(DevGraph G, Plan PL, Ctl *ctl,
+                                                                              Partials P, RoundBuf B, Trace tr,
+                                                                              LevelLaunch lv) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    using R = typename ST<T>::R;
+    if (ctl->done || ctl->mode != MODE_PULL) return;
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    __shared__ A sha[32];
+    __shared__ R shr[32];
+    const int t = ctl->round;
+    const int phase = ctl->gs_phase;
+    const V *wprev = static_cast<const V *>((t & 1) ? B.w[0] : B.w[1]);  // written by round t - 1
+    V *wcur = static_cast<V *>((t & 1) ? B.w[1] : B.w[0]);
+    const int split = phase ? lv.split : 0;
+    R Rl = ST<T>::rzero();
+    long long Fl = 0, El = 0;
+    int ul = 0;
+    if (phase == 3 && PL.nseg > 0) {  // commit of the synchronous round's activation, nothing else
+        T *x = static_cast<T *>(B.x);
+        T *r = static_cast<T *>(B.r);
+        for (int j = PL.seg[0].lo + blockIdx.x * blockDim.x + threadIdx.x; j < PL.seg[PL.nseg - 1].hi;
+             j += gridDim.x * blockDim.x) {
+            const T v = r[j];
+            if (is_active(v, ctl)) {
+                x[j] = ST<T>::add(x[j], ST<T>::mul(ST<T>::om(ctl), v));
+                r[j] = ST<T>::zero();
+            }
+        }
+    } else if (PL.nseg > 0) {
+        int lo = 0, hi = PL.nseg - 1;  // the last segment with blk0 <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (PL.seg[mid].blk0 <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        const Seg S = PL.seg[lo];
+        const int lb = blockIdx.x - S.blk0;
+        switch (S.lanes) {
+            case 1: level_rows<T, 1>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            case 2: level_rows<T, 2>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            case 4: level_rows<T, 4>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            case 8: level_rows<T, 8>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            case 16: level_rows<T, 16>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            case 32: level_rows<T, 32>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
+            default:
+                for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
+                    const bool ok = true;
+                    A acc = GT<V>::zero();
+                    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, &j, &ok, wcur, wprev, split, phase == 1,
+                                            threadIdx.x, blockDim.x, &acc);
+                    if (phase == 0)
+                        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, &j, &ok, wcur, wprev, split, false,
+                                                threadIdx.x, blockDim.x, &acc);
+                    acc = block_sum_gt<V>(acc, sha);
+                    if (threadIdx.x == 0) {
+                        if (phase == 0) {
+                            int pd = 0;
+                            pull_row_epilogue<T, true>(G, ctl, B, wcur, j, ST<T>::from_acc(acc), 0, pd, Rl, Fl, El,
+                                                       ul);
+                        } else {
+                            level_row_epilogue<T>(G, ctl, B, wcur, j, ST<T>::from_acc(acc), phase == 1, Rl, Fl, El);
+                        }
+                    }
+                }
+        }
+    }
+    const R Rb = block_sum_r<T>(Rl, shr);
+    const long long Fb = block_sum(Fl, shl);
+    const long long Eb = block_sum(El, shl);
+    const int ub = __syncthreads_or(ul);
+    const int slot = lv.slot_base + blockIdx.x;
+    if (threadIdx.x == 0) {
+        memcpy(reinterpret_cast<char *>(P.a) + 8 * (size_t)slot, &Rb, 8);
+        P.F[slot] = Fb;
+        P.E[slot] = Eb;
+        P.u[slot] = ub;
+    }
+    if (!lv.decide || !last_block(&ctl->ticket)) return;
+    const unsigned long long *pa = reinterpret_cast<const unsigned long long *>(P.a);
+    double Rs = 0.0;
+    long long F = 0, E = 0;
+    int u = 0;
+    for (int k = threadIdx.x; k < lv.slot_total; k += blockDim.x) {
+        R v;
+        const unsigned long long bits = __ldcg(pa + k);
+        memcpy(&v, &bits, 8);
+        Rs += ST<T>::r_to_d(v);
+        F += __ldcg(&P.F[k]);
+        E += __ldcg(&P.E[k]);
+        u |= __ldcg(&P.u[k]);
+    }
+    Rs = block_sum(Rs, shd);
+    F = block_sum(F, shl);
+    E = block_sum(E, shl);
+    u = __syncthreads_or(u);
+    if (threadIdx.x == 0) level_decision(ctl, t, phase, Rs, F, E, u, tr);
 }
 
 // ------------------------------------------------------------ sweeps: Power, correction, phase 2

@@ -67,8 +67,9 @@ __global__ void k_reset_run(Ctl *ctl) {
     ctl->mode = MODE_ACT;
     ctl->bin_cnt[0][0] = ctl->bin_cnt[0][1] = ctl->bin_cnt[0][2] = 0;
     ctl->bin_cnt[1][0] = ctl->bin_cnt[1][1] = ctl->bin_cnt[1][2] = 0;
-    ctl->want_bins = ctl->policy != MODE_PULL;
+    ctl->want_bins = ctl->policy != MODE_PULL && ctl->policy != POLICY_LEVELS;
     ctl->unref_active = 1;
+    ctl->gs_phase = 0;
 }
 
 __global__ void k_set_while(const Ctl *ctl, cudaGraphConditionalHandle h) {
@@ -226,7 +227,7 @@ struct Prof {
                 mode = (k >= 0 && k < (int)modes.size()) ? modes[k] : MODE_PULL;
                 next_round = t + 1;
             };
-            if (r.kind == PR_K_PULL && mode == MODE_PULL) {
+            if ((r.kind == PR_K_PULL || r.kind == PR_K_LEVELS) && mode == MODE_PULL) {
                 charge(r);
                 activate();
             } else if (r.kind == PR_K_PUSH && mode == MODE_PUSH) {
@@ -396,6 +397,10 @@ template <typename T> static int round_key();
 template <> int round_key<float>() { return 0; }
 template <> int round_key<double>() { return 2; }
 template <> int round_key<float2>() { return 4; }
+template <typename T> static int level_key();
+template <> int level_key<float>() { return 6; }
+template <> int level_key<double>() { return 7; }
+template <> int level_key<float2>() { return 8; }
 template <typename T> static int power_key();
 template <> int power_key<float>() { return 10; }
 template <> int power_key<double>() { return 11; }
@@ -426,6 +431,38 @@ static void launch_round(pr_graph *g, Workspace &W, cudaStream_t s, Prof *prof) 
         prof->add(PR_K_PULL, e0, e1);
         prof->add(PR_K_PUSH, e1, e2);
         prof->add(PR_K_ACTIVATE, e2, e3);
+    }
+}
+
+// One level-ordered round (IFP2, PR_MODE_LEVELS): one k_round_levels launch per
+// level in level order, then the rows without in-edges, whose launch takes the
+// round's decision over the partial slots of all of them.  Round 0 is the
+// activation of p (k_activate); the push kernel never runs in this mode.
+template <typename T>
+static void launch_round_levels(pr_graph *g, Workspace &W, cudaStream_t s, Prof *prof) {
+    const DevGraph &G = g->G;
+    Ctl *ctl = W.ctl.as<Ctl>();
+    const Partials P = partials_of(W);
+    const Trace tr = trace_of(W);
+    const RoundBuf B = round_bufs<T>(W);
+    int total = g->plan_unref.nblocks;
+    for (int l = 0; l < g->levels; l++) total += g->plan_lvl[l].nblocks;
+    const size_t e0 = prof ? prof->mark(s) : 0;
+    int base = 0;
+    for (int l = 0; l < g->levels; l++) {
+        const Plan &PL = g->plan_lvl[l];
+        k_round_levels<T><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, P, B, tr,
+                                                          LevelLaunch{g->level_lo[l], base, total, 0});
+        base += PL.nblocks;
+    }
+    k_round_levels<T><<<g->plan_unref.nblocks, kThreads, 0, s>>>(G, g->plan_unref, ctl, P, B, tr,
+                                                                 LevelLaunch{G.n_ref, base, total, 1});
+    const size_t e1 = prof ? prof->mark(s) : 0;
+    k_activate<T, true><<<grid_n(G.n_nd, g->num_sms, 8), kThreads, 0, s>>>(G, ctl, P, B, tr);
+    if (prof) {
+        const size_t e2 = prof->mark(s);
+        prof->add(PR_K_LEVELS, e0, e1);
+        prof->add(PR_K_ACTIVATE, e1, e2);
     }
 }
 
@@ -463,12 +500,16 @@ static pr_status while_graph(Workspace &W, int key, Ctl *ctl, F body, cudaStream
 // Rounds until the device stop flag is set: inside a CUDA-graph while node
 // (kUnroll rounds per body, no host synchronisation), or host-driven chunks.
 template <typename T, bool IFP2>
-static pr_status run_rounds(pr_graph *g, Workspace &W, bool use_graph, Prof *prof) {
+static pr_status run_rounds(pr_graph *g, Workspace &W, bool use_graph, bool levels, Prof *prof) {
     cudaStream_t s = g->stream;
     Ctl *ctl = W.ctl.as<Ctl>();
+    auto round = [&](cudaStream_t cs, Prof *pf) {
+        if (levels) launch_round_levels<T>(g, W, cs, pf);
+        else launch_round<T, IFP2>(g, W, cs, pf);
+    };
     if (use_graph && !prof)
-        return while_graph(W, round_key<T>() + (IFP2 ? 1 : 0), ctl, [&](cudaStream_t cs) {
-            for (int k = 0; k < kUnroll; k++) launch_round<T, IFP2>(g, W, cs, nullptr);
+        return while_graph(W, levels ? level_key<T>() : round_key<T>() + (IFP2 ? 1 : 0), ctl, [&](cudaStream_t cs) {
+            for (int k = 0; k < kUnroll; k++) round(cs, nullptr);
         }, s);
     int t0 = 0;
     if (prof) {
@@ -482,12 +523,15 @@ static pr_status run_rounds(pr_graph *g, Workspace &W, bool use_graph, Prof *pro
     int chunk = 2;
     std::vector<int8_t> modes;
     for (;;) {
-        for (int k = 0; k < chunk; k++) launch_round<T, IFP2>(g, W, s, prof);
+        for (int k = 0; k < chunk; k++) round(s, prof);
         PR_CK(cudaGetLastError());
         PR_CK(cudaMemcpyAsync(&W.hctl->done, &ctl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaMemcpyAsync(&W.hctl->gs_phase, &ctl->gs_phase, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
-        const int done = W.hctl->done, last = W.hctl->round;
+        const int done = W.hctl->done;
+        // a level-ordered round that stops has already advanced the round index
+        const int last = W.hctl->round - ((done && W.hctl->gs_phase) ? 1 : 0);
         if (prof) {
             const int hi = std::min(last, W.trace_len);
             modes.assign(std::max(hi - t0, 0), 0);
@@ -622,9 +666,9 @@ static pr_status setup_p(pr_graph *g, Workspace &W, const pr_pvec *p, Ctl &h, do
 
 // ------------------------------------------------------------ solve
 template <typename T>
-static pr_status ifp_phase1(pr_graph *g, Workspace &W, int algo, bool use_graph, Prof *prof) {
-    if (algo == PR_IFP2) return run_rounds<T, true>(g, W, use_graph, prof);
-    return run_rounds<T, false>(g, W, use_graph, prof);
+static pr_status ifp_phase1(pr_graph *g, Workspace &W, int algo, bool use_graph, bool levels, Prof *prof) {
+    if (algo == PR_IFP2) return run_rounds<T, true>(g, W, use_graph, levels, prof);
+    return run_rounds<T, false>(g, W, use_graph, false, prof);
 }
 
 // After phase 1 in format T: IFP1 dangling-mass report, IFP2 phase 2, then normalisation.
@@ -687,7 +731,10 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
     if (opt.pull_ratio <= 0) opt.pull_ratio = g->pull_ratio;
-    if (opt.mode < 0 || opt.mode > 2) return fail(PR_EINVAL, "unknown mode");
+    if (opt.mode < 0 || opt.mode > PR_MODE_LEVELS) return fail(PR_EINVAL, "unknown mode");
+    const bool levels = opt.mode == PR_MODE_LEVELS;
+    if (levels && algo != PR_IFP2) return fail(PR_EINVAL, "PR_MODE_LEVELS runs IFP2 only");
+    if (levels && g->levels <= 0) return fail(PR_EINVAL, "PR_MODE_LEVELS needs a graph created with levels");
     if (opt.xi_act < 0) return fail(PR_EINVAL, "xi_act must be >= 0");
     const bool use_graph = opt.use_graph >= 0;  // 0 = default (on); -1 = host-driven rounds
     Prof prof_obj;
@@ -719,8 +766,9 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     h.scan_ref = algo == PR_IFP2 ? g->scan_nd_ref : G.m_ref;
     h.scan_unref = algo == PR_IFP2 ? g->scan_nd_unref : G.m_unref;
     h.mode = MODE_ACT;
-    h.want_bins = opt.mode != MODE_PULL;
+    h.want_bins = opt.mode == PR_MODE_AUTO || opt.mode == PR_MODE_PUSH;
     h.unref_active = 1;
+    h.gs_phase = 0;
     *W.hctl = h;
     Ctl *ctl = W.ctl.as<Ctl>();
     PR_CK(cudaMemcpyAsync(ctl, W.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -735,10 +783,13 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     int64_t launches = 0;
     auto count_rounds = [&](int first_round) -> pr_status {
         PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaMemcpyAsync(&W.hctl->gs_phase, &ctl->gs_phase, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
-        const int64_t acts = W.hctl->round - first_round + 1;
+        // a stop in a level-ordered round counts that round (round = t + 1)
+        const int64_t acts = W.hctl->round - first_round + (W.hctl->gs_phase ? 0 : 1);
         const int64_t bodies = (acts + kUnroll - 1) / kUnroll;
-        launches += (use_graph && !prof) ? bodies * (kUnroll * kRoundLaunches + 1) : acts * kRoundLaunches;
+        const int per_round = levels ? g->levels + 2 : kRoundLaunches;
+        launches += (use_graph && !prof) ? bodies * (kUnroll * per_round + 1) : acts * per_round;
         return PR_OK;
     };
     if (algo == PR_POWER) {
@@ -747,14 +798,14 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         else PR_TRY(solve_power<float2>(g, W, use_graph, prof, dout, launches));
     } else if (prec == PR_FP64) {
         k_init_state<double><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s64.x.as<double>(), W.s64.r.as<double>());
-        PR_TRY(ifp_phase1<double>(g, W, algo, use_graph, prof));
+        PR_TRY(ifp_phase1<double>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(0));
         finish_ifp<double>(g, W, algo, dout, launches);
         launches += 1;
     } else if (prec == PR_DF64) {
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
         k_init_state<float2><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
-        PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
+        PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(0));
         if (algo == PR_IFP1 && G.n > G.n_nd) {  // pushes into dangling rows still in the inbox
             k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
@@ -764,7 +815,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         launches += 1;
     } else {  // FP32 rounds, FP64 correction sweep, double-float rounds to the end
         k_init_state<float><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s32.x.as<float>(), W.s32.r.as<float>());
-        PR_TRY(ifp_phase1<float>(g, W, algo, use_graph, prof));
+        PR_TRY(ifp_phase1<float>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(0));
         const int32_t r32_rounds = W.hctl->round;
         float2 *xdf = W.sdf.x.as<float2>(), *rdf = W.sdf.r.as<float2>();
@@ -779,7 +830,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         k_reset_run<<<1, 1, 0, s>>>(ctl);
         k_sweep<float2, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
-        PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, prof));
+        PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(r32_rounds));
         fp64_rounds = W.hctl->round - r32_rounds;
         if (algo == PR_IFP1 && G.n > G.n_nd) {

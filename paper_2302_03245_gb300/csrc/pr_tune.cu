@@ -25,14 +25,19 @@ void fill_tuning(const pr_graph *g, pr_tuning *t) {
     for (int k = 0; k < kNumThr; k++) t->pull_thr[k] = g->thr[k];
     t->block_budget = g->block_budget;
     t->pull_ratio = g->pull_ratio;
-    // rows per bin of the non-dangling rows: the referenced class is split at
-    // bound_ref; the unreferenced rows (no in-edges) run one lane each
-    int32_t a = 0;
-    for (int k = 0; k < kNumThr; k++) {
-        t->bin_rows[k] = g->bound_ref[k] - a;
-        a = g->bound_ref[k];
+    // rows per bin of the non-dangling rows: each referenced range (the class,
+    // or each of its levels) is split at its 6 bounds; the unreferenced rows
+    // (no in-edges) run one lane each
+    for (int k = 0; k < g->nranges - 1; k++) {
+        int32_t a = g->range_lo[k];
+        for (int t2 = 0; t2 < kNumThr; t2++) {
+            const int32_t b = g->bounds[k * kNumThr + t2];
+            t->bin_rows[t2] += b - a;
+            a = b;
+        }
+        t->bin_rows[kNumThr] += g->range_hi[k] - a;
     }
-    t->bin_rows[kNumThr] = g->G.n_nd - a;
+    t->bin_rows[kNumThr] += g->G.n_nd - g->G.n_ref;
     t->pull_blocks = g->plan_nd.nblocks;
 }
 

@@ -17,7 +17,8 @@ def same(a, b):
 
 @pytest.mark.parametrize("kw", [dict(scale=10), dict(scale=12, dag_frac=0.7, dangling=0.25),
                                 dict(scale=11, nverts=1500, edge_factor=12), dict(scale=9, permute=False),
-                                dict(scale=8, edge_factor=4, dangling=0.0, unref=0.0, seed=7)])
+                                dict(scale=8, edge_factor=4, dangling=0.0, unref=0.0, seed=7),
+                                dict(scale=10, undirected=True, dangling=0.1, unref=0.0)])
 def test_rmat_same_graph(kw, monkeypatch):
     monkeypatch.setattr(tg, "CHUNK", 1000)  # several passes with a ragged last one
     assert same(gg.rmat(**kw), tg.rmat(device="cpu", **kw))
@@ -43,3 +44,14 @@ def test_stats_and_host_copy():
     assert b.stats() == a.stats()
     assert same(a, b.to_host().__class__(b.n, *[torch.from_numpy(x) for x in (
         b.to_host().out_off, b.to_host().out_dst, b.to_host().in_off, b.to_host().in_src)]))
+
+
+def test_undirected_rmat_is_symmetric():
+    """Without deletions every edge comes with its reverse; no vertex is
+    dangling or unreferenced unless it is isolated."""
+    g = gg.rmat(11, 8, dangling=0.0, unref=0.0, undirected=True, seed=3)
+    src = np.repeat(np.arange(g.n), np.diff(g.out_off))
+    fwd = set(zip(src.tolist(), g.out_dst.tolist()))
+    assert fwd == {(d, s) for s, d in fwd}
+    outdeg, indeg = np.diff(g.out_off), np.diff(g.in_off)
+    assert np.array_equal(outdeg, indeg)
