@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--serve-max", type=int, default=400, help="requests per rate at most")
     ap.add_argument("--algo", default="ifp2", choices=["ifp2", "ifp1", "power"],
                     help="algorithm of the timed steps (ifp2 = the headline)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="prepare the graph with this many levels and run the timed IFP2 steps in "
+                         "level-ordered rounds (PR_MODE_LEVELS); 0 = synchronous rounds (the headline)")
     ap.add_argument("--skip-extras", action="store_true", help="only the timed IFP2 steps")
     ap.add_argument("--host-rounds", action="store_true",
                     help="launch rounds from the host instead of the CUDA-graph while loop (same kernels; "
@@ -68,11 +71,13 @@ def parse():
     return ap.parse_args()
 
 
-def workload(scale, algo="ifp2"):
-    return dict(workload=f"rmat{scale}_{algo}_df64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
+def workload(scale, algo="ifp2", levels=0):
+    lv = f"_levels{levels}" if levels and algo == "ifp2" else ""
+    return dict(workload=f"rmat{scale}_{algo}{lv}_df64", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
                 vertices=1 << scale, edge_factor=16, sampled_edges=16 << scale, dangling_deleted=0.20,
                 unref_deleted=0.10, relabel="seeded random permutation", seed=1, c=C, p="uniform",
-                algo=algo.upper() if algo != "power" else "Power", precision="df64", eps=1e-9)
+                algo=algo.upper() if algo != "power" else "Power", precision="df64", eps=1e-9,
+                rounds="level-ordered, %d levels" % levels if lv else "synchronous")
 
 
 def make_graph(scale):
@@ -299,6 +304,19 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
         eq = next((q for q in ladder if q["l1"] <= target), None)
         if eq:
             res[f"power_{pname}_at_equal_l1"] = dict(eq, speedup_ifp2=eq["ms"] / res["ifp2_fp32_auto"]["ms"])
+    G.close()
+    # level-ordered rounds on the same graph, prepared with 8 levels
+    gd = tg.rmat(24, 16, dangling=0.25, unref=0.0, seed=1, dag_frac=0.7, device="cuda")
+    off, dst = gd.csr32()
+    G = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream, levels=8)
+    del gd, off, dst
+    G.autotune(pr.PR_FP32, max_ms=2000.0)
+    for name, prec in (("fp32", pr.PR_FP32), ("df64", pr.PR_DF64)):
+        for mname, mode in (("auto", pr.PR_MODE_AUTO), ("levels8", pr.PR_MODE_LEVELS)):
+            ms, st = median_solve(G, flush, 2, C, eps, pr.PR_IFP2, prec, out=out, opts=dict(mode=mode))
+            res[f"leveled_graph_ifp2_{name}_{mname}"] = dict(ms=ms, rounds=st["rounds"], fp64_rounds=st["fp64_rounds"],
+                                                            l1=float((out - truth).abs().sum()),
+                                                            err_bound=st["err_bound"])
     G.close()
     return res
 
@@ -657,7 +675,7 @@ def main():
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - tgen0
     n_v, m_e = gd.n, gd.m
-    G = pr.Graph(n_v, m_e, d_off, d_dst, mem_is_device=True, stream=stream)
+    G = pr.Graph(n_v, m_e, d_off, d_dst, mem_is_device=True, stream=stream, levels=args.levels)
     g = gd.to_host()  # for the host-side legs (e2e copies, the oracle)
     del gd
     info = G.info
@@ -680,6 +698,8 @@ def main():
         opts = dict(opts or {})
         if args.host_rounds:
             opts.setdefault("use_graph", -1)
+        if args.levels and algo == pr.PR_IFP2:
+            opts.setdefault("mode", pr.PR_MODE_LEVELS)
         _, st, status = G.solve(C, eps, algo, prec, out=out, opts=opts)
         assert status == pr.PR_OK, st
         return st
@@ -718,7 +738,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "df64 (fp32 hi+lo pairs; fp64 final sums and output)",
             "data": "synthetic",
-            "config": dict(workload(args.scale, args.algo), l2="512 MB buffer written between timed steps",
+            "config": dict(workload(args.scale, args.algo, args.levels), l2="512 MB buffer written between timed steps",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "gpu_launches": int(launches), "clocks": clk,
             "graph": {k: info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_outdeg",
@@ -763,7 +783,7 @@ def main():
     scan_ref = pull_scan_total / max(len(pull_rounds), 1)
     kernels = {k: dict(launches=v["launches"] // prof_runs, avg_ms=v["ms"] / max(v["launches"], 1),
                        share=v["ms"] / total_k_ms) for k, v in agg.items()}
-    if dom == "k_round_pull":
+    if dom in ("k_round_pull", "k_round_levels"):  # a level-ordered round reads the in-lists once too
         F = trace["F"][pull_rounds].astype(np.float64)
         rows = info["n_nd"]
         bytes_per = [algorithmic_bytes_pull_round(info, s, scan_ref, rows, f) for f in F]
@@ -777,7 +797,7 @@ def main():
     line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (copy bandwidth)",
                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
-                        "traffic": recorded_traffic(dom, workload(args.scale, args.algo)["workload"]),
+                        "traffic": recorded_traffic(dom, workload(args.scale, args.algo, args.levels)["workload"]),
                         "timing": "CUDA events around every launch on the graph's stream, instrumented pass"}
     line["kernels"] = kernels
 
@@ -871,7 +891,7 @@ def main():
     # ---- default launch parameters against the tuned ones (same solve)
     if not args.no_tune:
         tuned = G.tuning()
-        G.set_tuning(pull_thr=[4096, 32, 16, 8, 4, 2], block_budget=info_sms(torch) * 16, pull_ratio=0.04)
+        G.set_tuning(pull_thr=[4096, 64, 32, 16, 8, 4], block_budget=info_sms(torch) * 16, pull_ratio=0.04)
         tms = []
         for _ in range(3):
             flush.zero_()

@@ -55,8 +55,11 @@ typedef enum {
 } pr_algo;
 
 typedef enum {
-    PR_FP64 = 0, /* residual, reserve and pushed mass in IEEE double (on GB300 the
-                    FP64 pipe runs at 1/64 of FP32: the reference form, slow) */
+    PR_FP64 = 0, /* residual, reserve, sums and output in IEEE double; the values a
+                    gather reads per source (pending pushes, Power's pi/deg) are
+                    stored as double-float pairs (48-bit significand, 8 bytes).
+                    On GB300 the FP64 pipe runs at 1/64 of FP32: the reference
+                    form, slow */
     PR_FP32 = 1, /* residual, reserve and pushed mass in float; sums of the
                     residual L1 and dangling mass in double-float with a final
                     FP64 sum; at the end a correction sweep recomputes the
@@ -230,6 +233,12 @@ pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);
  *  pull_thr:     in-degree thresholds of the gather bins, non-increasing, >= 0.
  *                Rows with in-degree above pull_thr[0] get a whole block; above
  *                pull_thr[1..5] they get 32, 16, 8, 4, 2 lanes; the rest 1 lane.
+ *                When pull_thr[1] <= 64, the single-solve kernels gather the
+ *                rows at or below pull_thr[1] by tiles instead: a block stages
+ *                up to 2048 in-list values of consecutive rows in shared
+ *                memory and one thread sums each row there (the batch engine
+ *                and the server keep the lane bins).  Default {4096, 64, 32,
+ *                16, 8, 4}.
  *  block_budget: blocks of a dense gather launch, split across the bins in
  *                proportion to their in-list entries (1 .. 8192).
  *  pull_ratio:   the AUTO delivery switch used when a solve passes

@@ -909,6 +909,7 @@ struct ServerImpl {
     // per-graph tile templates (prob index filled in when a table is built)
     struct Tiles {
         std::vector<Tile> round, vert, dang;
+        uint64_t plan_gen = 0;  // the graph's plans they were cut from
     };
     std::unordered_map<uint64_t, Tiles> tiles;  // by pr_graph::uid
     // device tables of the current step (grow-only)
@@ -920,8 +921,10 @@ struct ServerImpl {
 
     const Tiles &tiles_of(pr_graph *g) {
         auto it = tiles.find(g->uid);
-        if (it != tiles.end()) return it->second;
+        if (it != tiles.end() && it->second.plan_gen == g->plan_gen) return it->second;
+        if (it != tiles.end()) tiles.erase(it);  // retuned since: cut again
         Tiles T;
+        T.plan_gen = g->plan_gen;
         cut_plan(g->plan_nd, 0, T.round);
         if (T.round.empty()) T.round.push_back(Tile{0, 0, 0, 1});
         cut_rows(0, g->G.n, 0, T.vert);

@@ -400,6 +400,34 @@ static int bits_for(int32_t n) {
     return B;
 }
 
+// ------------------------------------------------------------ gather tiles
+// in-list offsets at the first and last tiled row of each range
+static __global__ void k_tile_ends(const int32_t *inr_off, const int32_t *lo, const int32_t *hi, int nr,
+                                   int32_t *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    out[2 * k] = lo[k] < hi[k] ? inr_off[lo[k]] : 0;
+    out[2 * k + 1] = lo[k] < hi[k] ? inr_off[hi[k] - 1] : 0;
+}
+
+// unit position of row j of a tiled range (entries before it plus kTileW per row)
+__device__ __forceinline__ long long tile_unit(const int32_t *inr_off, int32_t lo, int32_t e_lo, int32_t j) {
+    return (long long)(inr_off[j] - e_lo) + (long long)kTileW * (j - lo);
+}
+
+// tab[t] = first row of tile t, tab[nt] = hi: rows whose first unit lies in
+// [t U, (t+1) U) form tile t; a row spans fewer than U units, so every tile
+// index up to the last row's gets exactly one first row
+static __global__ void k_tile_marks(const int32_t *inr_off, int32_t lo, int32_t hi, int32_t *tab) {
+    const int32_t e_lo = inr_off[lo];
+    for (int32_t j = lo + blockIdx.x * blockDim.x + threadIdx.x; j < hi; j += gridDim.x * blockDim.x) {
+        const long long t = tile_unit(inr_off, lo, e_lo, j) / kTileU;
+        const bool first = j == lo || tile_unit(inr_off, lo, e_lo, j - 1) / kTileU != t;
+        if (first) tab[t] = j;
+        if (j == hi - 1) tab[t + 1] = hi;
+    }
+}
+
 // ------------------------------------------------------------ plans
 // Blocks go to segments in proportion to their work (in-list entries + 2 per
 // row), at most as many as the segment has row groups, within a budget of
@@ -407,6 +435,7 @@ static int bits_for(int32_t n) {
 struct RangeSpec {
     int32_t lo, hi, lanes;
     long long edges;
+    int32_t t0 = 0, nt = 0;  // gather tiles (lanes == kTileLanes)
 };
 
 static Plan make_plan(const RangeSpec *r, int nr, int budget) {
@@ -419,8 +448,8 @@ static Plan make_plan(const RangeSpec *r, int nr, int budget) {
         if (r[k].hi <= r[k].lo) continue;
         const int64_t rows = r[k].hi - r[k].lo;
         const double work = (double)r[k].edges + 2.0 * rows;
-        const int64_t groups_per_block = r[k].lanes ? kThreads / r[k].lanes : 1;
-        const int64_t need = (rows + groups_per_block - 1) / groups_per_block;
+        const int64_t groups_per_block = r[k].lanes > 0 ? kThreads / r[k].lanes : 1;
+        const int64_t need = r[k].lanes == kTileLanes ? r[k].nt : (rows + groups_per_block - 1) / groups_per_block;
         int64_t nb = (int64_t)(budget * (work / std::max(total, 1.0)) + 0.5);
         nb = std::max<int64_t>(1, std::min(nb, need));
         Seg &sg = P.seg[P.nseg++];
@@ -429,6 +458,8 @@ static Plan make_plan(const RangeSpec *r, int nr, int budget) {
         sg.lanes = r[k].lanes;
         sg.blk0 = blk;
         sg.nblk = (int32_t)nb;
+        sg.t0 = r[k].t0;
+        sg.nt = r[k].nt;
         blk += (int)nb;
     }
     P.nblocks = std::max(blk, 1);
@@ -444,7 +475,7 @@ static int class_ranges(int32_t lo, int32_t hi, const int32_t *bounds, const lon
     for (int k = 0; k <= kNumThr; k++) {
         const int32_t b = k < kNumThr ? bounds[k] : hi;
         const long long eb = k < kNumThr ? e_b[k] : e_hi;
-        out[k] = RangeSpec{a, b, lanes[k], eb - ea};
+        out[k] = RangeSpec{a, b, lanes[k], eb - ea, 0, 0};
         a = b;
         ea = eb;
     }
@@ -454,12 +485,23 @@ static int class_ranges(int32_t lo, int32_t hi, const int32_t *bounds, const lon
 void build_plans(pr_graph *g) {
     const int32_t n_nd = g->G.n_nd, n_ref = g->G.n_ref;
     const int nr = g->nranges;  // referenced ranges (levels), then the dangling range
-    std::vector<RangeSpec> ref, d, lvl[kMaxLevels];
+    std::vector<RangeSpec> ref, d, lvl[kMaxLevels], ref_t, d_t;
     for (int k = 0; k < nr; k++) {
         const long long *E = &g->range_edges[(size_t)k * (kNumThr + 2)];
         RangeSpec rs[kNumThr + 1];
         class_ranges(g->range_lo[k], g->range_hi[k], &g->bounds[(size_t)k * kNumThr], &E[0], &E[1], E[kNumThr + 1],
                      rs);
+        // the tiled variant: the block and warp bins, then the short rows as tiles
+        std::vector<RangeSpec> tiled;
+        if (g->tile_nt[k] > 0) {
+            tiled.push_back(rs[0]);
+            tiled.push_back(rs[1]);
+            RangeSpec t{g->tile_lo[k], g->range_hi[k], kTileLanes, 0, g->tile_t0[k], g->tile_nt[k]};
+            for (int c = 2; c <= kNumThr; c++) t.edges += rs[c].edges;
+            tiled.push_back(t);
+        } else {
+            tiled.assign(rs, rs + kNumThr + 1);
+        }
         for (const RangeSpec &r : rs) {
             if (k < nr - 1) {
                 ref.push_back(r);
@@ -468,18 +510,25 @@ void build_plans(pr_graph *g) {
                 d.push_back(r);
             }
         }
+        for (const RangeSpec &r : tiled) (k < nr - 1 ? ref_t : d_t).push_back(r);
     }
     // unreferenced rows (no in-edges): one lane each; their in-lists are empty
     const long long e_ref_end = g->range_edges[(size_t)(nr - 2) * (kNumThr + 2) + kNumThr + 1];
     const long long e_nd = g->range_edges[(size_t)(nr - 1) * (kNumThr + 2)];
-    const RangeSpec unref{n_ref, n_nd, 1, e_nd - e_ref_end};
-    std::vector<RangeSpec> nd = ref, all = ref;
+    const RangeSpec unref{n_ref, n_nd, 1, e_nd - e_ref_end, 0, 0};
+    std::vector<RangeSpec> nd = ref, all = ref, nd_t = ref_t, all_t = ref_t;
     nd.push_back(unref);
     all.push_back(unref);
     all.insert(all.end(), d.begin(), d.end());
+    nd_t.push_back(unref);
+    all_t.push_back(unref);
+    all_t.insert(all_t.end(), d_t.begin(), d_t.end());
     g->plan_nd = make_plan(nd.data(), (int)nd.size(), g->block_budget);
     g->plan_d = make_plan(d.data(), (int)d.size(), g->block_budget);
     g->plan_all = make_plan(all.data(), (int)all.size(), g->block_budget);
+    g->plan_nd_t = make_plan(nd_t.data(), (int)nd_t.size(), g->block_budget);
+    g->plan_d_t = make_plan(d_t.data(), (int)d_t.size(), g->block_budget);
+    g->plan_all_t = make_plan(all_t.data(), (int)all_t.size(), g->block_budget);
     // level-ordered rounds launch one level at a time, and a latency-bound
     // gather needs the whole GPU's resident warps: every level gets the full
     // block budget (capped so the round's launches fit the partial-sum slots);
@@ -545,6 +594,37 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     PR_CK(cudaMemcpyAsync(edges.data(), d_edges, sizeof(long long) * rows_n, cudaMemcpyDeviceToHost, s));
     PR_CK(cudaStreamSynchronize(s));
     PR_CK(cudaGetLastError());
+    // gather tiles over the short rows (in-degree <= thr[1] <= kTileDeg) of each range
+    int32_t t_lo[kMaxLevels + 1], t_nt[kMaxLevels + 1] = {}, t_t0[kMaxLevels + 1] = {};
+    const bool tiled = thr[1] <= kTileDeg;
+    for (int k = 0; k < nr; k++) t_lo[k] = tiled ? b[(size_t)k * kNumThr + 1] : hi[k];
+    Buf tiles;
+    {
+        int32_t *d_tlo = d_lo;  // [nr]: the range starts were consumed by k_bin_bounds (stream synchronized)
+        PR_CK(cudaMemcpyAsync(d_tlo, t_lo, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+        int32_t *d_ends = d_rows;  // [2 nr] (the class rows were consumed above)
+        k_tile_ends<<<1, 32, 0, s>>>(g->inr_off.as<int32_t>(), d_tlo, d_hi, nr, d_ends);
+        std::vector<int32_t> ends(2 * (size_t)nr);
+        PR_CK(cudaMemcpyAsync(ends.data(), d_ends, sizeof(int32_t) * ends.size(), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        int32_t total = 0;
+        for (int k = 0; k < nr; k++) {
+            if (t_lo[k] >= hi[k]) continue;
+            const long long u_last = (long long)(ends[2 * k + 1] - ends[2 * k]) + (long long)kTileW * (hi[k] - 1 - t_lo[k]);
+            t_nt[k] = (int32_t)(u_last / kTileU + 1);
+            t_t0[k] = total;
+            total += t_nt[k] + 1;
+        }
+        PR_TRY(tiles.alloc(sizeof(int32_t) * std::max(total, 1), s));
+        for (int k = 0; k < nr; k++) {
+            if (!t_nt[k]) continue;
+            const int rows = hi[k] - t_lo[k];
+            const int grid = std::max(1, std::min((rows + kThreads - 1) / kThreads, g->num_sms * 8));
+            k_tile_marks<<<grid, kThreads, 0, s>>>(g->inr_off.as<int32_t>(), t_lo[k], hi[k],
+                                                   tiles.as<int32_t>() + t_t0[k]);
+        }
+        PR_CK(cudaGetLastError());
+    }
     // plans are built into a scratch copy first: the graph keeps its bins on failure
     pr_graph *T = new (std::nothrow) pr_graph();
     if (!T) return fail(PR_ENOMEM, "host allocation failed");
@@ -559,9 +639,15 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     for (size_t k = 0; k < b.size(); k++) T->bounds[k] = b[k];
     for (size_t k = 0; k < rows_n; k++) T->range_edges[k] = edges[k];
     T->block_budget = budget;
+    for (int k = 0; k < nr; k++) {
+        T->tile_lo[k] = t_lo[k];
+        T->tile_nt[k] = t_nt[k];
+        T->tile_t0[k] = t_t0[k];
+    }
     build_plans(T);
-    bool ok = T->plan_all.nblocks <= kMaxBlocks && T->plan_nd.nblocks <= kMaxBlocks;
-    int lvl_blocks = T->plan_unref.nblocks;
+    bool ok = T->plan_all.nblocks <= kMaxBlocks && T->plan_nd.nblocks <= kMaxBlocks &&
+              T->plan_all_t.nblocks <= kMaxBlocks && T->plan_nd_t.nblocks <= kMaxBlocks;
+    int lvl_blocks = T->plan_unref.nblocks;  // one level-ordered round's launches share the slots
     for (int l = 0; l < T->levels; l++) lvl_blocks += T->plan_lvl[l].nblocks;
     ok = ok && lvl_blocks <= kMaxBlocks;
     if (!ok) {
@@ -581,8 +667,19 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     g->plan_nd = T->plan_nd;
     g->plan_d = T->plan_d;
     g->plan_all = T->plan_all;
+    g->plan_nd_t = T->plan_nd_t;
+    g->plan_d_t = T->plan_d_t;
+    g->plan_all_t = T->plan_all_t;
+    for (int k = 0; k <= kMaxLevels; k++) {
+        g->tile_lo[k] = T->tile_lo[k];
+        g->tile_nt[k] = T->tile_nt[k];
+        g->tile_t0[k] = T->tile_t0[k];
+    }
+    g->tile_row.swap(tiles);  // the old table is released when `tiles` leaves scope (stream synchronized)
+    g->G.tile_row = g->tile_row.as<int32_t>();
     for (int l = 0; l < kMaxLevels; l++) g->plan_lvl[l] = T->plan_lvl[l];
     g->plan_unref = T->plan_unref;
+    g->plan_gen++;
     delete T;
     return PR_OK;
 }

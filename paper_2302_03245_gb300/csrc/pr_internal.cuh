@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/pr.h"
 
@@ -46,6 +47,14 @@ struct Buf {
     pr_status alloc_async(size_t nbytes, cudaStream_t stream);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
+    void swap(Buf &o) noexcept {
+        std::swap(p, o.p);
+        std::swap(bytes, o.bytes);
+        std::swap(s, o.s);
+        std::swap(ffn, o.ffn);
+        std::swap(fctx, o.fctx);
+        std::swap(stream_ordered, o.stream_ordered);
+    }
     ~Buf() { release(); }
     Buf() = default;
     Buf(const Buf &) = delete;
@@ -78,6 +87,7 @@ struct DevGraph {
     const int32_t *perm;      // [n] internal -> caller id
     const int32_t *inv;       // [n] caller id -> internal
     const int32_t *gs_back;   // [n_nd] level-ordered graphs: valid out-edges into the row's own or a lower level
+    const int32_t *tile_row;  // first row of every gather tile (short-row ranges), see Seg::t0
 };
 
 // Row ranges of a gather kernel, by work-group size.  Rows inside each
@@ -86,10 +96,27 @@ struct DevGraph {
 // of two; 0 = the whole block per row).
 struct Seg {
     int32_t lo, hi;   // rows [lo, hi)
-    int32_t lanes;    // threads per row; 0 = one block per row
+    int32_t lanes;    // threads per row; 0 = one block per row; kTileLanes = gather tiles
     int32_t blk0;     // first block of this segment
     int32_t nblk;     // blocks assigned
+    int32_t t0, nt;   // gather tiles: rows [tile_row[t0 + k], tile_row[t0 + k + 1]), k < nt
 };
+// Short rows (in-list length <= kTileDeg) can be gathered by tiles: a block
+// loads the pending values of up to kTileE consecutive in-list entries at once
+// (independent loads) into shared memory, then each thread sums its rows there.
+// A tile is a run of whole rows: row j's units are its entries plus kTileW, and
+// tile k holds the rows whose first unit lies in [k U, (k+1) U) for
+// U = kTileE - kTileDeg - kTileW, so a tile has at most kTileE entries and
+// kTileRows rows.
+#ifndef PR_TILE_E
+#define PR_TILE_E 2048
+#endif
+constexpr int kTileLanes = -1;
+constexpr int kTileE = PR_TILE_E;
+constexpr int kTileDeg = 64;
+constexpr int kTileW = 2;
+constexpr int kTileU = kTileE - kTileDeg - kTileW;
+constexpr int kTileRows = kTileU / kTileW + 1;
 constexpr int kMaxSeg = 128;   // levels x 7 bins + the unreferenced rows + 7 dangling bins
 constexpr int kMaxLevels = 16;  // levels of level-ordered rounds
 struct Plan {
@@ -105,13 +132,16 @@ constexpr int kCtaRowMin = 4096;    // push bins: out-degree above which a verte
 // Pull bins (in-degree d): d > thr[0] block per row; thr[k] < d <= thr[k-1]
 // gets 32 >> (k-1) lanes; d <= thr[5] one lane.
 constexpr int kNumThr = 6;
-constexpr int32_t kDefaultThr[kNumThr] = {4096, 32, 16, 8, 4, 2};
+constexpr int32_t kDefaultThr[kNumThr] = {4096, 64, 32, 16, 8, 4};
 
 }  // namespace pr
 
 // The opaque ABI handle.
 struct pr_graph {
     uint64_t uid = 0;  // process-unique serial number (caches keyed by graph use it, not the address)
+    // bumped whenever the pull plans change (set_bins): captured CUDA graphs and
+    // tile tables hold plans by value and are rebuilt when it moves
+    uint64_t plan_gen = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -140,6 +170,12 @@ struct pr_graph {
     double pull_ratio = 0.04;  // AUTO push/pull switch used when a solve passes 0
     int64_t scan_nd_ref = 0, scan_nd_unref = 0;  // in-list entries of the non-dangling rows, per segment
     pr::Plan plan_nd{}, plan_d{}, plan_all{};
+    // the same rows with the short-row bins replaced by gather tiles (single
+    // solves); the batch engine and the server cut plan_nd / plan_d
+    pr::Plan plan_nd_t{}, plan_d_t{}, plan_all_t{};
+    pr::Buf tile_row;                                        // tile starts of every range, then its end
+    int32_t tile_t0[pr::kMaxLevels + 1] = {}, tile_nt[pr::kMaxLevels + 1] = {};  // per range (0 tiles: none)
+    int32_t tile_lo[pr::kMaxLevels + 1] = {};                // first row of the range's tiled rows
     // solver workspace (lazily allocated, reused across solves)
     void *ws = nullptr;
 };

@@ -472,6 +472,72 @@ template <int LANES> struct EntriesInFlight {
     static constexpr int value = LANES <= 2 ? 1 : (LANES < 32 ? 2 : 8);
 };
 
+// ------------------------------------------------------------ gather tiles
+// Single solves gather short rows by tiles; a build with PR_PULL_TILES=0
+// keeps the per-row lane bins (and reserves no shared memory for tiles).
+#ifndef PR_PULL_TILES
+#define PR_PULL_TILES 1
+#endif
+// A tile's pending values (in-list order) and its rows' entry offsets relative
+// to the tile's first entry, in shared memory.
+template <typename V> struct TileSmem {
+    V val[kTileE];
+    int32_t off[kTileRows + 1];
+};
+// the row state a tile's epilogues start from, fetched while the gathers fly
+template <typename T> struct TileRows {
+    T v[kTileRows];
+};
+
+// Stages tile t: every thread first loads its kTileE / kThreads in-list
+// entries (coalesced, evict-first), then gathers their values (independent
+// loads), then the row offsets are copied.  Rows [ra, rb) of the tile.
+template <typename V, typename T = float>
+__device__ __forceinline__ void tile_load(const DevGraph &G, int t, const V *__restrict__ val, TileSmem<V> &sm,
+                                          int &ra, int &rb, const T *rowv = nullptr, TileRows<T> *rs = nullptr) {
+    constexpr int U = kTileE / kThreads;
+    constexpr int RU = (kTileRows + kThreads - 1) / kThreads;
+    ra = __ldg(&G.tile_row[t]);
+    rb = __ldg(&G.tile_row[t + 1]);
+    T pre[RU];
+    if (rs) {  // the rows' state, in flight with the in-list loads and gathers below
+#pragma unroll
+        for (int k = 0; k < RU; k++) {
+            const int i = (int)threadIdx.x + k * kThreads;
+            if (i < rb - ra) pre[k] = rowv[ra + i];
+        }
+    }
+    const int ea = __ldg(&G.inr_off[ra]);
+    const int ne = __ldg(&G.inr_off[rb]) - ea;
+    int idx[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int k = (int)threadIdx.x + u * kThreads;
+        idx[u] = k < ne ? __ldcs(&G.inr_src[ea + k]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (idx[u] >= 0) sm.val[threadIdx.x + u * kThreads] = __ldg(&val[idx[u]]);
+    for (int i = threadIdx.x; i <= rb - ra; i += kThreads) sm.off[i] = __ldg(&G.inr_off[ra + i]) - ea;
+    if (rs) {
+#pragma unroll
+        for (int k = 0; k < RU; k++) {
+            const int i = (int)threadIdx.x + k * kThreads;
+            if (i < rb - ra) rs->v[i] = pre[k];
+        }
+    }
+    __syncthreads();
+}
+
+// sum of tile row i (entries in order, as one lane sums a row)
+template <typename V>
+__device__ __forceinline__ typename GT<V>::A tile_row_sum(const TileSmem<V> &sm, int i) {
+    typename GT<V>::A acc = GT<V>::zero();
+    const int e1 = sm.off[i + 1];
+    for (int e = sm.off[i]; e < e1; e++) acc = GT<V>::add(acc, sm.val[e]);
+    return acc;
+}
+
 // ------------------------------------------------------------ round decision
 // Executed by thread 0 of the last block of an activation (round t).
 __device__ __forceinline__ void round_decision(Ctl *ctl, int t, double R, long long F, long long E, int u,
@@ -624,17 +690,17 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
 
 // ------------------------------------------------------------ k_round_pull
 // commit + update + next activation of row j (run by one lane per row)
+// v: r_j as the row starts (prefetched by the caller)
 template <typename T, bool IFP2>
-__device__ __forceinline__ bool pull_row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
-                                                  typename ST<T>::V *wnext, int j, T in, int want, int &pd,
-                                                  typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+__device__ __forceinline__ bool pull_row_epilogue_v(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                                    typename ST<T>::V *wnext, int j, T v, T in, int want, int &pd,
+                                                    typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
     T *x = static_cast<T *>(B.x);
     T *r = static_cast<T *>(B.r);
     if (j >= G.n_nd) {  // dangling vertex (IFP1): receives, never pushes
-        r[j] = ST<T>::add(r[j], in);
+        r[j] = ST<T>::add(v, in);
         return false;
     }
-    const T v = r[j];
     T base_v = v;
     if (is_active(v, ctl)) {  // commit of round t-1 (decided on this same r_j)
         x[j] = ST<T>::add(x[j], ST<T>::mul(ST<T>::om(ctl), v));
@@ -644,6 +710,14 @@ __device__ __forceinline__ bool pull_row_epilogue(const DevGraph &G, const Ctl *
     r[j] = rn;
     Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(rn)));
     return activate_one<T, IFP2>(G, ctl, j, rn, want, wnext, static_cast<T *>(B.vbuf), pd, Fl, El, ul);
+}
+
+template <typename T, bool IFP2>
+__device__ __forceinline__ bool pull_row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                                  typename ST<T>::V *wnext, int j, T in, int want, int &pd,
+                                                  typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    return pull_row_epilogue_v<T, IFP2>(G, ctl, B, wnext, j, static_cast<const T *>(B.r)[j], in, want, pd, Rl, Fl,
+                                        El, ul);
 }
 
 // Rows of a plan segment handled by groups of LANES threads, ROWS rows per
@@ -690,6 +764,40 @@ __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int 
     }
 }
 
+// The gather tiles of a pull round's segment: block lb takes tiles lb, lb +
+// nblk, ...; one thread per row sums it from shared memory (plus the
+// unreferenced sources' segment from global memory while it can be nonzero)
+// and runs the row's epilogue.
+template <typename T, bool IFP2>
+__device__ __forceinline__ void round_tiles(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                            const RoundBuf &B, const typename ST<T>::V *wprev,
+                                            typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
+                                            typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    __shared__ TileSmem<V> sm;
+    __shared__ TileRows<T> rs;
+    for (int t = S.t0 + lb; t < S.t0 + S.nt; t += S.nblk) {
+        int ra, rb;
+        tile_load<V, T>(G, t, wprev, sm, ra, rb, static_cast<const T *>(B.r), &rs);
+        const int nrow = rb - ra;
+        for (int base = 0; base < nrow; base += kThreads) {
+            const int i = base + (int)threadIdx.x;
+            const int j = ra + i;
+            bool act = false;
+            int pd = 0;
+            if (i < nrow) {
+                A acc = tile_row_sum<V>(sm, i);
+                if (use_unref) acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, wprev, 0, 1));
+                act = pull_row_epilogue_v<T, IFP2>(G, ctl, B, wnext, j, rs.v[i], ST<T>::from_acc(acc), want, pd, Rl,
+                                                   Fl, El, ul);
+            }
+            if (want) bins_append(act, pd, j, bcnt, B.bins, G.n_nd);
+        }
+        __syncthreads();  // the next tile reuses the shared arrays
+    }
+}
+
 // One segment (or tile) of a pull round: rows [S.lo, S.hi) with S.lanes threads per
 // row (0: the whole block per row); block lb of S.nblk.
 template <typename T, bool IFP2>
@@ -701,6 +809,11 @@ __device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, i
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
     switch (S.lanes) {
+#if PR_PULL_TILES
+        case kTileLanes:
+            round_tiles<T, IFP2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul);
+            break;
+#endif
         case 1: round_rows<T, IFP2, 1>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
         case 2: round_rows<T, IFP2, 2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
         case 4: round_rows<T, IFP2, 4>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
@@ -854,6 +967,13 @@ __global__ void __launch_bounds__(kThreads, PR_PULL_MIN_BLOCKS) k_round_pull(Dev
 // One launch serves one level's rows (plan of the level); the launches of a
 // round run in level order, the rows without in-edges last, and the last
 // launch takes the round's decision over the partial slots of all of them.
+// a level's plan: its lane bins only (a kernel argument of 150 bytes instead
+// of the full plan's 2.6 KB)
+struct LevelPlan {
+    Seg seg[kNumThr + 1];
+    int32_t nseg, nblocks;
+};
+
 struct LevelLaunch {
     int32_t split;       // sources below this id belong to lower levels
     int32_t slot_base;   // this launch's first partial slot
@@ -1044,13 +1164,20 @@ __device__ __forceinline__ void level_decision(Ctl *ctl, int t, int phase, doubl
 #define PR_LEVEL_MIN_BLOCKS 5
 #endif
 
+// Launched with programmatic stream serialization: the launch of the next
+// level may begin while this one drains; griddepcontrol.wait holds every
+// thread until the previous launch has completed and its writes are visible,
+// and nothing is read before it.  Without the launch attribute both
+// instructions are no-ops.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(DevGraph G, Plan PL, Ctl *ctl,
+__global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(DevGraph G, LevelPlan PL, Ctl *ctl,
                                                                               Partials P, RoundBuf B, Trace tr,
                                                                               LevelLaunch lv) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
     using R = typename ST<T>::R;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (ctl->done || ctl->mode != MODE_PULL) return;
     __shared__ double shd[32];
     __shared__ long long shl[32];
@@ -1064,7 +1191,15 @@ __global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(
     R Rl = ST<T>::rzero();
     long long Fl = 0, El = 0;
     int ul = 0;
-    if (phase == 3 && PL.nseg > 0) {  // commit of the synchronous round's activation, nothing else
+    if (phase >= 1 && phase <= 2 && lv.decide && PL.nseg > 0) {
+        // the rows without in-edges: from the first level-ordered round on they
+        // receive nothing and hold at most a residual below xi_act (round 1
+        // committed what round 0 activated), so they only add |r| to R
+        const T *r = static_cast<const T *>(B.r);
+        for (int j = PL.seg[0].lo + blockIdx.x * blockDim.x + threadIdx.x; j < PL.seg[PL.nseg - 1].hi;
+             j += gridDim.x * blockDim.x)
+            Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(r[j])));
+    } else if (phase == 3 && PL.nseg > 0) {  // commit of the synchronous round's activation, nothing else
         T *x = static_cast<T *>(B.x);
         T *r = static_cast<T *>(B.r);
         for (int j = PL.seg[0].lo + blockIdx.x * blockDim.x + threadIdx.x; j < PL.seg[PL.nseg - 1].hi;
@@ -1160,14 +1295,29 @@ template <typename T> struct SweepArgs {
     Trace tr;
 };
 
+// the row value an epilogue starts from: Power's pi_k, the correction's
+// reserve, phase 2's residual (prefetched by the tile path)
 template <typename T, int OP>
-__device__ __forceinline__ void sweep_epilogue(const DevGraph &G, const Ctl *ctl, SweepArgs<T> &a, int j, T in,
-                                               typename ST<T>::R &s1, typename ST<T>::R &s2,
-                                               typename ST<T>::R &s3) {
+__device__ __forceinline__ T sweep_row_state(const SweepArgs<T> &a, int j) {
+    if constexpr (OP == OP_POWER) return a.pi_cur[j];
+    else if constexpr (OP == OP_CORRECT) return a.x[j];
+    else return a.r[j];
+}
+template <typename T, int OP>
+__device__ __forceinline__ const T *sweep_state_array(const SweepArgs<T> &a) {
+    if constexpr (OP == OP_POWER) return a.pi_cur;
+    else if constexpr (OP == OP_CORRECT) return a.x;
+    else return a.r;
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void sweep_epilogue_v(const DevGraph &G, const Ctl *ctl, SweepArgs<T> &a, int j, T pre,
+                                                 T in, typename ST<T>::R &s1, typename ST<T>::R &s2,
+                                                 typename ST<T>::R &s3) {
     if constexpr (OP == OP_POWER) {
         // pi_{k+1} = c P pi_k + gamma_k p, gamma_k = c d^T pi_k + (1-c) e^T pi_k  (Eq. 1)
         const T y = ST<T>::add(ST<T>::mul(ST<T>::c(ctl), in), ST<T>::mul(ST<T>::gamma(ctl), ST<T>::p(ctl, a.pv, j)));
-        const T old = a.pi_cur[j];
+        const T old = pre;
         s1 = ST<T>::radd(s1, ST<T>::rval(ST<T>::absv(ST<T>::add(y, ST<T>::neg(old)))));
         if (j >= G.n_nd) s2 = ST<T>::radd(s2, ST<T>::rval(y));
         s3 = ST<T>::radd(s3, ST<T>::rval(y));
@@ -1178,13 +1328,20 @@ __device__ __forceinline__ void sweep_epilogue(const DevGraph &G, const Ctl *ctl
         // evaluated in double-float (FP32 instructions; a per-row FP64 divide would cost
         // more than the whole gather on GB300's FP64 pipe)
         static_assert(std::is_same<T, float2>::value, "the correction writes double-float state");
-        const float2 sj = df_mul(a.x[j], ST<float2>::inv_om(ctl));
+        const float2 sj = df_mul(pre, ST<float2>::inv_om(ctl));
         const float2 pj = ctl->p_dense ? df_from_d(a.pv.p64[j]) : ctl->pu_df;
         a.r[j] = df_add(df_add(pj, df_mul(ST<float2>::c(ctl), in)), df_neg(sj));
     } else {  // OP_PHASE2: r_d = p_d + c sum_{u in S(d)} x_u / ((1-c) deg(u)); phase 1 never
               // touches a dangling residual, so r_d still holds p_d
-        a.r[j] = ST<T>::add(a.r[j], ST<T>::mul(ST<T>::c(ctl), in));
+        a.r[j] = ST<T>::add(pre, ST<T>::mul(ST<T>::c(ctl), in));
     }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void sweep_epilogue(const DevGraph &G, const Ctl *ctl, SweepArgs<T> &a, int j, T in,
+                                               typename ST<T>::R &s1, typename ST<T>::R &s2,
+                                               typename ST<T>::R &s3) {
+    sweep_epilogue_v<T, OP>(G, ctl, a, j, sweep_row_state<T, OP>(a, j), in, s1, s2, s3);
 }
 
 template <typename T, int OP, int LANES>
@@ -1217,6 +1374,28 @@ __device__ __forceinline__ void sweep_rows(const DevGraph &G, const Seg &S, int 
     }
 }
 
+// The gather tiles of a sweep's segment (see round_tiles)
+template <typename T, int OP>
+__device__ __forceinline__ void sweep_tiles(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl, SweepArgs<T> &a,
+                                            typename ST<T>::R &s1, typename ST<T>::R &s2, typename ST<T>::R &s3) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    __shared__ TileSmem<V> sm;
+    __shared__ TileRows<T> rs;
+    for (int t = S.t0 + lb; t < S.t0 + S.nt; t += S.nblk) {
+        int ra, rb;
+        tile_load<V, T>(G, t, a.val, sm, ra, rb, sweep_state_array<T, OP>(a), &rs);
+        const int nrow = rb - ra;
+        for (int i = threadIdx.x; i < nrow; i += kThreads) {
+            const int j = ra + i;
+            A acc = tile_row_sum<V>(sm, i);
+            acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, a.val, 0, 1));
+            sweep_epilogue_v<T, OP>(G, ctl, a, j, rs.v[i], ST<T>::from_acc(acc), s1, s2, s3);
+        }
+        __syncthreads();
+    }
+}
+
 // One segment (or tile) of a sweep: rows [S.lo, S.hi), S.lanes threads per row.
 template <typename T, int OP>
 __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
@@ -1225,6 +1404,9 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
     switch (S.lanes) {
+#if PR_PULL_TILES
+        case kTileLanes: sweep_tiles<T, OP>(G, S, lb, ctl, a, s1, s2, s3); break;
+#endif
         case 1: sweep_rows<T, OP, 1>(G, S, lb, ctl, a, s1, s2, s3); break;
         case 2: sweep_rows<T, OP, 2>(G, S, lb, ctl, a, s1, s2, s3); break;
         case 4: sweep_rows<T, OP, 4>(G, S, lb, ctl, a, s1, s2, s3); break;

@@ -266,6 +266,7 @@ struct Workspace {
     StateBufs s64, s32, sdf;  // FP64 (reference), FP32, double-float
     Ctl *hctl = nullptr;      // pinned host mirror
     int32_t trace_len = 0;
+    uint64_t plan_gen = 0;    // the graph's plan generation the captured graphs were built with
     cudaStream_t cap_stream = nullptr;
     struct CG {
         cudaGraph_t graph = nullptr;
@@ -406,6 +407,13 @@ template <> int power_key<float>() { return 10; }
 template <> int power_key<double>() { return 11; }
 template <> int power_key<float2>() { return 12; }
 
+// ------------------------------------------------------------ plans
+// Single solves gather the short rows by tiles (plan_*_t) unless built with
+// PR_PULL_TILES=0 (pr_kernels.cuh), which keeps the per-row lane bins.
+static const Plan &plan_nd_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_nd_t : g->plan_nd; }
+static const Plan &plan_all_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_all_t : g->plan_all; }
+static const Plan &plan_d_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_d_t : g->plan_d; }
+
 // ------------------------------------------------------------ round loop
 constexpr int kRoundLaunches = 3;  // k_round_pull, k_push, k_activate
 constexpr int kUnroll = 4;         // rounds per while-loop body
@@ -418,7 +426,7 @@ static void launch_round(pr_graph *g, Workspace &W, cudaStream_t s, Prof *prof) 
     const Trace tr = trace_of(W);
     const RoundBuf B = round_bufs<T>(W);
     const int sms = g->num_sms;
-    const Plan &PL = IFP2 ? g->plan_nd : g->plan_all;
+    const Plan &PL = IFP2 ? plan_nd_of(g) : plan_all_of(g);
     const int nbt = sms * 4, nbw = sms * 4, nbc = sms * 2;
     const size_t e0 = prof ? prof->mark(s) : 0;
     k_round_pull<T, IFP2><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, P, B, tr);
@@ -447,16 +455,31 @@ static void launch_round_levels(pr_graph *g, Workspace &W, cudaStream_t s, Prof 
     const RoundBuf B = round_bufs<T>(W);
     int total = g->plan_unref.nblocks;
     for (int l = 0; l < g->levels; l++) total += g->plan_lvl[l].nblocks;
+    // programmatic stream serialization: each level launch may start while the
+    // previous one drains (the kernel waits for it before reading anything)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    auto launch = [&](const Plan &PL, LevelLaunch lv) {
+        LevelPlan LP{};
+        LP.nseg = std::min(PL.nseg, kNumThr + 1);  // a level or the unreferenced rows: one range of lane bins
+        LP.nblocks = PL.nblocks;
+        for (int k = 0; k < LP.nseg; k++) LP.seg[k] = PL.seg[k];
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)PL.nblocks);
+        cfg.blockDim = dim3(kThreads);
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_round_levels<T>, G, LP, ctl, P, B, tr, lv);
+    };
     const size_t e0 = prof ? prof->mark(s) : 0;
     int base = 0;
     for (int l = 0; l < g->levels; l++) {
-        const Plan &PL = g->plan_lvl[l];
-        k_round_levels<T><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, P, B, tr,
-                                                          LevelLaunch{g->level_lo[l], base, total, 0});
-        base += PL.nblocks;
+        launch(g->plan_lvl[l], LevelLaunch{g->level_lo[l], base, total, 0});
+        base += g->plan_lvl[l].nblocks;
     }
-    k_round_levels<T><<<g->plan_unref.nblocks, kThreads, 0, s>>>(G, g->plan_unref, ctl, P, B, tr,
-                                                                 LevelLaunch{G.n_ref, base, total, 1});
+    launch(g->plan_unref, LevelLaunch{G.n_ref, base, total, 1});
     const size_t e1 = prof ? prof->mark(s) : 0;
     k_activate<T, true><<<grid_n(G.n_nd, g->num_sms, 8), kThreads, 0, s>>>(G, ctl, P, B, tr);
     if (prof) {
@@ -555,7 +578,7 @@ static void launch_power_pair(pr_graph *g, Workspace &W, cudaStream_t s, Prof *p
     a.pv = pvals_of(W);
     a.P = partials_of(W);
     a.tr = trace_of(W);
-    const Plan &PL = g->plan_all;
+    const Plan &PL = plan_all_of(g);
     const size_t m0 = prof ? prof->mark(s) : 0;
     a.val = S.w[0].as<V>();
     a.pi_cur = S.x.as<T>();
@@ -691,7 +714,7 @@ static void finish_ifp(pr_graph *g, Workspace &W, int algo, double *dout, int64_
         a.val = S.q.as<V>();
         a.r = S.r.as<T>();
         a.pv = pvals_of(W);
-        k_sweep<T, OP_PHASE2><<<g->plan_d.nblocks, kThreads, 0, s>>>(G, g->plan_d, ctl, a);
+        k_sweep<T, OP_PHASE2><<<plan_d_of(g).nblocks, kThreads, 0, s>>>(G, plan_d_of(g), ctl, a);
         launches += 2;
     }
     k_fin_sum<T><<<gn, kThreads, 0, s>>>(G, ctl, P, algo, S.x.as<T>(), S.r.as<T>());
@@ -746,6 +769,10 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     }
     PR_TRY(ensure_ws(g, prec, opt.max_rounds + 2));
     Workspace &W = *static_cast<Workspace *>(g->ws);
+    if (W.plan_gen != g->plan_gen) {  // the captured launches carry the old plans
+        W.drop_graphs();
+        W.plan_gen = g->plan_gen;
+    }
     cudaStream_t s = g->stream;
     const DevGraph &G = g->G;
     Ctl h{};
@@ -826,7 +853,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         a.r = rdf;
         a.x = xdf;
         a.pv = pv;
-        const Plan &PL = algo == PR_IFP2 ? g->plan_nd : g->plan_all;
+        const Plan &PL = algo == PR_IFP2 ? plan_nd_of(g) : plan_all_of(g);
         k_reset_run<<<1, 1, 0, s>>>(ctl);
         k_sweep<float2, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));

@@ -69,7 +69,8 @@ def test_gpu_reproduces_golden(path):
     with pr.Graph(g.n, g.m, *g.csr32()) as h:
         for algo in (pr.PR_IFP1, pr.PR_IFP2, pr.PR_POWER):
             for prec in (pr.PR_DF64, pr.PR_FP64, pr.PR_FP32):
-                eps = 1e-7 if prec == pr.PR_FP32 else 1e-12
+                # FP32 Power stops on ||delta||_1, whose FP32 rounding floor is near 1e-7
+                eps = (1e-6 if algo == pr.PR_POWER else 1e-7) if prec == pr.PR_FP32 else 1e-12
                 out, st, s = h.solve(c, eps, algo, prec, p=p)
                 assert s == pr.PR_OK
                 tol = st["err_bound"] + (2e-6 if prec == pr.PR_FP32 else 1e-13)

@@ -74,9 +74,11 @@ def test_closed_forms(case, algo, prec, mode):
     name, g, p, truth = case
     with gpu_graph(g) as G:
         fp32_power = algo == pr.PR_POWER and prec == pr.PR_FP32
-        # FP32 Power: ||delta||_1 has an FP32 rounding floor near 1e-7, and its
-        # certified error is c * delta / (1 - c)
-        eps = 1e-13 if algo != pr.PR_POWER else {pr.PR_FP64: 1e-14, pr.PR_DF64: 1e-13, pr.PR_FP32: 1e-6}[prec]
+        # Power stops on ||delta||_1, whose rounding floor is set by the gathered
+        # values: FP32 in the FP32 form (near 1e-7), double-float pairs (48-bit)
+        # in DF64 and FP64 (near 1e-14 on these graphs); the certified error is
+        # c * delta / (1 - c)
+        eps = 1e-13 if algo != pr.PR_POWER else {pr.PR_FP64: 1e-13, pr.PR_DF64: 1e-13, pr.PR_FP32: 1e-6}[prec]
         out, st, status = G.solve(C, eps, algo, prec, p=p, opts=dict(mode=mode))
         assert status == pr.PR_OK, st
         tol = 1e-12 if prec != pr.PR_FP32 else (C * eps / (1 - C) + 1e-6 if fp32_power else 2e-7)

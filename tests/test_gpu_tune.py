@@ -41,7 +41,7 @@ def l1(a, b):
 def test_default_tuning_describes_the_bins(graph):
     g, h, _ = graph
     t = h.tuning()
-    assert t["pull_thr"] == [4096, 32, 16, 8, 4, 2]
+    assert t["pull_thr"] == [4096, 64, 32, 16, 8, 4]
     assert sum(t["bin_rows"]) == h.info["n_nd"]
     assert all(r >= 0 for r in t["bin_rows"])
     assert 0 < t["pull_ratio"] < 1 and t["pull_blocks"] >= 1
@@ -69,6 +69,27 @@ def test_any_tuning_gives_the_same_pagerank(graph, thr, budget):
                     assert l1(out, ref) <= 1e-12
         out, st, s = h.solve(C, 1e-11, pr.PR_POWER, pr.PR_DF64)
         assert l1(out, truth) <= st["err_bound"] + 1e-12
+    finally:
+        h.set_tuning(pull_thr=old["pull_thr"], block_budget=old["block_budget"])
+
+
+def test_retuning_reaches_graph_launched_rounds(graph):
+    """The rounds run inside a captured CUDA graph whose launches carry the
+    plans: after a retune, a graph-launched solve must run the new plans, i.e.
+    match the host-driven rounds bit for bit (the pull order is fixed by the
+    plan, and different plans sum in different orders)."""
+    g, h, _ = graph
+    old = h.tuning()
+    try:
+        h.solve(C, 1e-11, pr.PR_IFP2, pr.PR_DF64, opts=dict(mode=pr.PR_MODE_PULL))  # captures the rounds
+        outs = []
+        for thr, budget in (([0] * 6, 152), ([1 << 30] * 6, 1000)):
+            h.set_tuning(pull_thr=thr, block_budget=budget)
+            a, _, _ = h.solve(C, 1e-11, pr.PR_IFP2, pr.PR_DF64, opts=dict(mode=pr.PR_MODE_PULL))
+            b, _, _ = h.solve(C, 1e-11, pr.PR_IFP2, pr.PR_DF64, opts=dict(mode=pr.PR_MODE_PULL, use_graph=-1))
+            assert np.array_equal(a, b)
+            outs.append(a)
+        assert not np.array_equal(outs[0], outs[1])  # the two plans really sum differently
     finally:
         h.set_tuning(pull_thr=old["pull_thr"], block_budget=old["block_budget"])
 
