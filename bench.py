@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned launch parameters (read if it has this graph, else written)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters")
-    ap.add_argument("--legs", default="dag,batch,serve,sweep",
+    ap.add_argument("--legs", default="dag,batch,serve,sweep,undirected,threads",
                     help="extra configurations after the headline: dag (scale-24 DAG-heavy, FP32 form), "
                          "batch (512 graphs in one batch), serve (continuous batching), sweep (time and "
                          "error against eps), undirected (symmetric scale-22 graph), threads (CTA-count "

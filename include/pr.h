@@ -233,12 +233,11 @@ pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);
  *  pull_thr:     in-degree thresholds of the gather bins, non-increasing, >= 0.
  *                Rows with in-degree above pull_thr[0] get a whole block; above
  *                pull_thr[1..5] they get 32, 16, 8, 4, 2 lanes; the rest 1 lane.
- *                When pull_thr[1] <= 64, the single-solve kernels gather the
- *                rows at or below pull_thr[1] by tiles instead: a block stages
- *                up to 2048 in-list values of consecutive rows in shared
- *                memory and one thread sums each row there (the batch engine
- *                and the server keep the lane bins).  Default {4096, 64, 32,
- *                16, 8, 4}.
+ *                When pull_thr[1] <= 64, IEEE FP64 solves gather the rows at
+ *                or below pull_thr[1] by tiles instead: a block stages up to
+ *                1024 in-list values of consecutive rows in shared memory and
+ *                one thread sums each row there.  Default {4096, 64, 32, 16,
+ *                8, 4}.
  *  block_budget: blocks of a dense gather launch, split across the bins in
  *                proportion to their in-list entries (1 .. 8192).
  *  pull_ratio:   the AUTO delivery switch used when a solve passes

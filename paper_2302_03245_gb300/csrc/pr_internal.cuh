@@ -109,7 +109,7 @@ struct Seg {
 // U = kTileE - kTileDeg - kTileW, so a tile has at most kTileE entries and
 // kTileRows rows.
 #ifndef PR_TILE_E
-#define PR_TILE_E 2048
+#define PR_TILE_E 1024
 #endif
 constexpr int kTileLanes = -1;
 constexpr int kTileE = PR_TILE_E;

@@ -473,11 +473,18 @@ template <int LANES> struct EntriesInFlight {
 };
 
 // ------------------------------------------------------------ gather tiles
-// Single solves gather short rows by tiles; a build with PR_PULL_TILES=0
-// keeps the per-row lane bins (and reserves no shared memory for tiles).
+// Single solves in IEEE FP64 gather short rows by tiles.  The tiles' shared
+// memory is reserved by every launch of a kernel that contains them and
+// shrinks L1, where the lane bins keep their hottest gathered values: measured
+// on R-MAT scale 22, tiles speed up the FP64 kernels (heavier row epilogues)
+// and slow down the FP32 and double-float ones, so only the FP64
+// instantiations carry them.  PR_PULL_TILES=0 removes them everywhere.
 #ifndef PR_PULL_TILES
 #define PR_PULL_TILES 1
 #endif
+template <typename T> struct UseTiles {
+    static constexpr bool value = PR_PULL_TILES && std::is_same<T, double>::value;
+};
 // A tile's pending values (in-list order) and its rows' entry offsets relative
 // to the tile's first entry, in shared memory.
 template <typename V> struct TileSmem {
@@ -808,12 +815,13 @@ __device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, i
                                               typename GT<typename ST<T>::V>::A *sha) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    switch (S.lanes) {
-#if PR_PULL_TILES
-        case kTileLanes:
+    if constexpr (UseTiles<T>::value) {
+        if (S.lanes == kTileLanes) {
             round_tiles<T, IFP2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul);
-            break;
-#endif
+            return;
+        }
+    }
+    switch (S.lanes) {
         case 1: round_rows<T, IFP2, 1>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
         case 2: round_rows<T, IFP2, 2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
         case 4: round_rows<T, IFP2, 4>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
@@ -1281,6 +1289,17 @@ __global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(
 }
 
 // ------------------------------------------------------------ sweeps: Power, correction, phase 2
+// resident blocks per SM the sweeps are compiled for (as the pull round: the
+// gathers are latency-bound, so warps in flight matter more than registers).
+// The double-float Power sweep keeps 5: at 6 (40 registers) it spills 384
+// bytes and measured 2% slower, while the FP32 and FP64 sweeps gained 9% and
+// 7% at 6.
+#ifndef PR_SWEEP_MIN_BLOCKS
+#define PR_SWEEP_MIN_BLOCKS 6
+#endif
+template <typename T, int OP> struct SweepMinBlocks {
+    static constexpr int value = (std::is_same<T, float2>::value && OP == 1) ? 5 : PR_SWEEP_MIN_BLOCKS;
+};
 enum { OP_POWER = 1, OP_CORRECT = 2, OP_PHASE2 = 3 };
 
 template <typename T> struct SweepArgs {
@@ -1403,10 +1422,13 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
                                               typename ST<T>::R &s3, typename GT<typename ST<T>::V>::A *sha) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
+    if constexpr (UseTiles<T>::value) {
+        if (S.lanes == kTileLanes) {
+            sweep_tiles<T, OP>(G, S, lb, ctl, a, s1, s2, s3);
+            return;
+        }
+    }
     switch (S.lanes) {
-#if PR_PULL_TILES
-        case kTileLanes: sweep_tiles<T, OP>(G, S, lb, ctl, a, s1, s2, s3); break;
-#endif
         case 1: sweep_rows<T, OP, 1>(G, S, lb, ctl, a, s1, s2, s3); break;
         case 2: sweep_rows<T, OP, 2>(G, S, lb, ctl, a, s1, s2, s3); break;
         case 4: sweep_rows<T, OP, 4>(G, S, lb, ctl, a, s1, s2, s3); break;
@@ -1424,7 +1446,8 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads) k_sweep(DevGraph G, Plan PL, Ctl *ctl, SweepArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (SweepMinBlocks<T, OP>::value)) k_sweep(DevGraph G, Plan PL, Ctl *ctl,
+                                                                                    SweepArgs<T> a) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
     using R = typename ST<T>::R;

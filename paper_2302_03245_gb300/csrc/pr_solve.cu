@@ -408,11 +408,17 @@ template <> int power_key<double>() { return 11; }
 template <> int power_key<float2>() { return 12; }
 
 // ------------------------------------------------------------ plans
-// Single solves gather the short rows by tiles (plan_*_t) unless built with
-// PR_PULL_TILES=0 (pr_kernels.cuh), which keeps the per-row lane bins.
-static const Plan &plan_nd_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_nd_t : g->plan_nd; }
-static const Plan &plan_all_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_all_t : g->plan_all; }
-static const Plan &plan_d_of(const pr_graph *g) { return PR_PULL_TILES ? g->plan_d_t : g->plan_d; }
+// The plans of a kernel instantiation: the tiled ones where its kernels carry
+// gather tiles (UseTiles, pr_kernels.cuh), else the per-row lane bins.
+template <typename T> static const Plan &plan_nd_of(const pr_graph *g) {
+    return UseTiles<T>::value ? g->plan_nd_t : g->plan_nd;
+}
+template <typename T> static const Plan &plan_all_of(const pr_graph *g) {
+    return UseTiles<T>::value ? g->plan_all_t : g->plan_all;
+}
+template <typename T> static const Plan &plan_d_of(const pr_graph *g) {
+    return UseTiles<T>::value ? g->plan_d_t : g->plan_d;
+}
 
 // ------------------------------------------------------------ round loop
 constexpr int kRoundLaunches = 3;  // k_round_pull, k_push, k_activate
@@ -426,7 +432,7 @@ static void launch_round(pr_graph *g, Workspace &W, cudaStream_t s, Prof *prof) 
     const Trace tr = trace_of(W);
     const RoundBuf B = round_bufs<T>(W);
     const int sms = g->num_sms;
-    const Plan &PL = IFP2 ? plan_nd_of(g) : plan_all_of(g);
+    const Plan &PL = IFP2 ? plan_nd_of<T>(g) : plan_all_of<T>(g);
     const int nbt = sms * 4, nbw = sms * 4, nbc = sms * 2;
     const size_t e0 = prof ? prof->mark(s) : 0;
     k_round_pull<T, IFP2><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, P, B, tr);
@@ -578,7 +584,7 @@ static void launch_power_pair(pr_graph *g, Workspace &W, cudaStream_t s, Prof *p
     a.pv = pvals_of(W);
     a.P = partials_of(W);
     a.tr = trace_of(W);
-    const Plan &PL = plan_all_of(g);
+    const Plan &PL = plan_all_of<T>(g);
     const size_t m0 = prof ? prof->mark(s) : 0;
     a.val = S.w[0].as<V>();
     a.pi_cur = S.x.as<T>();
@@ -714,7 +720,7 @@ static void finish_ifp(pr_graph *g, Workspace &W, int algo, double *dout, int64_
         a.val = S.q.as<V>();
         a.r = S.r.as<T>();
         a.pv = pvals_of(W);
-        k_sweep<T, OP_PHASE2><<<plan_d_of(g).nblocks, kThreads, 0, s>>>(G, plan_d_of(g), ctl, a);
+        k_sweep<T, OP_PHASE2><<<plan_d_of<T>(g).nblocks, kThreads, 0, s>>>(G, plan_d_of<T>(g), ctl, a);
         launches += 2;
     }
     k_fin_sum<T><<<gn, kThreads, 0, s>>>(G, ctl, P, algo, S.x.as<T>(), S.r.as<T>());
@@ -853,7 +859,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         a.r = rdf;
         a.x = xdf;
         a.pv = pv;
-        const Plan &PL = algo == PR_IFP2 ? plan_nd_of(g) : plan_all_of(g);
+        const Plan &PL = algo == PR_IFP2 ? plan_nd_of<float2>(g) : plan_all_of<float2>(g);
         k_reset_run<<<1, 1, 0, s>>>(ctl);
         k_sweep<float2, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));

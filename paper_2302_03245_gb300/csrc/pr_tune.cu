@@ -38,7 +38,7 @@ void fill_tuning(const pr_graph *g, pr_tuning *t) {
         t->bin_rows[kNumThr] += g->range_hi[k] - a;
     }
     t->bin_rows[kNumThr] += g->G.n_nd - g->G.n_ref;
-    t->pull_blocks = g->plan_nd_t.nblocks;  // the plan single solves launch
+    t->pull_blocks = g->plan_nd.nblocks;  // the plan of a double-float or FP32 solve
 }
 
 struct Trial {
