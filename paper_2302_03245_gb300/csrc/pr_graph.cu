@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "pr_internal.cuh"
@@ -715,15 +716,35 @@ extern "C" void pr_destroy(pr_graph *g) {
     delete g;
 }
 
+// The first index in [0, count) where bad(k) holds, or count: chunks scanned
+// by up to 16 host threads (a single-threaded scan of a 47M-entry edge array
+// took about 20 ms, most of a graph creation from host arrays).
+template <typename F> static int64_t first_bad(int64_t count, F bad) {
+    const int64_t kChunk = 1 << 20;
+    const int nt = (int)std::min<int64_t>({(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16,
+                                           (count + kChunk - 1) / kChunk});
+    auto scan = [&](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; k++)
+            if (bad(k)) return k;
+        return count;
+    };
+    if (nt <= 1) return scan(0, count);
+    std::vector<int64_t> found(nt, count);
+    std::vector<std::thread> th;
+    const int64_t per = (count + nt - 1) / nt;
+    for (int t = 0; t < nt; t++)
+        th.emplace_back([&, t]() { found[t] = scan(std::min(count, t * per), std::min(count, (t + 1) * per)); });
+    for (auto &x : th) x.join();
+    return *std::min_element(found.begin(), found.end());
+}
+
 static pr_status validate_host(int32_t n, int64_t m, const int32_t *off, const int32_t *dst) {
     if (off[0] != 0) return fail(PR_EINVAL, "out_off[0] must be 0");
-    for (int32_t i = 0; i < n; i++)
-        if (off[i + 1] < off[i])
-            return fail(PR_EINVAL, "out_off is not non-decreasing at row " + std::to_string(i));
+    const int64_t i = first_bad(n, [&](int64_t k) { return off[k + 1] < off[k]; });
+    if (i < n) return fail(PR_EINVAL, "out_off is not non-decreasing at row " + std::to_string(i));
     if ((int64_t)off[n] != m) return fail(PR_EINVAL, "out_off[n] != m");
-    for (int64_t e = 0; e < m; e++)
-        if (dst[e] < 0 || dst[e] >= n)
-            return fail(PR_EINVAL, "out_dst[" + std::to_string(e) + "] out of range");
+    const int64_t e = first_bad(m, [&](int64_t k) { return dst[k] < 0 || dst[k] >= n; });
+    if (e < m) return fail(PR_EINVAL, "out_dst[" + std::to_string(e) + "] out of range");
     return PR_OK;
 }
 
