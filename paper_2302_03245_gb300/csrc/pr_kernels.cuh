@@ -464,12 +464,21 @@ __device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const 
 template <int LANES> struct RowsInFlight {
     static constexpr int value = LANES <= 2 ? 4 : (LANES <= 16 ? 2 : 1);
 };
-// entries per row per step: the bins give rows of at most 2 * LANES entries
-// below 32 lanes (one step covers them; 1- and 2-lane rows interleave 4 rows
-// instead, which keeps the kernel at 48 registers); warp rows run up to 128
-// entries per lane
+// entries per row per step: with the default thresholds a row below 32 lanes
+// has at most 4 * LANES entries (two steps; 1- and 2-lane rows interleave 4
+// rows instead, within the register cap); warp rows run up to 128 entries per
+// lane
+#ifndef PR_U_SMALL
+#define PR_U_SMALL 1
+#endif
+#ifndef PR_U_MID
+#define PR_U_MID 2
+#endif
+#ifndef PR_U_WARP
+#define PR_U_WARP 8
+#endif
 template <int LANES> struct EntriesInFlight {
-    static constexpr int value = LANES <= 2 ? 1 : (LANES < 32 ? 2 : 8);
+    static constexpr int value = LANES <= 2 ? PR_U_SMALL : (LANES < 32 ? PR_U_MID : PR_U_WARP);
 };
 
 // ------------------------------------------------------------ gather tiles
