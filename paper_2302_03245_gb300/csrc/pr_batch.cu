@@ -22,6 +22,13 @@
 #include "pr_group.cuh"
 #include "pr_kernels.cuh"
 
+// requests of one graph in flight before new ones join a column group (a
+// group round gathers K columns at once; with few columns live, separate
+// tile rounds cost less)
+#ifndef PR_GROUP_MIN_INFLIGHT
+#define PR_GROUP_MIN_INFLIGHT 2
+#endif
+
 namespace pr {
 
 struct Tile {
@@ -1146,12 +1153,13 @@ struct ServerImpl {
     }
 
     // put a just-admitted request into a column group of its graph when the
-    // graph is large and has other requests in flight; false: tile engine
+    // graph is large and has at least PR_GROUP_MIN_INFLIGHT requests in
+    // flight; false: tile engine
     bool try_group(SReq *q) {
         if (q->g->G.n_nd < group_min_rows) return false;
         {
             std::lock_guard<std::mutex> lock(mu);
-            if (inflight[q->g->uid] < 2) return false;
+            if (inflight[q->g->uid] < PR_GROUP_MIN_INFLIGHT) return false;
         }
         const int fmt = q->prec == PR_FP32 ? 0 : 1;
         const int K = group_columns(fmt);

@@ -267,6 +267,7 @@ struct Workspace {
     Ctl *hctl = nullptr;      // pinned host mirror
     int32_t trace_len = 0;
     uint64_t plan_gen = 0;    // the graph's plan generation the captured graphs were built with
+    cudaError_t launch_err = cudaSuccess;  // first failed cudaLaunchKernelEx of a level-ordered round
     cudaStream_t cap_stream = nullptr;
     struct CG {
         cudaGraph_t graph = nullptr;
@@ -477,7 +478,8 @@ static void launch_round_levels(pr_graph *g, Workspace &W, cudaStream_t s, Prof 
         cfg.stream = s;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_round_levels<T>, G, LP, ctl, P, B, tr, lv);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_round_levels<T>, G, LP, ctl, P, B, tr, lv);
+        if (e != cudaSuccess && W.launch_err == cudaSuccess) W.launch_err = e;
     };
     const size_t e0 = prof ? prof->mark(s) : 0;
     int base = 0;
@@ -536,10 +538,14 @@ static pr_status run_rounds(pr_graph *g, Workspace &W, bool use_graph, bool leve
         if (levels) launch_round_levels<T>(g, W, cs, pf);
         else launch_round<T, IFP2>(g, W, cs, pf);
     };
-    if (use_graph && !prof)
-        return while_graph(W, levels ? level_key<T>() : round_key<T>() + (IFP2 ? 1 : 0), ctl, [&](cudaStream_t cs) {
+    W.launch_err = cudaSuccess;
+    if (use_graph && !prof) {
+        PR_TRY(while_graph(W, levels ? level_key<T>() : round_key<T>() + (IFP2 ? 1 : 0), ctl, [&](cudaStream_t cs) {
             for (int k = 0; k < kUnroll; k++) round(cs, nullptr);
-        }, s);
+        }, s));
+        if (W.launch_err != cudaSuccess) return cuda_fail(W.launch_err, "cudaLaunchKernelEx (level-ordered round)");
+        return PR_OK;
+    }
     int t0 = 0;
     if (prof) {
         PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -553,6 +559,7 @@ static pr_status run_rounds(pr_graph *g, Workspace &W, bool use_graph, bool leve
     std::vector<int8_t> modes;
     for (;;) {
         for (int k = 0; k < chunk; k++) round(s, prof);
+        if (W.launch_err != cudaSuccess) return cuda_fail(W.launch_err, "cudaLaunchKernelEx (level-ordered round)");
         PR_CK(cudaGetLastError());
         PR_CK(cudaMemcpyAsync(&W.hctl->done, &ctl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
