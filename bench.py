@@ -274,7 +274,8 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
     _, st_t, _ = G.solve(C, 1e-14, pr.PR_POWER, pr.PR_FP64, out=truth)
     res["reference_solution"] = f"GPU Power FP64 to ||delta||_1 <= 1e-14 ({st_t['rounds']} iterations)"
     eps = 1e-9
-    for name, mode, reps in (("auto", pr.PR_MODE_AUTO, 3), ("pull", pr.PR_MODE_PULL, 3), ("push", pr.PR_MODE_PUSH, 2)):
+    for name, mode, reps in (("auto", pr.PR_MODE_AUTO, 3), ("pull", pr.PR_MODE_PULL, 3), ("push", pr.PR_MODE_PUSH, 2),
+                             ("async", pr.PR_MODE_ASYNC, 2)):
         ms, st = median_solve(G, flush, reps, C, eps, pr.PR_IFP2, pr.PR_FP32, out=out, opts=dict(mode=mode))
         res[f"ifp2_fp32_{name}"] = dict(ms=ms, rounds=st["rounds"], rounds_push=st["rounds_push"],
                                         rounds_pull=st["rounds_pull"], fp64_rounds=st["fp64_rounds"],
@@ -810,13 +811,14 @@ def main():
     ifp2_ms = t_step
     legs = {"reference_solution": f"GPU Power IEEE FP64 to ||delta||_1 <= 1e-14 (certified L1 <= {ref_bound:.2e})",
             "ifp2_df64": dict(ms=ifp2_ms, l1=ifp2_l1, rounds=rounds[0], gedges_s=value)}
-    for nm, algo, prec, eps in (("ifp2_fp64", pr.PR_IFP2, pr.PR_FP64, args.eps),
-                                ("ifp1_df64", pr.PR_IFP1, pr.PR_DF64, args.eps),
-                                ("ifp2_fp32", pr.PR_IFP2, pr.PR_FP32, 1e-6)):
+    for nm, algo, prec, eps, mode in (("ifp2_fp64", pr.PR_IFP2, pr.PR_FP64, args.eps, None),
+                                      ("ifp1_df64", pr.PR_IFP1, pr.PR_DF64, args.eps, None),
+                                      ("ifp2_fp32", pr.PR_IFP2, pr.PR_FP32, 1e-6, None),
+                                      ("ifp2_df64_async", pr.PR_IFP2, pr.PR_DF64, args.eps, pr.PR_MODE_ASYNC)):
         tms = []
         for _ in range(3):
             flush.zero_()
-            st = solve(algo=algo, prec=prec, eps=eps)
+            st = solve(algo=algo, prec=prec, eps=eps, opts=dict(mode=mode) if mode is not None else None)
             tms.append(st["ms"])
         legs[nm] = dict(ms=statistics.median(tms), l1=float((out - truth).abs().sum()), rounds=st["rounds"],
                         fp64_rounds=st["fp64_rounds"], eps=eps,

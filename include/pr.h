@@ -76,7 +76,7 @@ typedef enum {
     PR_MODE_AUTO = 0, /* per round: atomic push when the frontier is small, else CSC pull */
     PR_MODE_PUSH = 1, /* always atomic push over the frontier's out-lists */
     PR_MODE_PULL = 2, /* always deterministic gather over in-lists */
-    PR_MODE_LEVELS = 3 /* IFP2 on a graph created with levels: after two synchronous
+    PR_MODE_LEVELS = 3, /* IFP2 on a graph created with levels: after two synchronous
                           rounds, every round scans the levels in order and a push
                           reaches a higher level in the same round -- the in-round
                           propagation of the asynchronous scans of Sec. 3.2, made
@@ -85,6 +85,16 @@ typedef enum {
                           are those of the other modes.  PR_EINVAL with another
                           algorithm, on a graph without levels, and in
                           pr_solve_batch and the server */
+    PR_MODE_ASYNC = 4   /* IFP1/IFP2 push rounds in the concurrency of Sec. 3.2: the
+                          frontier is chosen at the round's start as in the other
+                          modes, but each frontier vertex pushes all of its residual
+                          at the moment it is processed (an atomic exchange), so mass
+                          it received earlier in the same round moves on at once.
+                          Fewer rounds; the schedule, and so the rounding and the
+                          round count, vary from run to run.  The stopping rule,
+                          mass conservation and the certified bound are unchanged.
+                          PR_EINVAL with PR_POWER, and in pr_solve_batch and the
+                          server */
 } pr_mode;
 
 /*

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libpr.so")
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY = range(8)
 PR_POWER, PR_IFP1, PR_IFP2 = 0, 1, 2
 PR_FP64, PR_FP32, PR_DF64 = 0, 1, 2
-PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL, PR_MODE_LEVELS = 0, 1, 2, 3
+PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL, PR_MODE_LEVELS, PR_MODE_ASYNC = 0, 1, 2, 3, 4
 STATUS_NAMES = ["PR_OK", "PR_EINVAL", "PR_ENOMEM", "PR_ECUDA", "PR_ENOTCONV", "PR_ETIMEOUT", "PR_EAGAIN",
                 "PR_EBUSY"]
 

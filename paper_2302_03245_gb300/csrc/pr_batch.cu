@@ -508,7 +508,8 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     pr_opts opt{};
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
-    if (opt.mode == PR_MODE_LEVELS) return fail(PR_EINVAL, "PR_MODE_LEVELS runs in pr_solve only");
+    if (opt.mode == PR_MODE_LEVELS || opt.mode == PR_MODE_ASYNC)
+        return fail(PR_EINVAL, "PR_MODE_LEVELS and PR_MODE_ASYNC run in pr_solve only");
     if (opt.mode < 0 || opt.mode > 2) return fail(PR_EINVAL, "unknown mode");
     for (int k = 0; k < count; k++) {
         if (!gs[k]) return fail(PR_EINVAL, "pr_solve_batch: graph " + std::to_string(k) + " is NULL");

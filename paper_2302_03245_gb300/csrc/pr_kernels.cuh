@@ -50,6 +50,7 @@ namespace pr {
 
 enum { MODE_ACT = 0, MODE_PUSH = 1, MODE_PULL = 2 };
 constexpr int POLICY_LEVELS = 3;  // PR_MODE_LEVELS: level-ordered pull rounds
+constexpr int POLICY_ASYNC = 4;   // PR_MODE_ASYNC: push rounds that take r_i at push time
 
 struct Ctl {
     // parameters (host-written per solve), in every format the kernels use
@@ -205,6 +206,11 @@ template <> struct ST<double> {
     static __device__ __forceinline__ void push_to(double *r, double *, int j, double w) { atomicAdd(&r[j], w); }
     static __device__ __forceinline__ void commit_sub(double *r, int i, double v) { atomicAdd(&r[i], -v); }
     static __device__ __forceinline__ double fold(double *r, double *, int i) { return r[i]; }
+    // asynchronous push rounds: all of r_i at this moment, leaving 0
+    static __device__ __forceinline__ double take(double *r, double *, int i) {
+        return __longlong_as_double(
+            (long long)atomicExch(reinterpret_cast<unsigned long long *>(&r[i]), 0ull));
+    }
 };
 template <> struct ST<float> {
     using V = float;
@@ -237,6 +243,7 @@ template <> struct ST<float> {
     static __device__ __forceinline__ void push_to(float *r, double *, int j, float w) { atomicAdd(&r[j], w); }
     static __device__ __forceinline__ void commit_sub(float *r, int i, float v) { atomicAdd(&r[i], -v); }
     static __device__ __forceinline__ float fold(float *r, double *, int i) { return r[i]; }
+    static __device__ __forceinline__ float take(float *r, double *, int i) { return atomicExch(&r[i], 0.f); }
 };
 template <> struct ST<float2> {
     using V = float2;
@@ -282,6 +289,15 @@ template <> struct ST<float2> {
         const float2 v = df_add(r[i], df_from_d(d));
         r[i] = v;
         din[i] = 0.0;
+        return v;
+    }
+    // asynchronous push rounds: r_i (written only by vertex i itself in a push
+    // round) plus everything its inbox has received so far, leaving both 0
+    static __device__ __forceinline__ float2 take(float2 *r, double *din, int i) {
+        const double d = __longlong_as_double(
+            (long long)atomicExch(reinterpret_cast<unsigned long long *>(&din[i]), 0ull));
+        const float2 v = df_add(r[i], df_from_d(d));
+        r[i] = make_float2(0.f, 0.f);
         return v;
     }
 };
@@ -581,7 +597,7 @@ __device__ __forceinline__ void round_decision(Ctl *ctl, int t, double R, long l
         return;
     }
     int mode;
-    if (ctl->policy == MODE_PUSH) mode = MODE_PUSH;
+    if (ctl->policy == MODE_PUSH || ctl->policy == POLICY_ASYNC) mode = MODE_PUSH;
     else if (ctl->policy == MODE_PULL || ctl->policy == POLICY_LEVELS) mode = MODE_PULL;
     else mode = (want && (double)E < ctl->pull_edges) ? MODE_PUSH : MODE_PULL;
     ctl->mode = mode;
@@ -653,6 +669,30 @@ __device__ __forceinline__ void push_commit(const Ctl *ctl, T *x, T *r, int i, T
     ST<T>::commit_sub(r, i, v);
 }
 
+// The mass a frontier vertex pushes, decided by one thread (lane 0 or thread
+// 0) and its reserve committed there.  Synchronous rounds: the activation's
+// snapshot v_i, subtracted from r_i.  Asynchronous rounds (PR_MODE_ASYNC, the
+// concurrency of Sec. 3.2): all of r_i at this moment, taken atomically, so
+// mass that reached i earlier in the same round moves on now.
+template <typename T>
+__device__ __forceinline__ T push_mass(const Ctl *ctl, bool async, T *x, T *r, double *din, const T *vbuf, int i) {
+    T v;
+    if (async) {
+        v = ST<T>::take(r, din, i);
+        x[i] = ST<T>::add(x[i], ST<T>::mul(ST<T>::om(ctl), v));
+    } else {
+        v = vbuf[i];
+        push_commit<T>(ctl, x, r, i, v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double shfl0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ float shfl0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ float2 shfl0(float2 v) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0));
+}
+
 template <typename T, bool IFP2>
 __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, RoundBuf B, int nb_thread,
                                                   int nb_warp) {
@@ -664,13 +704,13 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
     const T *vbuf = static_cast<const T *>(B.vbuf);
     const int32_t *bins = B.bins;
     const T cT = ST<T>::c(ctl);
+    const bool async = ctl->policy == POLICY_ASYNC;
     const int b = blockIdx.x;
     if (b < nb_thread) {
         const uint32_t c0 = cnt[0];
         for (uint32_t k = b * blockDim.x + threadIdx.x; k < c0; k += nb_thread * blockDim.x) {
             const int i = bins[k];
-            const T v = vbuf[i];
-            push_commit<T>(ctl, x, r, i, v);
+            const T v = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
@@ -682,8 +722,9 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
         const int wpb = blockDim.x >> 5;
         for (uint32_t k = (b - nb_thread) * wpb + (threadIdx.x >> 5); k < c1; k += nb_warp * wpb) {
             const int i = bins[(size_t)n_nd + k];
-            const T v = vbuf[i];
-            if (lane == 0) push_commit<T>(ctl, x, r, i, v);
+            T v = ST<T>::zero();
+            if (lane == 0) v = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
+            v = shfl0(v);
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
@@ -692,10 +733,13 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
     } else {
         const uint32_t c2 = cnt[2];
         const int nb_cta = gridDim.x - nb_thread - nb_warp;
+        __shared__ T vsh;
         for (uint32_t k = b - nb_thread - nb_warp; k < c2; k += nb_cta) {
             const int i = bins[(size_t)2 * n_nd + k];
-            const T v = vbuf[i];
-            if (threadIdx.x == 0) push_commit<T>(ctl, x, r, i, v);
+            if (threadIdx.x == 0) vsh = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
+            __syncthreads();
+            const T v = vsh;
+            __syncthreads();  // vsh is rewritten by the next vertex
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];

@@ -767,7 +767,8 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
     if (opt.pull_ratio <= 0) opt.pull_ratio = g->pull_ratio;
-    if (opt.mode < 0 || opt.mode > PR_MODE_LEVELS) return fail(PR_EINVAL, "unknown mode");
+    if (opt.mode < 0 || opt.mode > PR_MODE_ASYNC) return fail(PR_EINVAL, "unknown mode");
+    if (opt.mode == PR_MODE_ASYNC && algo == PR_POWER) return fail(PR_EINVAL, "PR_MODE_ASYNC runs IFP1 and IFP2");
     const bool levels = opt.mode == PR_MODE_LEVELS;
     if (levels && algo != PR_IFP2) return fail(PR_EINVAL, "PR_MODE_LEVELS runs IFP2 only");
     if (levels && g->levels <= 0) return fail(PR_EINVAL, "PR_MODE_LEVELS needs a graph created with levels");
@@ -806,7 +807,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     h.scan_ref = algo == PR_IFP2 ? g->scan_nd_ref : G.m_ref;
     h.scan_unref = algo == PR_IFP2 ? g->scan_nd_unref : G.m_unref;
     h.mode = MODE_ACT;
-    h.want_bins = opt.mode == PR_MODE_AUTO || opt.mode == PR_MODE_PUSH;
+    h.want_bins = opt.mode == PR_MODE_AUTO || opt.mode == PR_MODE_PUSH || opt.mode == PR_MODE_ASYNC;
     h.unref_active = 1;
     h.gs_phase = 0;
     *W.hctl = h;
