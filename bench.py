@@ -218,7 +218,10 @@ def info_sms(torch):
 
 
 def median_solve(G, flush, reps, *a, **kw):
-    """Median device ms of `reps` solves (L2 flushed before each) and the last stats."""
+    """Median device ms of `reps` solves (L2 flushed before each) and the last stats.
+    With --host-rounds the rounds are launched from the host (for a profiler)."""
+    if ARGS is not None and ARGS.host_rounds:
+        kw["opts"] = dict(kw.get("opts") or {}, use_graph=-1)
     ms, st = [], None
     for _ in range(reps):
         flush.zero_()
@@ -266,7 +269,10 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
            "graph": {k: G.info[k] for k in ("n", "m", "n_nd", "n_ref", "n_d", "m_d", "n_u", "max_indeg",
                                              "max_outdeg", "ms_preprocess")}}
     t0 = time.perf_counter()
-    tuning, rep = G.autotune(pr.PR_FP32, max_ms=2000.0)
+    if ARGS is not None and ARGS.no_tune:
+        tuning, rep = G.tuning(), "default launch parameters (--no-tune)"
+    else:
+        tuning, rep = G.autotune(pr.PR_FP32, max_ms=2000.0)
     res["tuning"] = dict(tuning, autotune_s=time.perf_counter() - t0, report_last=rep.splitlines()[-1])
     n = G.info["n"]
     out = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -311,7 +317,8 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
     off, dst = gd.csr32()
     G = pr.Graph(gd.n, gd.m, off, dst, mem_is_device=True, stream=stream, levels=8)
     del gd, off, dst
-    G.autotune(pr.PR_FP32, max_ms=2000.0)
+    if ARGS is None or not ARGS.no_tune:
+        G.autotune(pr.PR_FP32, max_ms=2000.0)
     for name, prec in (("fp32", pr.PR_FP32), ("df64", pr.PR_DF64)):
         for mname, mode in (("auto", pr.PR_MODE_AUTO), ("levels8", pr.PR_MODE_LEVELS)):
             ms, st = median_solve(G, flush, 2, C, eps, pr.PR_IFP2, prec, out=out, opts=dict(mode=mode))
