@@ -453,6 +453,7 @@ static Plan make_plan(const RangeSpec *r, int nr, int budget) {
         const int64_t need = r[k].lanes == kTileLanes ? r[k].nt : (rows + groups_per_block - 1) / groups_per_block;
         int64_t nb = (int64_t)(budget * (work / std::max(total, 1.0)) + 0.5);
         nb = std::max<int64_t>(1, std::min(nb, need));
+        if (r[k].lanes == kClusterLanes) nb = rows * kLevelCluster;  // one cluster per row, whatever the budget
         Seg &sg = P.seg[P.nseg++];
         sg.lo = r[k].lo;
         sg.hi = r[k].hi;
@@ -503,10 +504,17 @@ void build_plans(pr_graph *g) {
         } else {
             tiled.assign(rs, rs + kNumThr + 1);
         }
-        for (const RangeSpec &r : rs) {
+        for (int c = 0; c <= kNumThr; c++) {
+            const RangeSpec &r = rs[c];
             if (k < nr - 1) {
                 ref.push_back(r);
-                if (g->levels) lvl[k].push_back(r);
+                if (!g->levels) continue;
+                if (c == 0) {  // the block rows: the longest ones by clusters, first in the plan
+                    lvl[k].push_back(RangeSpec{r.lo, g->cl_hi[k], kClusterLanes, r.edges, 0, 0});
+                    lvl[k].push_back(RangeSpec{g->cl_hi[k], r.hi, 0, r.edges, 0, 0});
+                } else {
+                    lvl[k].push_back(r);
+                }
             } else {
                 d.push_back(r);
             }
@@ -626,12 +634,29 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
         }
         PR_CK(cudaGetLastError());
     }
+    // level-ordered rounds: the block rows above kClusterRowMin entries of each level
+    int32_t cl_hi[kMaxLevels + 1];
+    for (int k = 0; k < nr; k++) cl_hi[k] = lo[k];
+    if (g->levels) {
+        const int32_t cthr = kClusterRowMin;
+        std::vector<int32_t> b0(nr);
+        for (int k = 0; k < nr; k++) b0[k] = b[(size_t)k * kNumThr];
+        PR_CK(cudaMemcpyAsync(d_thr, &cthr, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        PR_CK(cudaMemcpyAsync(d_lo, lo, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+        PR_CK(cudaMemcpyAsync(d_hi, b0.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+        k_bin_bounds<<<nr, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_lo, d_hi, d_thr, 1,
+                                       d_bounds);
+        PR_CK(cudaMemcpyAsync(cl_hi, d_bounds, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        PR_CK(cudaGetLastError());
+    }
     // plans are built into a scratch copy first: the graph keeps its bins on failure
     pr_graph *T = new (std::nothrow) pr_graph();
     if (!T) return fail(PR_ENOMEM, "host allocation failed");
     T->G = g->G;
     T->levels = g->levels;
     for (int l = 0; l <= kMaxLevels; l++) T->level_lo[l] = g->level_lo[l];
+    for (int k = 0; k < nr; k++) T->cl_hi[k] = cl_hi[k];
     T->nranges = nr;
     for (int k = 0; k < nr; k++) {
         T->range_lo[k] = lo[k];
@@ -648,8 +673,19 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     build_plans(T);
     bool ok = T->plan_all.nblocks <= kMaxBlocks && T->plan_nd.nblocks <= kMaxBlocks &&
               T->plan_all_t.nblocks <= kMaxBlocks && T->plan_nd_t.nblocks <= kMaxBlocks;
-    int lvl_blocks = T->plan_unref.nblocks;  // one level-ordered round's launches share the slots
-    for (int l = 0; l < T->levels; l++) lvl_blocks += T->plan_lvl[l].nblocks;
+    // one level-ordered round's launches share the slots; each grid is padded
+    // to whole clusters
+    auto padded = [](int nb) { return (nb + kLevelCluster - 1) / kLevelCluster * kLevelCluster; };
+    int lvl_blocks = T->levels ? padded(T->plan_unref.nblocks) : 0;
+    for (int l = 0; l < T->levels; l++) {
+        lvl_blocks += padded(T->plan_lvl[l].nblocks);
+        // a cluster segment must start and end on cluster boundaries (it is the first segment)
+        const Plan &PL = T->plan_lvl[l];
+        for (int q = 0; q < PL.nseg; q++)
+            if (PL.seg[q].lanes == kClusterLanes &&
+                (PL.seg[q].blk0 % kLevelCluster != 0 || PL.seg[q].nblk % kLevelCluster != 0))
+                ok = false;
+    }
     ok = ok && lvl_blocks <= kMaxBlocks;
     if (!ok) {
         delete T;
@@ -679,6 +715,7 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     g->tile_row.swap(tiles);  // the old table is released when `tiles` leaves scope (stream synchronized)
     g->G.tile_row = g->tile_row.as<int32_t>();
     for (int l = 0; l < kMaxLevels; l++) g->plan_lvl[l] = T->plan_lvl[l];
+    for (int k = 0; k <= kMaxLevels; k++) g->cl_hi[k] = T->cl_hi[k];
     g->plan_unref = T->plan_unref;
     g->plan_gen++;
     delete T;

@@ -112,6 +112,13 @@ struct Seg {
 #define PR_TILE_E 1024
 #endif
 constexpr int kTileLanes = -1;
+// Level-ordered rounds serve each row with more than kClusterRowMin in-list
+// entries by a cluster of kLevelCluster blocks (lanes = kClusterLanes): one
+// level launch is as long as its longest row, and one block takes a 100k-entry
+// row through about 50 dependent load steps.
+constexpr int kClusterLanes = -2;
+constexpr int kLevelCluster = 8;
+constexpr int kClusterRowMin = 16384;
 constexpr int kTileE = PR_TILE_E;
 constexpr int kTileDeg = 64;
 constexpr int kTileW = 2;
@@ -165,6 +172,7 @@ struct pr_graph {
     // into `levels` contiguous row ranges [level_lo[l], level_lo[l+1])
     int32_t levels = 0;
     int32_t level_lo[pr::kMaxLevels + 1] = {};
+    int32_t cl_hi[pr::kMaxLevels + 1] = {};  // per level: rows [level_lo, cl_hi) are served by block clusters
     pr::Buf gs_back;  // [n_nd] valid out-edges of a row into its own or a lower level
     pr::Plan plan_lvl[pr::kMaxLevels]{}, plan_unref{};
     double pull_ratio = 0.04;  // AUTO push/pull switch used when a solve passes 0

@@ -40,6 +40,7 @@
 // residual-L1 and other sums run in double-float with a final FP64 sum.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include <cmath>
@@ -1031,8 +1032,8 @@ __global__ void __launch_bounds__(kThreads, PR_PULL_MIN_BLOCKS) k_round_pull(Dev
 // a level's plan: its lane bins only (a kernel argument of 150 bytes instead
 // of the full plan's 2.6 KB)
 struct LevelPlan {
-    Seg seg[kNumThr + 1];
-    int32_t nseg, nblocks;
+    Seg seg[kNumThr + 2];    // the cluster rows, the other block rows, then the lane bins
+    int32_t nseg, nblocks;   // nblocks: blocks with work; the grid is padded to whole clusters
 };
 
 struct LevelLaunch {
@@ -1171,6 +1172,49 @@ __device__ __forceinline__ void level_rows(const DevGraph &G, const Seg &S, int 
     }
 }
 
+// A row with more than kClusterRowMin in-list entries, served by a cluster of
+// kLevelCluster blocks: block q of the cluster sums the entries q * 256 +
+// tid, stepping 8 * 256 (in entry order per thread), and the cluster's rank-0
+// block adds the blocks' sums in rank order through distributed shared memory
+// and runs the row's epilogue.  Every block of a cluster takes this path or
+// none does: the segment starts and ends on cluster boundaries (checked when
+// the plan is built, and here, together with the launch's cluster size).
+template <typename T>
+__device__ __forceinline__ void level_cluster_row(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                                  const RoundBuf &B, const typename ST<T>::V *wprev,
+                                                  typename ST<T>::V *wcur, int phase, int split,
+                                                  typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul,
+                                                  typename GT<typename ST<T>::V>::A *sha) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    if (cl.num_blocks() != kLevelCluster || S.blk0 % kLevelCluster != 0 || S.nblk % kLevelCluster != 0) return;
+    __shared__ A part;
+    const int rank = (int)cl.block_rank();
+    const int j = S.lo + lb / kLevelCluster;
+    const bool ok = j < S.hi;
+    A acc = GT<V>::zero();
+    const int start = rank * (int)blockDim.x + (int)threadIdx.x, step = kLevelCluster * (int)blockDim.x;
+    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, &j, &ok, wcur, wprev, split, phase == 1, start, step, &acc);
+    if (phase == 0)
+        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, &j, &ok, wcur, wprev, split, false, start, step, &acc);
+    acc = block_sum_gt<V>(acc, sha);
+    if (threadIdx.x == 0) part = acc;
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0 && ok) {
+        A tot = GT<V>::zero();
+        for (int q = 0; q < kLevelCluster; q++) tot = GT<V>::add(tot, *cl.map_shared_rank(&part, q));
+        if (phase == 0) {
+            int pd = 0;
+            pull_row_epilogue<T, true>(G, ctl, B, wcur, j, ST<T>::from_acc(tot), 0, pd, Rl, Fl, El, ul);
+        } else {
+            level_row_epilogue<T>(G, ctl, B, wcur, j, ST<T>::from_acc(tot), phase == 1, Rl, Fl, El);
+        }
+    }
+    cl.sync();  // the other blocks' shared memory is read above: they stay until rank 0 is done
+}
+
 // the decision after a round of level launches (t = the round just run)
 __device__ __forceinline__ void level_decision(Ctl *ctl, int t, int phase, double R, long long F, long long E,
                                                int u, const Trace &tr) {
@@ -1271,7 +1315,7 @@ __global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(
                 r[j] = ST<T>::zero();
             }
         }
-    } else if (PL.nseg > 0) {
+    } else if (PL.nseg > 0 && (int)blockIdx.x < PL.nblocks) {  // blocks past nblocks pad the last cluster
         int lo = 0, hi = PL.nseg - 1;  // the last segment with blk0 <= blockIdx.x
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -1281,6 +1325,9 @@ __global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(
         const Seg S = PL.seg[lo];
         const int lb = blockIdx.x - S.blk0;
         switch (S.lanes) {
+            case kClusterLanes:
+                level_cluster_row<T>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul, sha);
+                break;
             case 1: level_rows<T, 1>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
             case 2: level_rows<T, 2>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;
             case 4: level_rows<T, 4>(G, S, lb, ctl, B, wprev, wcur, phase, split, Rl, Fl, El, ul); break;

@@ -460,24 +460,31 @@ static void launch_round_levels(pr_graph *g, Workspace &W, cudaStream_t s, Prof 
     const Partials P = partials_of(W);
     const Trace tr = trace_of(W);
     const RoundBuf B = round_bufs<T>(W);
-    int total = g->plan_unref.nblocks;
-    for (int l = 0; l < g->levels; l++) total += g->plan_lvl[l].nblocks;
+    // grids padded to whole clusters of kLevelCluster blocks (the long rows'
+    // clusters; the padding blocks only take part in the reduction)
+    auto grid_of = [](const Plan &PL) { return (PL.nblocks + kLevelCluster - 1) / kLevelCluster * kLevelCluster; };
+    int total = grid_of(g->plan_unref);
+    for (int l = 0; l < g->levels; l++) total += grid_of(g->plan_lvl[l]);
     // programmatic stream serialization: each level launch may start while the
     // previous one drains (the kernel waits for it before reading anything)
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = kLevelCluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     auto launch = [&](const Plan &PL, LevelLaunch lv) {
         LevelPlan LP{};
-        LP.nseg = std::min(PL.nseg, kNumThr + 1);  // a level or the unreferenced rows: one range of lane bins
+        LP.nseg = std::min(PL.nseg, kNumThr + 2);  // a level (cluster rows, block rows, lane bins) or the unreferenced rows
         LP.nblocks = PL.nblocks;
         for (int k = 0; k < LP.nseg; k++) LP.seg[k] = PL.seg[k];
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)PL.nblocks);
+        cfg.gridDim = dim3((unsigned)grid_of(PL));
         cfg.blockDim = dim3(kThreads);
         cfg.stream = s;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, k_round_levels<T>, G, LP, ctl, P, B, tr, lv);
         if (e != cudaSuccess && W.launch_err == cudaSuccess) W.launch_err = e;
     };
@@ -485,7 +492,7 @@ static void launch_round_levels(pr_graph *g, Workspace &W, cudaStream_t s, Prof 
     int base = 0;
     for (int l = 0; l < g->levels; l++) {
         launch(g->plan_lvl[l], LevelLaunch{g->level_lo[l], base, total, 0});
-        base += g->plan_lvl[l].nblocks;
+        base += grid_of(g->plan_lvl[l]);
     }
     launch(g->plan_unref, LevelLaunch{G.n_ref, base, total, 1});
     const size_t e1 = prof ? prof->mark(s) : 0;

@@ -52,6 +52,9 @@ GRAPHS = [
     ("small3000", lambda: gg.random_small(3000, 6.0, 0.25, 0.1, seed=2)),
     ("rmat13", lambda: gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=4)),
     ("hub20k", lambda: hub_graph(20000, 3)),
+    # a row with more in-list entries than one block takes (kClusterRowMin =
+    # 16384): served by a cluster of 8 blocks in the level-ordered rounds
+    ("hub40k", lambda: hub_graph(40000, 4)),
 ]
 
 
@@ -87,6 +90,8 @@ def check_against_oracle(G, g, L, prec, eps, p=None, p_idx=None, p_dense=None, u
 @pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_DF64))
 def test_level_rounds_match_oracle_exactly(gcase, L, prec):
     g = gcase[1]()
+    if gcase[0] == "hub40k":
+        assert g.stats()["max_indeg"] > 16384
     with leveled(g, L) as G:
         assert G.info["levels"] == L
         check_against_oracle(G, g, L, prec, 1e-10)
