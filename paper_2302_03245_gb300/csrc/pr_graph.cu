@@ -488,6 +488,7 @@ void build_plans(pr_graph *g) {
     const int32_t n_nd = g->G.n_nd, n_ref = g->G.n_ref;
     const int nr = g->nranges;  // referenced ranges (levels), then the dangling range
     std::vector<RangeSpec> ref, d, lvl[kMaxLevels], ref_t, d_t;
+    long long cluster_blocks = 0;  // blocks of all levels' cluster segments
     for (int k = 0; k < nr; k++) {
         const long long *E = &g->range_edges[(size_t)k * (kNumThr + 2)];
         RangeSpec rs[kNumThr + 1];
@@ -510,8 +511,13 @@ void build_plans(pr_graph *g) {
                 ref.push_back(r);
                 if (!g->levels) continue;
                 if (c == 0) {  // the block rows: the longest ones by clusters, first in the plan
-                    lvl[k].push_back(RangeSpec{r.lo, g->cl_hi[k], kClusterLanes, r.edges, 0, 0});
-                    lvl[k].push_back(RangeSpec{g->cl_hi[k], r.hi, 0, r.edges, 0, 0});
+                    // at most half of a level's share of the partial-sum slots go to
+                    // clusters (the rows are sorted by in-degree: the longest first)
+                    const int32_t max_rows = std::max(1, kMaxBlocks / (g->levels + 1) / 2 / kLevelCluster);
+                    const int32_t ch = std::min(g->cl_hi[k], r.lo + max_rows);
+                    cluster_blocks += (long long)std::max(0, ch - r.lo) * kLevelCluster;
+                    lvl[k].push_back(RangeSpec{r.lo, ch, kClusterLanes, r.edges, 0, 0});
+                    lvl[k].push_back(RangeSpec{ch, r.hi, 0, r.edges, 0, 0});
                 } else {
                     lvl[k].push_back(r);
                 }
@@ -543,7 +549,10 @@ void build_plans(pr_graph *g) {
     // block budget (capped so the round's launches fit the partial-sum slots);
     // a small level is limited by its row groups in make_plan
     if (g->levels) {
-        const int cap = std::max(32, kMaxBlocks / (g->levels + 1) - kNumThr - 2);  // make_plan adds <= 1 per segment
+        // what the cluster segments and the padding to whole clusters leave,
+        // shared by the L + 1 launches (make_plan adds at most 1 per segment)
+        const long long left = kMaxBlocks - cluster_blocks - (long long)kLevelCluster * (g->levels + 1);
+        const int cap = std::max(32, (int)(left / (g->levels + 1)) - kNumThr - 3);
         const int b = std::min(g->block_budget, cap);
         for (int l = 0; l < g->levels; l++) g->plan_lvl[l] = make_plan(lvl[l].data(), (int)lvl[l].size(), b);
         const std::vector<RangeSpec> u{unref};
