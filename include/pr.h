@@ -249,7 +249,7 @@ pr_status pr_graph_get_info(const pr_graph *g, pr_graph_info *info);
  *                one thread sums each row there.  Default {4096, 64, 32, 16,
  *                8, 4}.
  *  block_budget: blocks of a dense gather launch, split across the bins in
- *                proportion to their in-list entries (1 .. 8192).
+ *                proportion to their in-list entries (1 .. 16384).
  *  pull_ratio:   the AUTO delivery switch used when a solve passes
  *                pull_ratio = 0: a round pulls when its frontier's out-edges
  *                reach pull_ratio x the valid edges (m, or m - m_d for IFP2).

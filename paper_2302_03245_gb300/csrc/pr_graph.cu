@@ -488,7 +488,19 @@ void build_plans(pr_graph *g) {
     const int32_t n_nd = g->G.n_nd, n_ref = g->G.n_ref;
     const int nr = g->nranges;  // referenced ranges (levels), then the dangling range
     std::vector<RangeSpec> ref, d, lvl[kMaxLevels], ref_t, d_t;
-    long long cluster_blocks = 0;  // blocks of all levels' cluster segments
+    // level-ordered rounds: every row above kClusterRowMin in-list entries gets
+    // a block cluster, unless all levels' clusters together would take more
+    // than half the partial-sum slots; then the clusters per level are halved
+    // until they fit (the rows are sorted by in-degree: the longest keep theirs)
+    int32_t max_rows = kMaxBlocks / kLevelCluster;
+    auto cluster_total = [&](int32_t cap) {
+        long long t = 0;
+        for (int k = 0; k + 1 < nr && g->levels; k++)
+            t += (long long)std::min(cap, std::max(0, g->cl_hi[k] - g->range_lo[k])) * kLevelCluster;
+        return t;
+    };
+    while (max_rows > 1 && cluster_total(max_rows) > kMaxBlocks / 2) max_rows /= 2;
+    const long long cluster_blocks = g->levels ? cluster_total(max_rows) : 0;
     for (int k = 0; k < nr; k++) {
         const long long *E = &g->range_edges[(size_t)k * (kNumThr + 2)];
         RangeSpec rs[kNumThr + 1];
@@ -510,14 +522,15 @@ void build_plans(pr_graph *g) {
             if (k < nr - 1) {
                 ref.push_back(r);
                 if (!g->levels) continue;
-                if (c == 0) {  // the block rows: the longest ones by clusters, first in the plan
-                    // at most half of a level's share of the partial-sum slots go to
-                    // clusters (the rows are sorted by in-degree: the longest first)
-                    const int32_t max_rows = std::max(1, kMaxBlocks / (g->levels + 1) / 2 / kLevelCluster);
+                // the longest rows by clusters (first in the plan), then one block
+                // per row down to kLevelBlockRowMin entries, then warps
+                const int32_t bh = std::max(rs[0].hi, g->lb_hi[k]);  // end of the level's block rows
+                if (c == 0) {
                     const int32_t ch = std::min(g->cl_hi[k], r.lo + max_rows);
-                    cluster_blocks += (long long)std::max(0, ch - r.lo) * kLevelCluster;
                     lvl[k].push_back(RangeSpec{r.lo, ch, kClusterLanes, r.edges, 0, 0});
-                    lvl[k].push_back(RangeSpec{ch, r.hi, 0, r.edges, 0, 0});
+                    lvl[k].push_back(RangeSpec{ch, bh, 0, r.edges, 0, 0});
+                } else if (c == 1) {
+                    lvl[k].push_back(RangeSpec{bh, r.hi, 32, r.edges, 0, 0});
                 } else {
                     lvl[k].push_back(r);
                 }
@@ -550,9 +563,12 @@ void build_plans(pr_graph *g) {
     // a small level is limited by its row groups in make_plan
     if (g->levels) {
         // what the cluster segments and the padding to whole clusters leave,
-        // shared by the L + 1 launches (make_plan adds at most 1 per segment)
+        // shared by the L + 1 launches (make_plan adds at most 1 per segment);
+        // and no more than kLevelRoundBlocks / (L + 1): a level launch is short,
+        // and more blocks than that measured slower (their scheduling and the
+        // round's final reduction over all slots grow with them)
         const long long left = kMaxBlocks - cluster_blocks - (long long)kLevelCluster * (g->levels + 1);
-        const int cap = std::max(32, (int)(left / (g->levels + 1)) - kNumThr - 3);
+        const int cap = std::max(32, (int)(std::min<long long>(left, kLevelRoundBlocks) / (g->levels + 1)) - kNumThr - 3);
         const int b = std::min(g->block_budget, cap);
         for (int l = 0; l < g->levels; l++) g->plan_lvl[l] = make_plan(lvl[l].data(), (int)lvl[l].size(), b);
         const std::vector<RangeSpec> u{unref};
@@ -643,21 +659,27 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
         }
         PR_CK(cudaGetLastError());
     }
-    // level-ordered rounds: the block rows above kClusterRowMin entries of each level
-    int32_t cl_hi[kMaxLevels + 1];
-    for (int k = 0; k < nr; k++) cl_hi[k] = lo[k];
+    // level-ordered rounds: per level, the rows above kClusterRowMin entries
+    // (clusters) and above kLevelBlockRowMin (one block each), both within the
+    // rows the tuning gives a block or a warp ([lo, bounds[1]))
+    int32_t cl_hi[kMaxLevels + 1], lb_hi[kMaxLevels + 1];
+    for (int k = 0; k < nr; k++) cl_hi[k] = lb_hi[k] = lo[k];
     if (g->levels) {
-        const int32_t cthr = kClusterRowMin;
-        std::vector<int32_t> b0(nr);
-        for (int k = 0; k < nr; k++) b0[k] = b[(size_t)k * kNumThr];
-        PR_CK(cudaMemcpyAsync(d_thr, &cthr, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        const int32_t lthr[2] = {kClusterRowMin, kLevelBlockRowMin};
+        std::vector<int32_t> b1(nr), out(2 * (size_t)nr);
+        for (int k = 0; k < nr; k++) b1[k] = b[(size_t)k * kNumThr + 1];
+        PR_CK(cudaMemcpyAsync(d_thr, lthr, sizeof(lthr), cudaMemcpyHostToDevice, s));
         PR_CK(cudaMemcpyAsync(d_lo, lo, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
-        PR_CK(cudaMemcpyAsync(d_hi, b0.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
-        k_bin_bounds<<<nr, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_lo, d_hi, d_thr, 1,
+        PR_CK(cudaMemcpyAsync(d_hi, b1.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, s));
+        k_bin_bounds<<<nr, 32, 0, s>>>(g->inr_off.as<int32_t>(), g->inu_off.as<int32_t>(), d_lo, d_hi, d_thr, 2,
                                        d_bounds);
-        PR_CK(cudaMemcpyAsync(cl_hi, d_bounds, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaMemcpyAsync(out.data(), d_bounds, sizeof(int32_t) * out.size(), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
         PR_CK(cudaGetLastError());
+        for (int k = 0; k < nr; k++) {
+            cl_hi[k] = out[2 * (size_t)k];
+            lb_hi[k] = out[2 * (size_t)k + 1];
+        }
     }
     // plans are built into a scratch copy first: the graph keeps its bins on failure
     pr_graph *T = new (std::nothrow) pr_graph();
@@ -665,7 +687,10 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     T->G = g->G;
     T->levels = g->levels;
     for (int l = 0; l <= kMaxLevels; l++) T->level_lo[l] = g->level_lo[l];
-    for (int k = 0; k < nr; k++) T->cl_hi[k] = cl_hi[k];
+    for (int k = 0; k < nr; k++) {
+        T->cl_hi[k] = cl_hi[k];
+        T->lb_hi[k] = lb_hi[k];
+    }
     T->nranges = nr;
     for (int k = 0; k < nr; k++) {
         T->range_lo[k] = lo[k];
@@ -724,7 +749,10 @@ pr_status set_bins(pr_graph *g, const int32_t *thr, int32_t budget, cudaStream_t
     g->tile_row.swap(tiles);  // the old table is released when `tiles` leaves scope (stream synchronized)
     g->G.tile_row = g->tile_row.as<int32_t>();
     for (int l = 0; l < kMaxLevels; l++) g->plan_lvl[l] = T->plan_lvl[l];
-    for (int k = 0; k <= kMaxLevels; k++) g->cl_hi[k] = T->cl_hi[k];
+    for (int k = 0; k <= kMaxLevels; k++) {
+        g->cl_hi[k] = T->cl_hi[k];
+        g->lb_hi[k] = T->lb_hi[k];
+    }
     g->plan_unref = T->plan_unref;
     g->plan_gen++;
     delete T;

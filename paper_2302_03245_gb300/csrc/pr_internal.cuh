@@ -119,6 +119,13 @@ constexpr int kTileLanes = -1;
 constexpr int kClusterLanes = -2;
 constexpr int kLevelCluster = 8;
 constexpr int kClusterRowMin = 16384;
+// and rows above kLevelBlockRowMin entries get a whole block there, whatever
+// the tuned block-row threshold (a warp takes a 16k-entry row through 64 steps)
+constexpr int kLevelBlockRowMin = 4096;
+#ifndef PR_LEVEL_ROUND_BLOCKS
+#define PR_LEVEL_ROUND_BLOCKS 16384
+#endif
+constexpr int kLevelRoundBlocks = PR_LEVEL_ROUND_BLOCKS;  // lane-bin blocks of one level-ordered round, all launches
 constexpr int kTileE = PR_TILE_E;
 constexpr int kTileDeg = 64;
 constexpr int kTileW = 2;
@@ -133,7 +140,7 @@ struct Plan {
 };
 
 constexpr int kThreads = 256;       // block size of every row/vertex kernel
-constexpr int kMaxBlocks = 16384;   // partial-sum slots of a reduction (>= any grid)
+constexpr int kMaxBlocks = 32768;   // partial-sum slots of a reduction (>= any grid; one level-ordered round shares them)
 constexpr int kWarpRowMin = 32;     // push bins: out-degree above which a vertex gets a warp
 constexpr int kCtaRowMin = 4096;    // push bins: out-degree above which a vertex gets a CTA
 // Pull bins (in-degree d): d > thr[0] block per row; thr[k] < d <= thr[k-1]
@@ -173,6 +180,7 @@ struct pr_graph {
     int32_t levels = 0;
     int32_t level_lo[pr::kMaxLevels + 1] = {};
     int32_t cl_hi[pr::kMaxLevels + 1] = {};  // per level: rows [level_lo, cl_hi) are served by block clusters
+    int32_t lb_hi[pr::kMaxLevels + 1] = {};  // per level: rows above kLevelBlockRowMin entries end here
     pr::Buf gs_back;  // [n_nd] valid out-edges of a row into its own or a lower level
     pr::Plan plan_lvl[pr::kMaxLevels]{}, plan_unref{};
     double pull_ratio = 0.04;  // AUTO push/pull switch used when a solve passes 0
