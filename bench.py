@@ -743,7 +743,9 @@ def main():
     value = my_edges / my_time / 1e9
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_step,
+            "ms_per_step_median_min": [statistics.median(ms), min(ms)],
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "df64 (fp32 hi+lo pairs; fp64 final sums and output)",
             "data": "synthetic",
             "config": dict(workload(args.scale, args.algo, args.levels), l2="512 MB buffer written between timed steps",
