@@ -568,11 +568,28 @@ void build_plans(pr_graph *g) {
         // and more blocks than that measured slower (their scheduling and the
         // round's final reduction over all slots grow with them)
         const long long left = kMaxBlocks - cluster_blocks - (long long)kLevelCluster * (g->levels + 1);
-        const int cap = std::max(32, (int)(std::min<long long>(left, kLevelRoundBlocks) / (g->levels + 1)) - kNumThr - 3);
-        const int b = std::min(g->block_budget, cap);
-        for (int l = 0; l < g->levels; l++) g->plan_lvl[l] = make_plan(lvl[l].data(), (int)lvl[l].size(), b);
+        const long long round_blocks = std::min<long long>(left, kLevelRoundBlocks);
+        // the round's lane-bin blocks go to the levels in proportion to their
+        // work (R-MAT's hubs crowd the middle levels), at least 32 each, and no
+        // level more than twice the block budget
+        auto work_of = [](const std::vector<RangeSpec> &v) {
+            double w = 0;
+            for (const RangeSpec &r : v)
+                if (r.hi > r.lo && r.lanes != kClusterLanes) w += (double)r.edges + 2.0 * (r.hi - r.lo);
+            return w;
+        };
         const std::vector<RangeSpec> u{unref};
-        g->plan_unref = make_plan(u.data(), 1, b);
+        double wsum = work_of(u);
+        for (int l = 0; l < g->levels; l++) wsum += work_of(lvl[l]);
+        const long long spare = round_blocks - (long long)(g->levels + 1) * (kNumThr + 3 + 32);
+        auto budget_of = [&](const std::vector<RangeSpec> &v) {
+            const double share = wsum > 0 ? work_of(v) / wsum : 0.0;
+            const long long b = 32 + (long long)(std::max<long long>(spare, 0) * share);
+            return (int)std::min<long long>(b, 2LL * g->block_budget);
+        };
+        for (int l = 0; l < g->levels; l++)
+            g->plan_lvl[l] = make_plan(lvl[l].data(), (int)lvl[l].size(), budget_of(lvl[l]));
+        g->plan_unref = make_plan(u.data(), 1, budget_of(u));
     }
 }
 
