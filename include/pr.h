@@ -218,12 +218,17 @@ pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const in
                           void *cuda_stream, pr_graph **g);
 
 /*
- * Graph options (pr_graph_create_ex; NULL or zero-initialised = defaults).
+ * pr_graph_create with options (the in-round propagation of the asynchronous
+ * scans of Sec. 3.2 needs an order of the vertices; see PR_MODE_LEVELS).
+ * Arguments, ownership and errors as pr_graph_create; opts may be NULL
+ * (zero-initialised = defaults); the reserved fields are not read (set them 0).
  *  levels: 0, or L in [1, 16] to prepare level-ordered rounds (PR_MODE_LEVELS):
  *          the non-dangling vertices with in-edges are ranked by
  *          q = floor(2^31 (indeg + 1) / (indeg + outdeg + 2)), ascending (ties
- *          by id), and rank r of n_ref gets level floor(r L / n_ref).  Every
- *          solve works on such a graph; only PR_MODE_LEVELS needs it.
+ *          by caller id), and rank r of n_ref gets level floor(r L / n_ref);
+ *          inside the referenced class the internal ids run level by level.
+ *          Every mode works on such a graph; only PR_MODE_LEVELS needs it.
+ *          PR_EINVAL for L outside [0, 16].
  */
 typedef struct {
     int32_t levels;
