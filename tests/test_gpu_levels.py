@@ -160,6 +160,20 @@ def test_fp32_form_and_certified_bound(seed):
         assert st["rounds"] < sync["rounds"]
 
 
+@pytest.mark.parametrize("L", (1, 3, 16))
+def test_cluster_rows_in_every_precision(L):
+    """A hub row above 16384 entries (an 8-block cluster) in the FP32 form,
+    double-float and IEEE FP64, against the exact PageRank."""
+    g = hub_graph(40000, 5)
+    assert g.stats()["max_indeg"] > 16384
+    truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
+    with leveled(g, L) as G:
+        for prec, eps, slack in ((pr.PR_FP32, 1e-7, 2e-7), (pr.PR_DF64, 1e-11, 1e-13), (pr.PR_FP64, 1e-11, 1e-13)):
+            out, st, status = G.solve(C, eps, pr.PR_IFP2, prec, opts=dict(mode=pr.PR_MODE_LEVELS))
+            assert status == pr.PR_OK, pr.pr_last_error()
+            assert l1(out, truth) <= st["err_bound"] + slack, (prec, l1(out, truth), st["err_bound"])
+
+
 @pytest.mark.parametrize("mode", (pr.PR_MODE_AUTO, pr.PR_MODE_PUSH, pr.PR_MODE_PULL))
 @pytest.mark.parametrize("algo", (pr.PR_IFP1, pr.PR_IFP2))
 def test_leveled_graph_in_the_other_modes(mode, algo):
