@@ -81,6 +81,7 @@ def _bind(lib):
     lib.orc_ifp_sequential.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, P, i32, P, P, P, P]
     lib.orc_ifp_rounds.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32,
                                    P, P, P, P, P, P, P, P]
+    lib.orc_ifp_async.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32, P, P, P, P, P, P]
     lib.orc_ifp2_levels.argtypes = [i32, P, P, dbl, dbl, dbl, P, P, i32, i32,
                                     P, P, P, P, P, P, P, P]
     return lib
@@ -161,6 +162,28 @@ class Oracle:
             out.update(R=tR[:k + 1].copy(), F=tF[:k].copy(), E=tE[:k].copy(), mass=tM[1:k + 1].copy())
         return out
 
+
+    def ifp_async(self, algo, g, c, eps, p, xi_act=None, max_rounds=100000, trace=True):
+        """IFP1/IFP2 asynchronous rounds, frontier in id order (orc_ifp_async).
+        Returns dict(pi, x, r, rounds, status, R, F)."""
+        off, dst = _csr(g)
+        p = _f64(p)
+        n = g.n
+        if xi_act is None:
+            n_nd = int((np.diff(off) > 0).sum())
+            xi_act = eps / max(n_nd, 1)
+        x, r, pi = np.empty(n), np.empty(n), np.empty(n)
+        T = max_rounds + 2
+        tR = np.zeros(T) if trace else None
+        tF = np.zeros(T, np.int64) if trace else None
+        rounds = ctypes.c_int32()
+        st = self.L.orc_ifp_async(algo, n, _p(off), _p(dst), c, eps, xi_act, _p(p), max_rounds,
+                                  _p(x), _p(r), _p(pi), ctypes.byref(rounds), _p(tR), _p(tF))
+        k = rounds.value
+        out = dict(pi=pi, x=x, r=r, rounds=k, status=st, xi_act=xi_act)
+        if trace:
+            out.update(R=tR[:k + 1].copy(), F=tF[:k].copy())
+        return out
 
     def ifp2_levels(self, g, c, eps, p, levels, L, xi_act=None, max_rounds=100000, trace=True):
         """IFP2 in level-ordered rounds (orc_ifp2_levels).  levels[i] in [0, L]
@@ -245,6 +268,10 @@ def ifp_rounds(*a, **k):
 
 def ifp2_levels(*a, **k):
     return default().ifp2_levels(*a, **k)
+
+
+def ifp_async(*a, **k):
+    return default().ifp_async(*a, **k)
 
 
 def certified_l1_bound(algo: int, c: float, R: float) -> float:

@@ -24,6 +24,11 @@
  *   orc_ifp2_levels     IFP2 in level-ordered rounds: the in-round
  *                       propagation of Sec. 3.2's asynchronous scans, with
  *                       levels scanned in a fixed order.
+ *   orc_ifp_async       IFP1 / IFP2 rounds in which each vertex of the
+ *                       round's frontier pushes all the residual it holds
+ *                       when its turn comes (Sec. 3.2's threads), the
+ *                       frontier taken in id order: one schedule of the
+ *                       GPU's asynchronous rounds.
  *
  * Arrays: out_off[n+1] (int64), out_dst[m] (int32), vertex ids 0..n-1.
  * Every loop is the textbook one; nothing is blocked, fused or reordered.
@@ -177,6 +182,50 @@ static void build_in_lists(int32_t n, const int64_t *out_off, const int32_t *out
     *in_src_out = in_src;
 }
 
+/* R = sum of |r_i| over the non-dangling vertices: the quantity whose bound
+ * ends the rounds of Sec. 3.1 (dangling residuals are settled at the end). */
+static double nd_residual(int32_t n, const int64_t *out_off, const double *r) {
+    double R = 0.0;
+    for (int32_t i = 0; i < n; i++)
+        if (outdeg(out_off, i) > 0) R += fabs(r[i]);
+    return R;
+}
+
+/*
+ * The end of IFP1 / IFP2 rounds from reserves x and residuals r.  IFP2
+ * (Alg. 3) first runs phase 2 once: a dangling d, which never pushed, gets
+ * r_d = p_d + sum over in-neighbours u of c * x_u / ((1-c) deg(u)).  Then
+ * z_i = x_i + (1-c) r_i for IFP1 (Alg. 2: pibar + h, scaled by 1-c); for
+ * IFP2 z_i = x_i on non-dangling vertices and (1-c) r_d on dangling ones.
+ * pi = z / sum z.
+ */
+static void ifp_finalise(int algo, int32_t n, const int64_t *out_off, const int32_t *out_dst, double c,
+                         const double *p, const double *x, double *r, double *pi) {
+    double total = 0.0;
+    if (algo == ORC_IFP2) {
+        int64_t *in_off;
+        int32_t *in_src;
+        build_in_lists(n, out_off, out_dst, &in_off, &in_src);
+        for (int32_t d = 0; d < n; d++) {
+            if (outdeg(out_off, d) != 0) continue;
+            double s = p[d];
+            for (int64_t e = in_off[d]; e < in_off[d + 1]; e++) {
+                int32_t u = in_src[e];
+                s += c * x[u] / ((1.0 - c) * (double)outdeg(out_off, u));
+            }
+            r[d] = s;
+        }
+        free(in_off);
+        free(in_src);
+        for (int32_t i = 0; i < n; i++)
+            pi[i] = outdeg(out_off, i) > 0 ? x[i] : (1.0 - c) * r[i];
+    } else {
+        for (int32_t i = 0; i < n; i++) pi[i] = x[i] + (1.0 - c) * r[i];
+    }
+    for (int32_t i = 0; i < n; i++) total += pi[i];
+    for (int32_t i = 0; i < n; i++) pi[i] /= total;
+}
+
 /*
  * Alg. 2 (IFP1) and Alg. 3 (IFP2) with K = 1: one Calculation thread scans
  * the vertices in id order, again and again; a vertex v_i with h_i > xi
@@ -255,6 +304,57 @@ int orc_ifp_sequential(int algo, int32_t n, const int64_t *out_off, const int32_
     if (scans_out) *scans_out = scans;
     if (pushes_out) *pushes_out = pushes;
     if (edges_out) *edges_out = edges;
+    return status;
+}
+
+/*
+ * IFP1 / IFP2 with the asynchronous pushes of Sec. 3.2, in one schedule.  A
+ * round starts like a synchronous one: R = sum of |r| over non-dangling
+ * vertices, the stop and cap tests, and the frontier F = {non-dangling i :
+ * |r_i| > xi_act}.  Then the vertices of F are taken in increasing id, and
+ * each pushes the residual it holds at that moment (its value at the round's
+ * start plus what earlier vertices of this round pushed to it): (1-c) of it
+ * to its reserve, c/deg of it to every out-neighbour (IFP2: non-dangling
+ * ones only).  The rounds end in ifp_finalise.  Returns 0 when R <= eps, 1
+ * at the round cap, 2 when F is empty while R > eps.
+ */
+int orc_ifp_async(int algo, int32_t n, const int64_t *out_off, const int32_t *out_dst, double c,
+                  double eps, double xi_act, const double *p, int32_t max_rounds, double *x, double *r,
+                  double *pi, int32_t *rounds_out, double *trace_R, int64_t *trace_F) {
+    size_t N = (size_t)(n > 0 ? n : 1);
+    unsigned char *in_f = (unsigned char *)calloc(N, 1);
+    for (int32_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = p[i]; }
+    int32_t t = 0;
+    int status = 1;
+    for (;;) {
+        double R = nd_residual(n, out_off, r);
+        if (trace_R) trace_R[t] = R;
+        if (R <= eps) { status = 0; break; }
+        if (t >= max_rounds) { status = 1; break; }
+        int64_t nF = 0;
+        for (int32_t i = 0; i < n; i++) {
+            in_f[i] = outdeg(out_off, i) > 0 && fabs(r[i]) > xi_act;
+            if (in_f[i]) nF++;
+        }
+        if (nF == 0) { status = 2; break; }
+        for (int32_t i = 0; i < n; i++) {
+            if (!in_f[i]) continue;
+            double v = r[i]; /* everything i holds now */
+            r[i] -= v;       /* i hands all of it on: r_i becomes 0 */
+            x[i] += (1.0 - c) * v;
+            int64_t deg = outdeg(out_off, i);
+            for (int64_t e = out_off[i]; e < out_off[i + 1]; e++) {
+                int32_t j = out_dst[e];
+                if (algo == ORC_IFP2 && outdeg(out_off, j) == 0) continue; /* dangling target */
+                r[j] += c * v / (double)deg;
+            }
+        }
+        if (trace_F) trace_F[t] = nF;
+        t++;
+    }
+    if (rounds_out) *rounds_out = t;
+    ifp_finalise(algo, n, out_off, out_dst, c, p, x, r, pi);
+    free(in_f);
     return status;
 }
 
@@ -371,27 +471,7 @@ int orc_ifp2_levels(int32_t n, const int64_t *out_off, const int32_t *out_dst, d
     if (rounds_out) *rounds_out = rounds;
     if (r_pending)
         for (int32_t i = 0; i < n; i++) r_pending[i] = pend[i];
-    /* IFP2 phase 2 and finalisation (as in orc_ifp_rounds) */
-    int64_t *in_off;
-    int32_t *in_src;
-    build_in_lists(n, out_off, out_dst, &in_off, &in_src);
-    for (int32_t d = 0; d < n; d++) {
-        if (outdeg(out_off, d) != 0) continue;
-        double sd = p[d];
-        for (int64_t e = in_off[d]; e < in_off[d + 1]; e++) {
-            int32_t u = in_src[e];
-            sd += c * x[u] / ((1.0 - c) * (double)outdeg(out_off, u));
-        }
-        r[d] = sd;
-    }
-    free(in_off);
-    free(in_src);
-    double total = 0.0;
-    for (int32_t i = 0; i < n; i++) {
-        pi[i] = outdeg(out_off, i) > 0 ? x[i] : (1.0 - c) * r[i];
-        total += pi[i];
-    }
-    for (int32_t i = 0; i < n; i++) pi[i] /= total;
+    ifp_finalise(ORC_IFP2, n, out_off, out_dst, c, p, x, r, pi);
     free(pend);
     free(v);
     free(active);
@@ -438,9 +518,7 @@ int orc_ifp_rounds(int algo, int32_t n, const int64_t *out_off, const int32_t *o
     int32_t t = 0;
     int status = 1;
     for (;;) {
-        double R = 0.0;
-        for (int32_t i = 0; i < n; i++)
-            if (outdeg(out_off, i) > 0) R += fabs(r[i]);
+        double R = nd_residual(n, out_off, r);
         if (trace_R) trace_R[t] = R;
         if (R <= eps) { status = 0; break; }
         if (t >= max_rounds) { status = 1; break; }
@@ -474,29 +552,7 @@ int orc_ifp_rounds(int algo, int32_t n, const int64_t *out_off, const int32_t *o
         }
     }
     if (rounds_out) *rounds_out = t;
-    double total = 0.0;
-    if (algo == ORC_IFP2) {
-        int64_t *in_off;
-        int32_t *in_src;
-        build_in_lists(n, out_off, out_dst, &in_off, &in_src);
-        for (int32_t d = 0; d < n; d++) {
-            if (outdeg(out_off, d) != 0) continue;
-            double s = p[d];
-            for (int64_t e = in_off[d]; e < in_off[d + 1]; e++) {
-                int32_t u = in_src[e];
-                s += c * x[u] / ((1.0 - c) * (double)outdeg(out_off, u));
-            }
-            r[d] = s;
-        }
-        free(in_off);
-        free(in_src);
-        for (int32_t i = 0; i < n; i++)
-            pi[i] = outdeg(out_off, i) > 0 ? x[i] : (1.0 - c) * r[i];
-    } else {
-        for (int32_t i = 0; i < n; i++) pi[i] = x[i] + (1.0 - c) * r[i];
-    }
-    for (int32_t i = 0; i < n; i++) total += pi[i];
-    for (int32_t i = 0; i < n; i++) pi[i] /= total;
+    ifp_finalise(algo, n, out_off, out_dst, c, p, x, r, pi);
     free(v);
     free(active);
     return status;

@@ -1,10 +1,11 @@
 """Asynchronous push rounds (PR_MODE_ASYNC): each frontier vertex pushes all
 of its residual at the moment it is processed, as the threads of Sec. 3.2
-do, so the schedule decides how far mass travels within a round.  No oracle
-can replay that schedule; the tests check what holds for every schedule:
-the certified error bound against the exact PageRank, the stopping rule, a
-round count no larger than the synchronous one (mass only travels further
-within a round), exact results where the arithmetic is exact, and refusals."""
+do, so the schedule decides how far mass travels within a round.  The
+oracle runs one schedule (frontier in id order); the GPU's is another, so
+the tests check what holds for every schedule: the certified error bound
+against the exact PageRank, the stopping rule, round 0's frontier, a
+residual that falls at least as fast as in synchronous rounds, exact results
+where the arithmetic is exact, and refusals."""
 import numpy as np
 import pytest
 
@@ -92,6 +93,35 @@ def test_async_ppr(k):
     with pr.Graph(g.n, g.m, *g.csr32()) as G:
         out, st, s = G.solve(C, 1e-11, pr.PR_IFP2, pr.PR_DF64, p=val, p_idx=idx, opts=dict(mode=pr.PR_MODE_ASYNC))
         assert s == pr.PR_OK and l1(out, truth) <= st["err_bound"] + 1e-13
+
+
+@pytest.mark.parametrize("algo", (pr.PR_IFP1, pr.PR_IFP2))
+@pytest.mark.parametrize("prec", (pr.PR_FP64, pr.PR_DF64))
+def test_async_rounds_against_the_oracle_schedules(algo, prec):
+    """Every schedule takes round 0's frontier before any push, so its size and
+    its edges are those of the synchronous round.  With p >= 0 each frontier
+    vertex then pushes at least its round-start residual: R after round 1 is
+    at most the synchronous R, and R never rises.  The oracle's id-order
+    schedule obeys the same rules; both results sit within the certified
+    bound of each other's residual."""
+    g = gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=4)
+    p = gg.p_uniform(g.n)
+    eps = 1e-11
+    sync = oracle.ifp_rounds(algo, g, C, eps, p, xi_act=1e-300)
+    ido = oracle.ifp_async(algo, g, C, eps, p, xi_act=1e-300)
+    assert ido["status"] == 0 and ido["R"][1] <= sync["R"][1]
+    with pr.Graph(g.n, g.m, *g.csr32()) as G:
+        out, st, s = G.solve(C, eps, algo, prec, opts=dict(mode=pr.PR_MODE_ASYNC, xi_act=1e-300,
+                                                          trace_cap=sync["rounds"] + 5))
+        assert s == pr.PR_OK
+        k, tr = st["rounds"], st["trace"]
+        assert k <= sync["rounds"]
+        assert tr["F"][0] == sync["F"][0] and tr["E"][0] == sync["E"][0]
+        assert abs(tr["R"][0] - sync["R"][0]) <= 1e-14 * sync["R"][0]
+        assert tr["R"][1] <= sync["R"][1] * (1 + 1e-12)
+        assert np.all(np.diff(tr["R"][:k + 1]) <= 1e-15 * tr["R"][0])
+        bound = oracle.certified_l1_bound(algo, C, st["resid_l1"]) + oracle.certified_l1_bound(algo, C, ido["R"][-1])
+        assert l1(out, ido["pi"]) <= bound + 1e-13
 
 
 def test_async_refused_where_it_does_not_apply():

@@ -62,6 +62,18 @@ MUTANTS = {
     "levels_residual_without_pending": (
         "if (outdeg(out_off, i) > 0) R += fabs(r[i]) + fabs(pend[i]);",
         "if (outdeg(out_off, i) > 0) R += fabs(r[i]);"),
+    "async_reserve_unscaled": (
+        "x[i] += (1.0 - c) * v;",
+        "x[i] += v;"),
+    "async_residual_kept_after_push": (
+        "r[i] -= v;       /* i hands all of it on: r_i becomes 0 */",
+        "/* residual kept */"),
+    "async_frontier_includes_dangling": (
+        "in_f[i] = outdeg(out_off, i) > 0 && fabs(r[i]) > xi_act;",
+        "in_f[i] = fabs(r[i]) > xi_act;"),
+    "async_scans_in_reverse_id_order": (
+        "        for (int32_t i = 0; i < n; i++) {\n            if (!in_f[i]) continue;",
+        "        for (int32_t i = n - 1; i >= 0; i--) {\n            if (!in_f[i]) continue;"),
     "power_off_by_one_degree": (
         "next[out_dst[e]] += c * pi[i] / (double)deg;",
         "next[out_dst[e]] += c * pi[i] / (double)(deg + 1);"),

@@ -412,3 +412,132 @@ def test_levels_fewer_rounds_than_synchronous(orc):
     gs = orc.ifp2_levels(g, C, 1e-10, p, lv, 16)
     assert gs["rounds"] < 0.75 * sync["rounds"]
     assert l1(gs["pi"], sync["pi"]) < 2e-9
+
+
+# --------------------------------------- asynchronous rounds in id order
+def ordered_dag(n, avg_deg, seed, forward):
+    """random_small's edges re-pointed so that every edge runs to a higher id
+    (forward, self-loops dropped) or to a lower or equal id (self-loops kept)."""
+    g = gg.random_small(n, avg_deg=avg_deg, dangling=0.2, unref=0.1, seed=seed, loops=True)
+    src = np.repeat(np.arange(g.n), g.outdeg).astype(np.int32)
+    dst = g.out_dst.astype(np.int32)
+    lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+    if forward:
+        keep = lo != hi
+        return gg.from_edges(n, lo[keep], hi[keep])
+    return gg.from_edges(n, hi, lo)
+
+
+@pytest.mark.parametrize("n", [2, 3, 40])
+def test_async_chain_drains_in_one_round(orc, n):
+    """Path 0->...->n-1 taken in id order: each vertex passes on, in the same
+    round, all that its predecessor just gave it, so one round carries every
+    residual to the dangling end (synchronous rounds need n-1)."""
+    g = gg.chain(n)
+    y = (1 - C ** (np.arange(n) + 1)) / (n * (1 - C))
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_async(algo, g, C, 0.0, gg.p_uniform(n), xi_act=0.0)
+        assert o["status"] == 0 and o["rounds"] == 1 and o["R"][-1] == 0.0
+        assert l1(o["pi"], y / y.sum()) < 1e-14
+        assert orc.ifp_rounds(algo, g, C, 0.0, gg.p_uniform(n), xi_act=0.0)["rounds"] == n - 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_async_forward_dag_drains_in_one_round(orc, seed):
+    """Every edge runs to a higher id: when a vertex's turn comes, all its
+    in-neighbours have pushed, and nothing reaches it afterwards.  One round
+    leaves no residual on a non-dangling vertex, and the result is the exact
+    PageRank (eigenvector of the Google matrix)."""
+    g = ordered_dag(120, 4.0, seed, forward=True)
+    for p in (gg.p_uniform(g.n), gg.p_random(g.n, seed) / gg.p_random(g.n, seed).sum()):
+        truth = eig_pagerank(g, C, p)
+        for algo in (IFP1, IFP2):
+            o = orc.ifp_async(algo, g, C, 0.0, p, xi_act=0.0)
+            assert o["status"] == 0 and o["rounds"] == 1 and o["R"][-1] == 0.0
+            assert l1(o["pi"], truth) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_async_equals_synchronous_when_edges_point_down(orc, seed):
+    """Every edge runs to a lower or equal id: a vertex receives nothing
+    before its turn in a round, so the id-order schedule pushes exactly the
+    round-start values, in the same order, as the synchronous rounds."""
+    g = ordered_dag(150, 4.0, seed, forward=False)
+    p = gg.p_random(g.n, seed + 10, zero_frac=0.3)
+    p /= p.sum()
+    for algo in (IFP1, IFP2):
+        for cap in (1, 4, 100000):
+            a = orc.ifp_async(algo, g, C, 1e-12, p, max_rounds=cap)
+            s = orc.ifp_rounds(algo, g, C, 1e-12, p, max_rounds=cap)
+            assert a["status"] == s["status"] and a["rounds"] == s["rounds"]
+            for k in ("x", "r", "pi", "R", "F"):
+                assert np.array_equal(a[k], s[k]), (algo, cap, k)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_async_identity_and_mass_at_any_stop(orc, seed):
+    """A push moves (1-c)v to the reserve and cv along the out-edges, whatever
+    the schedule, so after any round: IFP1 keeps sum x + sum r = sum p and
+    r = p + c P s - s (s = x/(1-c)); IFP2 keeps that identity on the
+    non-dangling vertices with P~ (edges into dangling vertices dropped)."""
+    g = gg.random_small(200, avg_deg=5.0, dangling=0.2, unref=0.1, seed=seed, loops=True)
+    p = gg.p_uniform(g.n)
+    P = sparse_P(g)
+    nd = (g.outdeg > 0).astype(float)
+    Pt = sp.diags(nd) @ P
+    for cap in (1, 2, 5):
+        o = orc.ifp_async(IFP1, g, C, 1e-30, p, max_rounds=cap)
+        assert o["status"] == 1 and o["rounds"] == cap
+        assert abs(o["x"].sum() + o["r"].sum() - 1.0) < 1e-14
+        s = o["x"] / (1 - C)
+        assert l1(o["r"], p + C * (P @ s) - s) < 1e-13
+        o = orc.ifp_async(IFP2, g, C, 1e-30, p, max_rounds=cap)
+        s = o["x"] / (1 - C)
+        assert l1(o["r"] * nd, (p + C * (Pt @ s) - s) * nd) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("eps", [1e-5, 1e-11])
+def test_async_within_certified_bound(orc, seed, eps):
+    """The bound depends only on the final residual, not on how it was
+    reached: l1(pi, exact) <= 2cR/(1-c) (IFP1), 2R/(1-c) (IFP2)."""
+    g = gg.random_small(150, avg_deg=4.0, dangling=0.2, unref=0.1, seed=seed)
+    p = gg.p_random(g.n, seed, zero_frac=0.5)
+    p /= p.sum()
+    truth = eig_pagerank(g, C, p)
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_async(algo, g, C, eps, p)
+        assert o["status"] == 0 and o["R"][-1] <= eps
+        assert l1(o["pi"], truth) <= oracle.certified_l1_bound(algo, C, o["R"][-1]) + 1e-14
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_async_residual_falls_at_least_as_fast_in_a_round(orc, seed):
+    """With p >= 0 every residual stays >= 0, and a pushed amount of v lowers
+    R by at least (1-c)v; a vertex of the frontier pushes at least its
+    round-start value.  So R never rises, and after the first round it is no
+    larger than after a synchronous round from the same start."""
+    g = gg.random_small(200, avg_deg=5.0, dangling=0.2, unref=0.1, seed=seed)
+    p = gg.p_random(g.n, seed, zero_frac=0.3)
+    p /= p.sum()
+    for algo in (IFP1, IFP2):
+        a = orc.ifp_async(algo, g, C, 1e-12, p)
+        s = orc.ifp_rounds(algo, g, C, 1e-12, p)
+        assert np.all(np.diff(a["R"]) <= 0.0)
+        assert a["R"][1] <= s["R"][1]
+        assert np.all(a["r"] >= 0.0)
+
+
+def test_async_statuses_and_rounds_on_rmat(orc):
+    g = gg.rmat(11, 8, dangling=0.2, unref=0.1, seed=1)
+    p = gg.p_uniform(g.n)
+    for algo in (IFP1, IFP2):
+        a = orc.ifp_async(algo, g, C, 1e-10, p)
+        s = orc.ifp_rounds(algo, g, C, 1e-10, p)
+        assert a["status"] == 0 and a["rounds"] < s["rounds"]
+        assert l1(a["pi"], s["pi"]) <= oracle.certified_l1_bound(algo, C, 1e-10) * 2
+    assert orc.ifp_async(IFP1, g, C, 1e-12, p, max_rounds=3)["status"] == 1
+    o = orc.ifp_async(IFP1, g, C, 1e-12, p, xi_act=1.0)
+    assert o["status"] == 2 and o["rounds"] == 0
+    o = orc.ifp_async(IFP2, gg.empty(5), C, 1e-12, gg.p_uniform(5))
+    assert o["status"] == 0 and o["rounds"] == 0 and l1(o["pi"], gg.p_uniform(5)) < 1e-15
