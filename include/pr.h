@@ -210,8 +210,12 @@ pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
  * repeated edge is rejected (the adjacency matrix is 0/1, Sec. 2.1); self
  * loops are allowed.  mem_is_device: all four arrays are device pointers,
  * else host.  cuda_stream: the cudaStream_t to run on (NULL = legacy default).
- * The arrays are copied; the caller keeps ownership.  Errors: PR_EINVAL
- * (bad size, offsets, ids, duplicate edge, CSC mismatch), PR_ENOMEM, PR_ECUDA.
+ * The arrays are copied; the caller keeps ownership.  Host arrays are read
+ * only within out_off[0..n] and out_dst[0..m): out_off[0] = 0 and out_off[n]
+ * = m are checked first, then the O(n + m) checks run on host threads while
+ * the arrays are copied, and no kernel reads the copies before they pass.
+ * Errors: PR_EINVAL (bad size, offsets, ids, duplicate edge, CSC mismatch;
+ * reported ahead of any device error), PR_ENOMEM, PR_ECUDA.
  */
 pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                           const int32_t *in_off, const int32_t *in_src, int mem_is_device,

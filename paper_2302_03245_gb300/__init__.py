@@ -181,6 +181,16 @@ def _ptr(a) -> int | None:
     return a.data_ptr()
 
 
+def _on_device(a) -> bool:
+    """Whether an output array is device memory: True for a CUDA tensor, False
+    for a numpy array or a host torch tensor (pinned or not)."""
+    if isinstance(a, np.ndarray):
+        return False
+    if a.element_size() != 8 or not a.is_contiguous():
+        raise TypeError("output tensors must be contiguous float64")
+    return bool(a.is_cuda)
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         return None
@@ -310,8 +320,9 @@ def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_
              p_is_device: bool = False, opts: dict | None = None, check: bool = True):
     """Wraps pr_solve_ex.  Returns (out, stats dict, status).
 
-    out: None (a new host numpy array), a numpy float64 array, or a torch
-    float64 CUDA tensor (device output).  opts: pr_opts fields by name; with
+    out: None (a new host numpy array), a numpy float64 array, or a contiguous
+    float64 torch tensor: a CUDA tensor is device output, a CPU (e.g. pinned)
+    tensor host output.  opts: pr_opts fields by name; with
     trace_cap > 0 the per-round traces are returned in stats["trace"].
     """
     info = pr_graph_get_info(g)
@@ -319,7 +330,7 @@ def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_
     pv, keep = make_pvec(n, p, p_idx, p_is_device)
     if out is None:
         out = np.empty(n, dtype=np.float64)
-    out_dev = not isinstance(out, np.ndarray)
+    out_dev = _on_device(out)
     st = pr_stats()
     o = pr_opts()
     trace = None
@@ -354,7 +365,8 @@ def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_
 def pr_solve_batch(graphs, c, eps, algo, prec=PR_DF64, outs=None, opts: dict | None = None, check: bool = True):
     """Wraps pr_solve_batch.  graphs: list of handles (or Graph objects); c, eps:
     scalars or per-graph sequences; outs: None (new host arrays), a list of numpy
-    float64 arrays, or a list of torch float64 CUDA tensors.  Returns
+    float64 arrays, or a list of float64 torch tensors, all on the device or all
+    on the host.  Returns
     (outs, list of stats dicts, status)."""
     hs = [g.h if isinstance(g, Graph) else g for g in graphs]
     k = len(hs)
@@ -363,7 +375,9 @@ def pr_solve_batch(graphs, c, eps, algo, prec=PR_DF64, outs=None, opts: dict | N
     es = (ctypes.c_double * k)(*([float(eps)] * k if np.isscalar(eps) else [float(v) for v in eps]))
     if outs is None:
         outs = [np.empty(n, dtype=np.float64) for n in ns]
-    dev = not isinstance(outs[0], np.ndarray)
+    dev = _on_device(outs[0])
+    if any(_on_device(o) != dev for o in outs):
+        raise TypeError("outs must all be device arrays or all host arrays")
     optr = (ctypes.c_void_p * k)(*[_ptr(o) for o in outs])
     harr = (ctypes.c_void_p * k)(*[h.value for h in hs])
     sts = (pr_stats * k)()

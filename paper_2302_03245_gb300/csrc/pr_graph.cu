@@ -217,19 +217,52 @@ static __global__ void k_invert(int32_t n, const int32_t *perm, int32_t *inv) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) inv[perm[i]] = i;
 }
 
-// key = (inv[src] << B) | inv[dst]; the source row is found by binary search
-static __global__ void k_edge_keys(int32_t n, int64_t m, const int32_t *off, const int32_t *dst,
-                                   const int32_t *inv, int B, uint64_t *keys) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
-        int32_t lo = 0, hi = n;  // largest row with off[row] <= e
+// Edge keys in internal ids, packed as src << (B+1) | flag << B | dst, with
+// flag = (src >= n_ref): the source is unreferenced.  off/ent are caller
+// lists: row v holds the entries ent[off[v] .. off[v+1]), and row_is_src says
+// whether the row is the source end (out-lists) or the target end (in-lists).
+// A warp takes chunks of 32 * kEdgeChunk consecutive entries, lane l the
+// entries base + l + 32 j; a lane finds the row of its first entry by binary
+// search and then walks forward through the offsets, so the row lookup costs
+// about one cached offset read per entry (a binary search per entry cost
+// 0.8 ms on 47M edges).  With pos (the internal out-list offsets), entry e of
+// row v is written to pos[inv[v]] + (e - off[v]), which groups the keys by
+// internal source; without it, to index e.  The offsets are validated before
+// this runs: off[0] = 0, non-decreasing, off[n] = m.
+constexpr int kEdgeChunk = 16;
+static __global__ void k_edge_keys(int32_t n, int64_t m, const int32_t *off, const int32_t *ent,
+                                   const int32_t *inv, int B, int32_t n_ref, int row_is_src,
+                                   const int32_t *pos, uint64_t *keys) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t chunk = 32 * kEdgeChunk;
+    for (int64_t base = warp * chunk; base < m; base += nwarps * chunk) {
+        int64_t e = base + lane;
+        if (e >= m) break;
+        int32_t lo = 0, hi = n;  // the last row with off[row] <= e (off[n] = m > e)
         while (hi - lo > 1) {
-            int32_t mid = lo + ((hi - lo) >> 1);
+            const int32_t mid = lo + ((hi - lo) >> 1);
             if ((int64_t)off[mid] <= e) lo = mid;
             else hi = mid;
         }
-        keys[e] = ((uint64_t)inv[lo] << B) | (uint64_t)inv[dst[e]];
+        int32_t row = lo;
+        for (int j = 0; j < kEdgeChunk && e < m; j++, e += 32) {
+            while ((int64_t)off[row + 1] <= e) row++;
+            const uint64_t r = (uint64_t)inv[row], c = (uint64_t)inv[ent[e]];
+            const uint64_t src = row_is_src ? r : c, dst = row_is_src ? c : r;
+            const uint64_t key = (src << (B + 1)) | ((src >= (uint64_t)n_ref ? 1ULL : 0ULL) << B) | dst;
+            keys[pos ? (int64_t)pos[r] + (e - (int64_t)off[row]) : e] = key;
+        }
     }
+}
+
+// deg[i] = out-degree of internal vertex i (caller vertex perm[i]); deg[n] = 0.
+// Its exclusive sum is the internal out-list offsets.
+static __global__ void k_new_degrees(int32_t n, const int32_t *off, const int32_t *perm, int32_t *deg) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
+        deg[i] = i < n ? off[perm[i] + 1] - off[perm[i]] : 0;
 }
 
 static __global__ void k_count_dups(int64_t m, const uint64_t *keys, unsigned long long *cnt) {
@@ -240,49 +273,36 @@ static __global__ void k_count_dups(int64_t m, const uint64_t *keys, unsigned lo
     if (c) atomicAdd(cnt, c);
 }
 
-// low field of a sorted key array -> int32 column array; high field -> counted elsewhere
-static __global__ void k_low_field(int64_t m, const uint64_t *keys, int B, int32_t *col) {
-    const uint64_t mask = (1ULL << B) - 1;
+// a field of every key: col[e] = (keys[e] >> shift) & mask
+static __global__ void k_field(int64_t m, const uint64_t *keys, int shift, uint64_t mask, int32_t *col) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
-        col[e] = (int32_t)(keys[e] & mask);
+        col[e] = (int32_t)((keys[e] >> shift) & mask);
 }
 
-// off[r] = first e in [lo, hi) with keys[e] >= base + (r << B), minus lo; off[n] = hi - lo
-static __global__ void k_row_offsets(int32_t n, const uint64_t *keys, int64_t lo, int64_t hi,
-                                     uint64_t base, int B, int32_t *off) {
+// keys[lo, hi) ordered by the field f(k) = (k >> shift) & mask:
+// off[r] = (first e in [lo, hi) with f(keys[e]) >= base + r) - lo, r in [0, n]
+static __global__ void k_row_offsets(int32_t n, const uint64_t *keys, int64_t lo, int64_t hi, uint64_t base,
+                                     int shift, uint64_t mask, int32_t *off) {
     int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += stride) {
-        uint64_t target = base + ((uint64_t)r << B);
+        const uint64_t target = base + (uint64_t)r;
         int64_t a = lo, b = hi;
         while (a < b) {
             int64_t mid = a + ((b - a) >> 1);
-            if (keys[mid] < target) a = mid + 1;
+            if (((keys[mid] >> shift) & mask) < target) a = mid + 1;
             else b = mid;
         }
         off[r] = (int32_t)(a - lo);
     }
 }
 
-// CSR key (src << B | dst) -> CSC key (flag << 2B | dst << B | src), flag = src is unreferenced
-static __global__ void k_csc_keys(int64_t m, const uint64_t *csr, int B, int32_t n_ref,
-                                  uint64_t *csc) {
-    const uint64_t mask = (1ULL << B) - 1;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
-        uint64_t k = csr[e];
-        uint64_t s = k >> B, d = k & mask;
-        uint64_t flag = s >= (uint64_t)n_ref ? 1ULL : 0ULL;
-        csc[e] = (flag << (2 * B)) | (d << B) | s;
-    }
-}
-
-// first index with keys[e] >= target (single thread)
-static __global__ void k_lower_bound(const uint64_t *keys, int64_t m, uint64_t target, int64_t *out) {
+// first index e with (keys[e] & mask) >= target, keys ordered by that field (single thread)
+static __global__ void k_lower_bound(const uint64_t *keys, int64_t m, uint64_t mask, uint64_t target, int64_t *out) {
     int64_t a = 0, b = m;
     while (a < b) {
         int64_t mid = a + ((b - a) >> 1);
-        if (keys[mid] < target) a = mid + 1;
+        if ((keys[mid] & mask) < target) a = mid + 1;
         else b = mid;
     }
     *out = a;
@@ -373,13 +393,6 @@ static __global__ void k_range_edges(const int32_t *inr_off, const int32_t *inu_
 }
 
 // (hi << B | lo) -> (lo << B | hi)
-static __global__ void k_swap_halves(int64_t m, uint64_t *k, int B) {
-    const uint64_t mask = (1ULL << B) - 1;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
-        k[e] = ((k[e] & mask) << B) | (k[e] >> B);
-}
-
 static __global__ void k_count_diff(int64_t m, const uint64_t *a, const uint64_t *b,
                                     unsigned long long *cnt) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -807,37 +820,87 @@ extern "C" void pr_destroy(pr_graph *g) {
     delete g;
 }
 
-// The first index in [0, count) where bad(k) holds, or count: chunks scanned
-// by up to 16 host threads (a single-threaded scan of a 47M-entry edge array
-// took about 20 ms, most of a graph creation from host arrays).
+// The first index in [0, count) where bad(k) holds, or count.  Chunks are
+// scanned by up to 16 host threads; inside a chunk, blocks of 4096 indices are
+// OR-reduced without an early exit (a loop the compiler vectorises), and only
+// a block that holds a bad index is searched for the first one.  The
+// element-by-element loop with an early exit took about 3 ms on a 47M-entry
+// edge array with 16 threads; this one runs at memory speed.
 template <typename F> static int64_t first_bad(int64_t count, F bad) {
-    const int64_t kChunk = 1 << 20;
+    const int64_t kChunk = 1 << 20, kBlock = 4096;
     const int nt = (int)std::min<int64_t>({(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16,
                                            (count + kChunk - 1) / kChunk});
     auto scan = [&](int64_t lo, int64_t hi) {
-        for (int64_t k = lo; k < hi; k++)
-            if (bad(k)) return k;
+        for (int64_t b = lo; b < hi; b += kBlock) {
+            const int64_t e = std::min(hi, b + kBlock);
+            unsigned any = 0;
+            for (int64_t k = b; k < e; k++) any |= (unsigned)bad(k);
+            if (any)
+                for (int64_t k = b; k < e; k++)
+                    if (bad(k)) return k;
+        }
         return count;
     };
     if (nt <= 1) return scan(0, count);
     std::vector<int64_t> found(nt, count);
     std::vector<std::thread> th;
     const int64_t per = (count + nt - 1) / nt;
-    for (int t = 0; t < nt; t++)
-        th.emplace_back([&, t]() { found[t] = scan(std::min(count, t * per), std::min(count, (t + 1) * per)); });
+    for (int t = 0; t < nt; t++) {
+        auto part = [&, t]() { found[t] = scan(std::min(count, t * per), std::min(count, (t + 1) * per)); };
+        try {
+            th.emplace_back(part);
+        } catch (...) {  // no thread to be had: scan this part here
+            part();
+        }
+    }
     for (auto &x : th) x.join();
     return *std::min_element(found.begin(), found.end());
 }
 
-static pr_status validate_host(int32_t n, int64_t m, const int32_t *off, const int32_t *dst) {
-    if (off[0] != 0) return fail(PR_EINVAL, "out_off[0] must be 0");
+// The checks of one host CSR (or CSC) pair: "" when they hold, else the message.
+static std::string check_host_lists(int32_t n, int64_t m, const int32_t *off, const int32_t *dst) {
+    if (off[0] != 0) return "out_off[0] must be 0";
     const int64_t i = first_bad(n, [&](int64_t k) { return off[k + 1] < off[k]; });
-    if (i < n) return fail(PR_EINVAL, "out_off is not non-decreasing at row " + std::to_string(i));
-    if ((int64_t)off[n] != m) return fail(PR_EINVAL, "out_off[n] != m");
-    const int64_t e = first_bad(m, [&](int64_t k) { return dst[k] < 0 || dst[k] >= n; });
-    if (e < m) return fail(PR_EINVAL, "out_dst[" + std::to_string(e) + "] out of range");
-    return PR_OK;
+    if (i < n) return "out_off is not non-decreasing at row " + std::to_string(i);
+    if ((int64_t)off[n] != m) return "out_off[n] != m";
+    // one unsigned compare covers both ends: a negative id wraps above n
+    const int64_t e = first_bad(m, [&](int64_t k) { return (uint32_t)dst[k] >= (uint32_t)n; });
+    if (e < m) return "out_dst[" + std::to_string(e) + "] out of range";
+    return "";
 }
+
+// The checks of host arrays, run on a host thread of their own while the
+// arrays are copied to the device.  get() waits for them; it is called before
+// the first kernel that reads the copies, and again (a no-op then) when the
+// creation ends, so that a failed check is reported ahead of a device error.
+namespace {
+struct HostChecks {
+    std::thread th;
+    std::string msg;
+    bool joined = true;
+    void start(int32_t n, int64_t m, const int32_t *off, const int32_t *dst, const int32_t *ioff,
+               const int32_t *isrc) {
+        auto run = [=]() {
+            msg = check_host_lists(n, m, off, dst);
+            if (msg.empty() && ioff) msg = check_host_lists(n, m, ioff, isrc);
+        };
+        try {
+            th = std::thread(run);
+            joined = false;
+        } catch (...) {  // no thread to be had: check here and now
+            run();
+        }
+    }
+    const std::string &get() {
+        if (!joined) {
+            th.join();
+            joined = true;
+        }
+        return msg;
+    }
+    ~HostChecks() { get(); }
+};
+}  // namespace
 
 namespace {
 // CUB helper that takes temporary storage from the library allocator
@@ -849,21 +912,23 @@ struct Temp {
     }
 };
 
-pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int end_bit,
+// Stable LSD radix sort of keys on bits [begin_bit, end_bit): keys equal in
+// those bits keep their order.
+pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int begin_bit, int end_bit,
                     cudaStream_t s) {
     if (m <= 1) return PR_OK;
     cub::DoubleBuffer<uint64_t> db(keys, alt);
     size_t bytes = 0;
-    PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, db, (int)m, 0, end_bit, s));
+    PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, db, (int)m, begin_bit, end_bit, s));
     PR_TRY(tmp.need(bytes, s));
-    PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, db, (int)m, 0, end_bit, s));
+    PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, db, (int)m, begin_bit, end_bit, s));
     if (db.Current() != keys) std::swap(keys, alt);
     return PR_OK;
 }
 
 pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                       const int32_t *in_off, const int32_t *in_src, int mem_is_device,
-                      cudaStream_t s, int32_t levels, pr_graph *g) {
+                      cudaStream_t s, int32_t levels, HostChecks *checks, pr_graph *g) {
     int dev = 0;
     PR_CK(cudaGetDevice(&dev));
     int sms = 0;
@@ -899,6 +964,10 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     Buf scratch;
     PR_TRY(scratch.alloc(256, s));
     PR_CK(cudaMemsetAsync(scratch.p, 0, 256, s));
+    if (checks) {  // host arrays: their checks must pass before any kernel reads the copies
+        const std::string &e = checks->get();
+        if (!e.empty()) return fail(PR_EINVAL, e);
+    }
     unsigned long long *bad = scratch.as<unsigned long long>();         // [0],[1]
     unsigned long long *dups = bad + 2;                                 // [2]
     unsigned long long *m_d = bad + 3;                                  // [3]
@@ -971,41 +1040,36 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     for (int l = 0; l <= levels; l++)  // level l holds the ranks [ceil(l n_ref / L), ceil((l+1) n_ref / L))
         g->level_lo[l] = (int32_t)(((int64_t)l * n_ref + levels - 1) / levels);
 
-    // out-lists in internal ids
+    // Edges in internal ids.  The keys (k_edge_keys) pack src << (B+1) |
+    // flag << B | dst; the caller's rows are written to their internal rows,
+    // so the keys arrive grouped by src.  A stable sort on the low B+1 bits
+    // then orders them by (flag, dst, src): the in-lists, referenced sources
+    // first.  A second stable sort, on the src bits, orders them by (src, dst)
+    // (the flag is a function of src): the out-lists.  Each sort covers B+1 or
+    // B bits, where one sort of whole keys covers 2B.
+    const uint64_t low_mask = (1ULL << (B + 1)) - 1, id_mask = (1ULL << B) - 1;
+    PR_TRY(g->out_off.alloc(sizeof(int32_t) * (n + 1), s));
+    PR_TRY(g->out_dst.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    {
+        Buf deg;
+        PR_TRY(deg.alloc(sizeof(int32_t) * (n + 1), s));
+        k_new_degrees<<<gn, kThreads, 0, s>>>(n, d_off, g->perm.as<int32_t>(), deg.as<int32_t>());
+        size_t bytes = 0;
+        PR_CK(cub::DeviceScan::ExclusiveSum(nullptr, bytes, deg.as<int32_t>(), g->out_off.as<int32_t>(), n + 1, s));
+        PR_TRY(tmp.need(bytes, s));
+        PR_CK(cub::DeviceScan::ExclusiveSum(tmp.b.p, bytes, deg.as<int32_t>(), g->out_off.as<int32_t>(), n + 1, s));
+    }
     Buf ek, ek2;
     PR_TRY(ek.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
     PR_TRY(ek2.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
     uint64_t *keys = ek.as<uint64_t>(), *alt = ek2.as<uint64_t>();
-    if (m) k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, g->inv.as<int32_t>(), B, keys);
-    PR_TRY(sort_keys(tmp, keys, alt, m, 2 * B, s));
-    if (m > 1) k_count_dups<<<gm, kThreads, 0, s>>>(m, keys, dups);
-    PR_TRY(g->out_off.alloc(sizeof(int32_t) * (n + 1), s));
-    PR_TRY(g->out_dst.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
-    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m, 0, B, g->out_off.as<int32_t>());
-    if (m) k_low_field<<<gm, kThreads, 0, s>>>(m, keys, B, g->out_dst.as<int32_t>());
-    // optional caller in-lists: same edge set?
-    if (d_ioff) {
-        // transpose keys of the caller's CSC: (inv[src] << B | inv[dst]) sorted must equal `keys`
-        Buf ck;
-        PR_TRY(ck.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
-        uint64_t *ckeys = ck.as<uint64_t>();
-        // in-list row = dst; entry = src.  k_edge_keys builds (inv[row] << B | inv[entry]);
-        // swap the two halves to compare with the out-list keys.
-        if (m) k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, g->inv.as<int32_t>(), B, ckeys);
-        if (m) k_swap_halves<<<gm, kThreads, 0, s>>>(m, ckeys, B);
-        uint64_t *calt = alt;  // reuse the spare buffer
-        PR_TRY(sort_keys(tmp, ckeys, calt, m, 2 * B, s));
-        if (m) k_count_diff<<<gm, kThreads, 0, s>>>(m, keys, ckeys, bad + 1);
-        unsigned long long hb = 0;
-        PR_CK(cudaMemcpyAsync(&hb, bad + 1, sizeof(hb), cudaMemcpyDeviceToHost, s));
-        PR_CK(cudaStreamSynchronize(s));
-        if (hb) return fail(PR_EINVAL, "in_off/in_src do not describe the same edges as out_off/out_dst");
-    }
-    // in-lists: flag(src unreferenced) << 2B | dst << B | src, sorted
-    if (m) k_csc_keys<<<gm, kThreads, 0, s>>>(m, keys, B, n_ref, alt);
-    std::swap(keys, alt);
-    PR_TRY(sort_keys(tmp, keys, alt, m, 2 * B + 1, s));
-    k_lower_bound<<<1, 1, 0, s>>>(keys, m, 1ULL << (2 * B), lb);
+    if (m)
+        k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, g->inv.as<int32_t>(), B, n_ref, 1,
+                                            g->out_off.as<int32_t>(), keys);
+    // in-lists
+    PR_TRY(sort_keys(tmp, keys, alt, m, 0, B + 1, s));
+    if (m > 1) k_count_dups<<<gm, kThreads, 0, s>>>(m, keys, dups);  // a repeated edge is a repeated key
+    k_lower_bound<<<1, 1, 0, s>>>(keys, m, low_mask, 1ULL << B, lb);
     int64_t m_ref = 0;
     unsigned long long hdup = 0;
     PR_CK(cudaMemcpyAsync(&m_ref, lb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1017,10 +1081,30 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_TRY(g->inu_off.alloc(sizeof(int32_t) * (n + 1), s));
     PR_TRY(g->inr_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_ref, 1), s));
     PR_TRY(g->inu_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_unref, 1), s));
-    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m_ref, 0, B, g->inr_off.as<int32_t>());
-    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, m_ref, m, 1ULL << (2 * B), B, g->inu_off.as<int32_t>());
-    if (m_ref) k_low_field<<<gm, kThreads, 0, s>>>(m_ref, keys, B, g->inr_src.as<int32_t>());
-    if (m_unref) k_low_field<<<gm, kThreads, 0, s>>>(m_unref, keys + m_ref, B, g->inu_src.as<int32_t>());
+    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m_ref, 0, 0, low_mask, g->inr_off.as<int32_t>());
+    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, m_ref, m, 1ULL << B, 0, low_mask, g->inu_off.as<int32_t>());
+    if (m_ref) k_field<<<gm, kThreads, 0, s>>>(m_ref, keys, B + 1, id_mask, g->inr_src.as<int32_t>());
+    if (m_unref) k_field<<<gm, kThreads, 0, s>>>(m_unref, keys + m_ref, B + 1, id_mask, g->inu_src.as<int32_t>());
+    // out-lists (offsets from the scan above)
+    PR_TRY(sort_keys(tmp, keys, alt, m, B + 1, 2 * B + 1, s));
+    if (m) k_field<<<gm, kThreads, 0, s>>>(m, keys, 0, id_mask, g->out_dst.as<int32_t>());
+    // optional caller in-lists: the same edge set?  Their keys, sorted whole,
+    // must equal the out-list keys, which are now in ascending order.
+    if (d_ioff) {
+        Buf ck;
+        PR_TRY(ck.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+        uint64_t *ckeys = ck.as<uint64_t>();
+        if (m)
+            k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, g->inv.as<int32_t>(), B, n_ref, 0, nullptr,
+                                                ckeys);
+        uint64_t *calt = alt;  // the spare buffer of the sorts
+        PR_TRY(sort_keys(tmp, ckeys, calt, m, 0, 2 * B + 1, s));
+        if (m) k_count_diff<<<gm, kThreads, 0, s>>>(m, keys, ckeys, bad + 1);
+        unsigned long long hb = 0;
+        PR_CK(cudaMemcpyAsync(&hb, bad + 1, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        if (hb) return fail(PR_EINVAL, "in_off/in_src do not describe the same edges as out_off/out_dst");
+    }
     ek.release();
     ek2.release();
     tmp.b.release();
@@ -1124,17 +1208,26 @@ extern "C" pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out
     if (in_off && m > 0 && !in_src) return fail(PR_EINVAL, "in_off given without in_src");
     const int32_t levels = opts ? opts->levels : 0;
     if (levels < 0 || levels > kMaxLevels) return fail(PR_EINVAL, "levels must be in [0, 16]");
-    if (!mem_is_device) {  // host arrays are checked before any CUDA call
-        PR_TRY(validate_host(n, m, out_off, out_dst));
-        if (in_off) PR_TRY(validate_host(n, m, in_off, in_src));
+    HostChecks checks;  // host arrays: checked on a host thread while they are copied
+    if (!mem_is_device) {
+        // the two ends first, here: the copies read m entries, so off[n] = m must hold before they start
+        if (out_off[0] != 0 || (int64_t)out_off[n] != m) return fail(PR_EINVAL, "out_off must run from 0 to m");
+        if (in_off && (in_off[0] != 0 || (int64_t)in_off[n] != m))
+            return fail(PR_EINVAL, "in_off must run from 0 to m");
+        checks.start(n, m, out_off, out_dst, in_off, in_src);
     }
     pr_graph *G = new (std::nothrow) pr_graph();
-    if (!G) return fail(PR_ENOMEM, "host allocation failed");
+    if (!G) {
+        if (!checks.get().empty()) return fail(PR_EINVAL, checks.get());
+        return fail(PR_ENOMEM, "host allocation failed");
+    }
     static std::atomic<uint64_t> serial{0};
     G->uid = ++serial;
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
-                               (cudaStream_t)cuda_stream, levels, G);
+                               (cudaStream_t)cuda_stream, levels, mem_is_device ? nullptr : &checks, G);
     if (st != PR_OK) {
+        // a failed argument check outranks a device error met before it was read
+        if (!checks.get().empty()) st = fail(PR_EINVAL, checks.get());
         std::string msg = pr_last_error();
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
         cudaGetLastError();

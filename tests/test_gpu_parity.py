@@ -241,6 +241,41 @@ def test_device_arrays_and_device_output():
         assert status == pr.PR_OK and l1(out.cpu().numpy(), truth) <= 1e-9
 
 
+def test_output_placements_and_host_created_graphs():
+    """The same graph created from host arrays (checked on host threads while
+    they are copied) and from device arrays gives the same solve, bit for bit,
+    and every output placement receives it: a numpy array, a pinned CPU
+    tensor and an unpinned CPU tensor (host copies), and a CUDA tensor."""
+    g = gg.rmat(12, 8, dangling=0.15, unref=0.1, seed=9)
+    off, dst = g.csr32()
+    outs = []
+    with pr.Graph(g.n, g.m, off, dst) as H, \
+            pr.Graph(g.n, g.m, *[torch.tensor(a, device="cuda") for a in (off, dst)], mem_is_device=True,
+                     stream=torch.cuda.current_stream()) as D:
+        for G in (H, D):
+            for out in (np.empty(g.n), torch.empty(g.n, dtype=torch.float64).pin_memory(),
+                        torch.empty(g.n, dtype=torch.float64), torch.empty(g.n, dtype=torch.float64, device="cuda")):
+                res, st, status = G.solve(C, 1e-11, pr.PR_IFP2, pr.PR_DF64, out=out)
+                torch.cuda.synchronize()
+                assert status == pr.PR_OK and res is out
+                outs.append(out.cpu().numpy() if isinstance(out, torch.Tensor) else out)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    with pr.Graph(g.n, g.m, off, dst) as H:
+        with pytest.raises(TypeError):
+            H.solve(C, 1e-11, pr.PR_IFP2, out=torch.empty(g.n, dtype=torch.float32, device="cuda"))
+
+
+def test_invalid_host_sizes_rejected_before_any_copy():
+    """m that disagrees with out_off[n] is refused before the m entries are read."""
+    g = gg.random_small(50, 3.0, 0.2, 0.1, seed=1)
+    off, dst = g.csr32()
+    for m in (g.m + 1, g.m - 1):
+        with pytest.raises(pr.PrError) as e:
+            pr.pr_graph_create(g.n, m, off, dst)
+        assert e.value.status == pr.PR_EINVAL
+
+
 def test_graph_info_matches_table1_columns():
     g = gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=2)
     s = g.stats()
