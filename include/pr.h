@@ -212,8 +212,9 @@ pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
  * else host.  cuda_stream: the cudaStream_t to run on (NULL = legacy default).
  * The arrays are copied; the caller keeps ownership.  Host arrays are read
  * only within out_off[0..n] and out_dst[0..m): out_off[0] = 0 and out_off[n]
- * = m are checked first, then the O(n + m) checks run on host threads while
- * the arrays are copied, and no kernel reads the copies before they pass.
+ * = m are checked on the host before the copy, the rest of the checks run on
+ * the device on the copies before any kernel indexes by them, and if the
+ * device fails before that (no device, no memory) they run on the host.
  * Errors: PR_EINVAL (bad size, offsets, ids, duplicate edge, CSC mismatch;
  * reported ahead of any device error), PR_ENOMEM, PR_ECUDA.
  */

@@ -869,39 +869,6 @@ static std::string check_host_lists(int32_t n, int64_t m, const int32_t *off, co
     return "";
 }
 
-// The checks of host arrays, run on a host thread of their own while the
-// arrays are copied to the device.  get() waits for them; it is called before
-// the first kernel that reads the copies, and again (a no-op then) when the
-// creation ends, so that a failed check is reported ahead of a device error.
-namespace {
-struct HostChecks {
-    std::thread th;
-    std::string msg;
-    bool joined = true;
-    void start(int32_t n, int64_t m, const int32_t *off, const int32_t *dst, const int32_t *ioff,
-               const int32_t *isrc) {
-        auto run = [=]() {
-            msg = check_host_lists(n, m, off, dst);
-            if (msg.empty() && ioff) msg = check_host_lists(n, m, ioff, isrc);
-        };
-        try {
-            th = std::thread(run);
-            joined = false;
-        } catch (...) {  // no thread to be had: check here and now
-            run();
-        }
-    }
-    const std::string &get() {
-        if (!joined) {
-            th.join();
-            joined = true;
-        }
-        return msg;
-    }
-    ~HostChecks() { get(); }
-};
-}  // namespace
-
 namespace {
 // CUB helper that takes temporary storage from the library allocator
 struct Temp {
@@ -928,7 +895,7 @@ pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int b
 
 pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                       const int32_t *in_off, const int32_t *in_src, int mem_is_device,
-                      cudaStream_t s, int32_t levels, HostChecks *checks, pr_graph *g) {
+                      cudaStream_t s, int32_t levels, pr_graph *g) {
     int dev = 0;
     PR_CK(cudaGetDevice(&dev));
     int sms = 0;
@@ -964,10 +931,6 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     Buf scratch;
     PR_TRY(scratch.alloc(256, s));
     PR_CK(cudaMemsetAsync(scratch.p, 0, 256, s));
-    if (checks) {  // host arrays: their checks must pass before any kernel reads the copies
-        const std::string &e = checks->get();
-        if (!e.empty()) return fail(PR_EINVAL, e);
-    }
     unsigned long long *bad = scratch.as<unsigned long long>();         // [0],[1]
     unsigned long long *dups = bad + 2;                                 // [2]
     unsigned long long *m_d = bad + 3;                                  // [3]
@@ -977,7 +940,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     int64_t *lb = reinterpret_cast<int64_t *>(bad + 12);                // lower bounds
 
     const int gm = grid_for(std::max<int64_t>(m, n + 1), sms), gn = grid_for(n + 1, sms);
-    if (mem_is_device) {
+    {  // the caller's lists, on the device (host arrays: the copies), before any kernel indexes by them
         k_validate<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, bad);
         if (d_ioff) k_validate<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, bad);
         unsigned long long hb[2];
@@ -1208,26 +1171,26 @@ extern "C" pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out
     if (in_off && m > 0 && !in_src) return fail(PR_EINVAL, "in_off given without in_src");
     const int32_t levels = opts ? opts->levels : 0;
     if (levels < 0 || levels > kMaxLevels) return fail(PR_EINVAL, "levels must be in [0, 16]");
-    HostChecks checks;  // host arrays: checked on a host thread while they are copied
     if (!mem_is_device) {
-        // the two ends first, here: the copies read m entries, so off[n] = m must hold before they start
+        // the two ends first, on the host: the copies read m entries, so off[n] = m must hold before they start
         if (out_off[0] != 0 || (int64_t)out_off[n] != m) return fail(PR_EINVAL, "out_off must run from 0 to m");
         if (in_off && (in_off[0] != 0 || (int64_t)in_off[n] != m))
             return fail(PR_EINVAL, "in_off must run from 0 to m");
-        checks.start(n, m, out_off, out_dst, in_off, in_src);
     }
     pr_graph *G = new (std::nothrow) pr_graph();
-    if (!G) {
-        if (!checks.get().empty()) return fail(PR_EINVAL, checks.get());
-        return fail(PR_ENOMEM, "host allocation failed");
-    }
+    if (!G) return fail(PR_ENOMEM, "host allocation failed");
     static std::atomic<uint64_t> serial{0};
     G->uid = ++serial;
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
-                               (cudaStream_t)cuda_stream, levels, mem_is_device ? nullptr : &checks, G);
+                               (cudaStream_t)cuda_stream, levels, G);
+    if (st != PR_OK && st != PR_EINVAL && !mem_is_device) {
+        // the device failed before it could check the lists (no device, no memory): check
+        // host arrays here, so that invalid arguments are reported as such on any machine
+        std::string e = check_host_lists(n, m, out_off, out_dst);
+        if (e.empty() && in_off) e = check_host_lists(n, m, in_off, in_src);
+        if (!e.empty()) st = fail(PR_EINVAL, e);
+    }
     if (st != PR_OK) {
-        // a failed argument check outranks a device error met before it was read
-        if (!checks.get().empty()) st = fail(PR_EINVAL, checks.get());
         std::string msg = pr_last_error();
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
         cudaGetLastError();

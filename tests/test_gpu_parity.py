@@ -242,8 +242,8 @@ def test_device_arrays_and_device_output():
 
 
 def test_output_placements_and_host_created_graphs():
-    """The same graph created from host arrays (checked on host threads while
-    they are copied) and from device arrays gives the same solve, bit for bit,
+    """The same graph created from host arrays (copied, then checked on the
+    device) and from device arrays gives the same solve, bit for bit,
     and every output placement receives it: a numpy array, a pinned CPU
     tensor and an unpinned CPU tensor (host copies), and a CUDA tensor."""
     g = gg.rmat(12, 8, dangling=0.15, unref=0.1, seed=9)
