@@ -541,3 +541,19 @@ def test_async_statuses_and_rounds_on_rmat(orc):
     assert o["status"] == 2 and o["rounds"] == 0
     o = orc.ifp_async(IFP2, gg.empty(5), C, 1e-12, gg.p_uniform(5))
     assert o["status"] == 0 and o["rounds"] == 0 and l1(o["pi"], gg.p_uniform(5)) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ifp2_mass_with_phase2_at_any_stop(orc, seed):
+    """IFP2 defers the pushes into dangling vertices: each push of v keeps
+    (1-c)v, sends c v ndeg/deg to non-dangling targets, and leaves
+    c v (deg - ndeg)/deg for phase 2 (Alg. 3), which hands it to the dangling
+    targets in one step.  So once phase 2 has run, sum x + sum r = sum p at any
+    stopping point, whatever the schedule."""
+    g = gg.random_small(200, avg_deg=5.0, dangling=0.25, unref=0.1, seed=seed, loops=True)
+    p = gg.p_random(g.n, seed, zero_frac=0.2)
+    p /= p.sum()
+    for run in (orc.ifp_rounds, orc.ifp_async):
+        for cap in (1, 3, 100000):
+            o = run(IFP2, g, C, 1e-13, p, max_rounds=cap)
+            assert abs(o["x"].sum() + o["r"].sum() - 1.0) < 1e-14, (run.__name__, cap)
