@@ -194,9 +194,9 @@ typedef void (*pr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
 
 /*
- * Build the device form of G(V,E) (Sec. 2.1) and run the preprocessing of
- * Alg. 2 line 2 / Alg. 3 line 2 (Sec. 3.4: "invalidate edges between dangling
- * vertices and their source vertices"):
+ * Build the device form of G(V,E) (Sec. 2.1) and run the preprocessing that
+ * Alg. 2 and Alg. 3 start with (Sec. 3.4: in IFP2 the edges from a vertex
+ * into dangling vertices are marked invalid, so pushes skip them):
  *   out-degree, in-degree, dangling (deg(v) = 0) and unreferenced (no in-link)
  *   classes; vertices are renumbered internally so that every out-list is
  *   [non-dangling targets | dangling targets] and every in-list is

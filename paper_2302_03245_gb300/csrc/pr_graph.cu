@@ -1,5 +1,5 @@
 // pr_graph.cu -- error state, device allocator, and pr_graph_create: the
-// preprocessing of Alg. 2 line 2 / Alg. 3 line 2 (Sec. 3.4) on the GPU.
+// preprocessing that Alg. 2 and Alg. 3 start with (Sec. 3.4), on the GPU.
 //
 // From the caller's out-lists this builds, on the device:
 //   * out-degree / in-degree, the dangling (deg = 0) and unreferenced
