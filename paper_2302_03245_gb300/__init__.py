@@ -181,14 +181,22 @@ def _ptr(a) -> int | None:
     return a.data_ptr()
 
 
-def _on_device(a) -> bool:
+def _on_device(a, n: int | None = None) -> bool:
     """Whether an output array is device memory: True for a CUDA tensor, False
-    for a numpy array or a host torch tensor (pinned or not)."""
+    for a numpy array or a host torch tensor (pinned or not).  The library
+    writes n doubles there, so the array must be contiguous float64 with at
+    least n elements."""
     if isinstance(a, np.ndarray):
-        return False
-    if a.element_size() != 8 or not a.is_contiguous():
-        raise TypeError("output tensors must be contiguous float64")
-    return bool(a.is_cuda)
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("output arrays must be contiguous float64")
+        size, dev = a.size, False
+    else:
+        if a.element_size() != 8 or not a.is_floating_point() or not a.is_contiguous():
+            raise TypeError("output tensors must be contiguous float64")
+        size, dev = a.numel(), bool(a.is_cuda)
+    if n is not None and size < n:
+        raise ValueError(f"output holds {size} values; the graph has {n} vertices")
+    return dev
 
 
 def _stream_handle(stream) -> int | None:
@@ -330,7 +338,7 @@ def pr_solve(g, c: float, eps: float, algo: int, prec: int = PR_FP64, p=None, p_
     pv, keep = make_pvec(n, p, p_idx, p_is_device)
     if out is None:
         out = np.empty(n, dtype=np.float64)
-    out_dev = _on_device(out)
+    out_dev = _on_device(out, n)
     st = pr_stats()
     o = pr_opts()
     trace = None
@@ -375,8 +383,8 @@ def pr_solve_batch(graphs, c, eps, algo, prec=PR_DF64, outs=None, opts: dict | N
     es = (ctypes.c_double * k)(*([float(eps)] * k if np.isscalar(eps) else [float(v) for v in eps]))
     if outs is None:
         outs = [np.empty(n, dtype=np.float64) for n in ns]
-    dev = _on_device(outs[0])
-    if any(_on_device(o) != dev for o in outs):
+    dev = _on_device(outs[0], ns[0])
+    if any(_on_device(o, n) != dev for o, n in zip(outs, ns)):
         raise TypeError("outs must all be device arrays or all host arrays")
     optr = (ctypes.c_void_p * k)(*[_ptr(o) for o in outs])
     harr = (ctypes.c_void_p * k)(*[h.value for h in hs])
@@ -415,6 +423,7 @@ def pr_server_poll(server, ticket: int, n: int, out=None):
     (host or CUDA)."""
     if out is None:
         out = np.empty(n, dtype=np.float64)
+    _on_device(out, n)  # the result is copied in: float64, contiguous, n values
     st = pr_stats()
     status = lib().pr_server_poll(server, int(ticket), _ptr(out), ctypes.byref(st))
     if status == PR_EBUSY:

@@ -108,3 +108,26 @@ def test_allocator_arguments_checked(prlib):
     st = lib.pr_set_allocator(prlib._ALLOC_FN(lambda a, b, c: None), prlib._FREE_FN(), None)
     assert st == prlib.PR_EINVAL
     assert lib.pr_set_allocator(prlib._ALLOC_FN(), prlib._FREE_FN(), None) == prlib.PR_OK
+
+
+def test_output_arrays_checked_before_any_call(prlib):
+    """Solve, batch and poll write n doubles into the caller's output: the
+    binding refuses anything else before the library is called."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    on_device = prlib._on_device
+    assert on_device(np.empty(5), 5) is False
+    assert on_device(np.empty(8), 5) is False                      # longer is fine
+    assert on_device(torch.empty(5, dtype=torch.float64), 5) is False
+    with pytest.raises(TypeError):
+        on_device(np.empty(5, np.float32), 5)
+    with pytest.raises(TypeError):
+        on_device(np.empty(10)[::2], 5)                             # not contiguous
+    with pytest.raises(TypeError):
+        on_device(torch.empty(5, dtype=torch.int64), 5)             # 8 bytes, not floating point
+    with pytest.raises(TypeError):
+        on_device(torch.empty(10, dtype=torch.float64)[::2], 5)
+    with pytest.raises(ValueError):
+        on_device(np.empty(4), 5)
+    with pytest.raises(ValueError):
+        on_device(torch.empty(4, dtype=torch.float64), 5)
