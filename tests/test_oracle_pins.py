@@ -557,3 +557,23 @@ def test_ifp2_mass_with_phase2_at_any_stop(orc, seed):
         for cap in (1, 3, 100000):
             o = run(IFP2, g, C, 1e-13, p, max_rounds=cap)
             assert abs(o["x"].sum() + o["r"].sum() - 1.0) < 1e-14, (run.__name__, cap)
+
+
+@pytest.mark.parametrize("n", [2, 5, 30])
+def test_async_cycle_closed_form(orc, n):
+    """Directed cycle 0->1->...->n-1->0, uniform p, frontier in id order.  In
+    round 1 vertex k pushes everything it holds, (1 - c^(k+1))/(n(1-c)), so
+    only vertex 0 keeps a residual: c(1 - c^n)/(n(1-c)).  From then on the
+    frontier is the one vertex holding mass (the others received theirs after
+    the round started), so each round moves it one step: R_t = c^(t-1) R_1.
+    The result is still 1/n everywhere."""
+    g = gg.cycle(n)
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_async(algo, g, C, 1e-12, gg.p_uniform(n), xi_act=0.0)
+        R1 = C * (1 - C ** n) / (n * (1 - C))
+        t = np.arange(1, len(o["R"]))
+        assert o["R"][0] == pytest.approx(1.0, abs=1e-15)
+        assert np.allclose(o["R"][1:], R1 * C ** (t - 1), rtol=1e-12, atol=0)
+        assert list(o["F"]) == [n] + [1] * (o["rounds"] - 1)
+        assert o["rounds"] == 1 + int(math.ceil(math.log(1e-12 / R1) / math.log(C)))
+        assert l1(o["pi"], np.full(n, 1.0 / n)) < 1e-11
