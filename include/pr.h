@@ -55,17 +55,16 @@ typedef enum {
 } pr_algo;
 
 typedef enum {
-    PR_FP64 = 0, /* residual, reserve, sums and output in IEEE double; the values a
-                    gather reads per source (pending pushes, Power's pi/deg) are
-                    stored as double-float pairs (48-bit significand, 8 bytes).
-                    On GB300 the FP64 pipe runs at 1/64 of FP32: the reference
-                    form, slow */
-    PR_FP32 = 1, /* residual, reserve and pushed mass in float; sums of the
-                    residual L1 and dangling mass in double-float with a final
-                    FP64 sum; at the end a correction sweep recomputes the
-                    residual from the reserve in double-float arithmetic, and
-                    double-float rounds finish the solve (not in the paper; the
-                    identity used is that of Eq. 4) */
+    PR_FP64 = 0, /* IEEE double throughout, the paper's arithmetic (Sec. 4 computes
+                    in double): residual, reserve, the pushed mass a gather reads
+                    per source (pending pushes, Power's pi/deg), the gathered
+                    sums, the reductions and the output.  On GB300 the FP64 pipe
+                    runs at 1/64 of FP32 */
+    PR_FP32 = 1, /* residual, reserve and pushed mass in float; the residual-L1
+                    and dangling-mass sums in IEEE double; at the end a
+                    correction sweep recomputes the residual from the reserve in
+                    IEEE double (r = p + c P~ s - s, s = x/(1-c), from Eq. 4; not
+                    in the paper), and IEEE FP64 rounds finish the solve */
     PR_DF64 = 2  /* residual, reserve and pushed mass as double-float pairs
                     (hi + lo floats, 48-bit significand, FP32 instructions); push
                     rounds add into an FP64 inbox with double atomics, folded into
@@ -315,8 +314,8 @@ pr_status pr_solve_ex(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec
 
 /*
  * Allocation-free Power-method PageRank.  The paper has no counterpart: this
- * is the Power iteration of its Sec. 4 baseline, packaged for callers that
- * cannot allocate device memory -- a framework that owns the whole device
+ * is the library's Power iteration, packaged for callers that cannot
+ * allocate device memory -- a framework that owns the whole device
  * memory pool, code on a path where cudaMalloc/cudaFree could synchronise the
  * device, a plug-in that is only handed buffers.  It calls no cudaMalloc,
  * cudaFree or allocating library routine: its working vectors live in one
@@ -383,7 +382,7 @@ pr_status pr_solve_batch(pr_graph *const *gs, int32_t count, const double *c, co
  * pr_server_submit: queue one request on graph g (created on the server's
  *   device; it must stay alive until every ticket on it has been polled
  *   to completion).  c, eps as in pr_solve; prec is PR_DF64 or PR_FP32 (float
- *   rounds, correction sweep, double-float rounds: see pr_prec); p is a host pr_pvec
+ *   rounds, FP64 correction sweep, FP64 rounds: see pr_prec); p is a host pr_pvec
  *   (NULL = uniform; sparse seeds for personalized PageRank), copied.
  *   *ticket receives the request's id.  Thread-safe.  Errors: PR_EINVAL
  *   (arguments, p, a request larger than the whole budget), PR_EAGAIN
@@ -421,6 +420,10 @@ typedef struct {
     int64_t tile_launches;            /* tile-engine phase kernels launched */
     int32_t groups, active;           /* live column groups; requests admitted, not finished */
     double ms_admit, ms_rounds, ms_correct, ms_finish;
+    int64_t queued_sum;               /* requests waiting in the queue, summed over steps */
+    int64_t running_sum;              /* requests in their rounds (groups and tile engine), summed over steps */
+    double ms_tables;                 /* rebuilding and uploading tile tables (part of ms_rounds) */
+    double ms_step_max;               /* the longest step */
 } pr_server_stats;
 pr_status pr_server_get_stats(pr_server *s, pr_server_stats *st);
 

@@ -89,7 +89,8 @@ class pr_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("finished", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("group_launches", ctypes.c_int64), ("tile_launches", ctypes.c_int64), ("groups", ctypes.c_int32),
                 ("active", ctypes.c_int32), ("ms_admit", ctypes.c_double), ("ms_rounds", ctypes.c_double),
-                ("ms_correct", ctypes.c_double), ("ms_finish", ctypes.c_double)]
+                ("ms_correct", ctypes.c_double), ("ms_finish", ctypes.c_double), ("queued_sum", ctypes.c_int64),
+                ("running_sum", ctypes.c_int64), ("ms_tables", ctypes.c_double), ("ms_step_max", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -407,27 +408,42 @@ def pr_server_create(hbm_budget_bytes: int, stream=None) -> ctypes.c_void_p:
     return s
 
 
+# vertex count of each ticket's graph, recorded at submit: pr_server_poll writes that
+# many values, so the output is checked against it (not against a caller's number)
+_TICKET_N: dict = {}
+
+
 def pr_server_submit(server, g, c: float, eps: float, prec: int = PR_DF64, p=None, p_idx=None) -> int:
     """Wraps pr_server_submit; p/p_idx as in pr_solve (host only).  Returns the ticket."""
     n = pr_graph_get_info(g)["n"]
     pv, keep = make_pvec(n, p, p_idx, False)
     t = ctypes.c_int64()
     _check(lib().pr_server_submit(server, g, float(c), float(eps), int(prec), ctypes.byref(pv), ctypes.byref(t)))
+    _TICKET_N[(server.value, t.value)] = n
     return t.value
 
 
-def pr_server_poll(server, ticket: int, n: int, out=None):
+def pr_server_poll(server, ticket: int, n: int | None = None, out=None):
     """Wraps pr_server_poll.  Returns None while the request runs (PR_EBUSY), else
     (out, stats dict, status) with status PR_OK or PR_ENOTCONV; raises on errors.
+    The result has one value per vertex of the request's graph, recorded when the
+    ticket was submitted through this binding; n, if given, must equal it.
     out: None (a new host array), a float64 numpy array, or a float64 torch tensor
-    (host or CUDA)."""
+    (host or CUDA) of at least that many values."""
+    key = (server.value, int(ticket))
+    if key not in _TICKET_N:
+        raise ValueError(f"ticket {ticket} was not submitted to this server through this binding")
+    n_req = _TICKET_N[key]
+    if n is not None and int(n) != n_req:
+        raise ValueError(f"ticket {ticket} is a request on a graph of {n_req} vertices, not {n}")
     if out is None:
-        out = np.empty(n, dtype=np.float64)
-    _on_device(out, n)  # the result is copied in: float64, contiguous, n values
+        out = np.empty(n_req, dtype=np.float64)
+    _on_device(out, n_req)  # the result is copied in: float64, contiguous, n_req values
     st = pr_stats()
     status = lib().pr_server_poll(server, int(ticket), _ptr(out), ctypes.byref(st))
     if status == PR_EBUSY:
         return None
+    _TICKET_N.pop(key, None)
     if status not in (PR_OK, PR_ENOTCONV):
         _check(status)
     return out, st.as_dict(), status
@@ -441,6 +457,8 @@ def pr_server_get_stats(server) -> dict:
 
 def pr_server_destroy(server) -> None:
     if server is not None and server.value:
+        for key in [k for k in _TICKET_N if k[0] == server.value]:
+            del _TICKET_N[key]
         lib().pr_server_destroy(server)
         server.value = None
 
@@ -455,11 +473,11 @@ class Server:
     def submit(self, g, c, eps, prec=PR_DF64, p=None, p_idx=None) -> int:
         h = g.h if isinstance(g, Graph) else g
         t = pr_server_submit(self.h, h, c, eps, prec, p, p_idx)
-        self._n[t] = pr_graph_get_info(h)["n"]
+        self._n[t] = _TICKET_N[(self.h.value, t)]
         return t
 
     def poll(self, ticket, out=None):
-        r = pr_server_poll(self.h, ticket, self._n[ticket], out)
+        r = pr_server_poll(self.h, ticket, None, out)
         if r is not None:
             self._n.pop(ticket, None)
         return r

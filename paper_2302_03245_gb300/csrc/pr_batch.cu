@@ -43,7 +43,7 @@ struct BProb {
     int32_t v0, nv;              // vertex tiles
     int32_t d0, nd;              // dangling-row tiles
     PVals pv;
-    float2 *qc;                  // FP32 form: gather values x_u / ((1-c) deg u) of the correction
+    double *qc;                  // FP32 form: gather values x_u / ((1-c) deg u) of the correction
     void *q;                     // phase-2 gather values
     double *out;                 // normalised result (device)
 };
@@ -243,44 +243,43 @@ __global__ void k_batch_init(const BProb *probs, const Tile *vt, int nvt) {
     }
 }
 
-// FP32 reserve -> double-float state (exactly) with an empty push inbox, and the
-// gather values q_u = x_u / ((1-c) deg(u)) of the correction sweep; IFP2's
-// dangling residual is p (phase 1 never touches it), IFP1's comes from the sweep
+// FP32 reserve -> IEEE double state (exactly), and the gather values
+// q_u = x_u / ((1-c) deg(u)) of the correction sweep in double; IFP2's dangling
+// residual is p (phase 1 never touches it), IFP1's comes from the sweep
 template <bool IFP2>
-__global__ void k_batch_to_df(const BProb *probs, const BProb *probs_df, const Tile *vt, int nvt) {
+__global__ void k_batch_to_fp64(const BProb *probs, const BProb *probs64, const Tile *vt, int nvt) {
     for (int k = blockIdx.x; k < nvt; k += gridDim.x) {
         const Tile tl = vt[k];
         const BProb &P = probs[tl.prob];
-        const BProb &Q = probs_df[tl.prob];
+        const BProb &Q = probs64[tl.prob];
         const float *x32 = static_cast<const float *>(P.B.x);
-        float2 *x = static_cast<float2 *>(Q.B.x);
-        float2 *r = static_cast<float2 *>(Q.B.r);
+        double *x = static_cast<double *>(Q.B.x);
+        double *r = static_cast<double *>(Q.B.r);
         for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
-            const float2 xv = make_float2(x32[i], 0.f);
+            const double xv = (double)x32[i];
             x[i] = xv;
-            Q.B.din[i] = 0.0;
-            if (i < P.G.n_nd) Q.qc[i] = df_mul(xv, df_mul(P.G.inv_degdf[i], P.ctl->inv_om_df));
-            else if (IFP2) r[i] = P.ctl->p_dense ? df_from_d(P.pv.p64[i]) : P.ctl->pu_df;
+            if (i < P.G.n_nd) Q.qc[i] = xv * (P.G.inv_deg64[i] * P.ctl->inv_om);
+            else if (IFP2) r[i] = P.ctl->p_dense ? P.pv.p64[i] : P.ctl->pu;
         }
     }
 }
 
-// correction sweep r = p + c P~ s - s (double-float) over the round tiles, into
-// the double-float state
-__global__ void __launch_bounds__(kThreads) k_batch_correct(const BProb *probs_df, const Tile *tiles, int ntiles) {
-    using A = typename GT<float2>::A;
+// correction sweep r = p + c P~ s - s (IEEE double) over the round tiles, into
+// the FP64 state
+__global__ void __launch_bounds__(kThreads) k_batch_correct(const BProb *probs64, const Tile *tiles, int ntiles) {
+    using A = typename GT<double>::A;
     __shared__ A sha[32];
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const Tile tl = tiles[k];
-        const BProb &Q = probs_df[tl.prob];
-        SweepArgs<float2> a{};
+        const BProb &Q = probs64[tl.prob];
+        SweepArgs<double> a{};
         a.val = Q.qc;
-        a.r = static_cast<float2 *>(Q.B.r);
-        a.x = static_cast<const float2 *>(Q.B.x);
+        a.r = static_cast<double *>(Q.B.r);
+        a.x = static_cast<const double *>(Q.B.x);
         a.pv = Q.pv;
-        float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
         const Seg S{tl.lo, tl.hi, tl.lanes, 0, 1};
-        sweep_segment<float2, OP_CORRECT>(Q.G, S, 0, Q.ctl, a, s1, s2, s3, sha);
+        sweep_segment<double, OP_CORRECT>(Q.G, S, 0, Q.ctl, a, s1, s2, s3, sha);
     }
 }
 
@@ -524,7 +523,7 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     const int sms = gs[0]->num_sms;
     // tiles
     std::vector<Tile> rt, vt, dt;
-    std::vector<BProb> hp(count), hp_df;
+    std::vector<BProb> hp(count), hp64;
     for (int k = 0; k < count; k++) {
         pr_graph *g = gs[k];
         hp[k].t0 = (int32_t)rt.size();
@@ -548,19 +547,19 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     Arena A;
     const size_t off_ctl = A.take(sizeof(Ctl) * count);
     const size_t off_bc = A.take(sizeof(BCtl));
-    std::vector<StateOffsets> so(count), so_df(fp32 ? count : 0);
+    std::vector<StateOffsets> so(count), so64(fp32 ? count : 0);
     std::vector<size_t> off_out(count), off_qc(count);
     for (int k = 0; k < count; k++) {
         const size_t n = gs[k]->G.n, nnd = std::max(gs[k]->G.n_nd, 1);
         so[k] = take_state(A, n, nnd, tb, vb, prec == PR_DF64);
         if (fp32) {
-            so_df[k] = take_state(A, n, nnd, sizeof(float2), sizeof(float2), true);
-            off_qc[k] = A.take(sizeof(float2) * n);
+            so64[k] = take_state(A, n, nnd, sizeof(double), sizeof(double), false);
+            off_qc[k] = A.take(sizeof(double) * n);
         }
         off_out[k] = outs_are_device ? 0 : A.take(sizeof(double) * n);
     }
     const size_t off_probs = A.take(sizeof(BProb) * count);
-    const size_t off_probs_df = fp32 ? A.take(sizeof(BProb) * count) : 0;
+    const size_t off_probs64 = fp32 ? A.take(sizeof(BProb) * count) : 0;
     const size_t off_rt = A.take(sizeof(Tile) * rt.size());
     const size_t off_vt = A.take(sizeof(Tile) * vt.size());
     const size_t off_dt = A.take(sizeof(Tile) * std::max<size_t>(dt.size(), 1));
@@ -603,14 +602,14 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
         P.q = A.at<char>(so[k].q);
         P.out = outs_are_device ? outs[k] : A.at<double>(off_out[k]);
         if (fp32) {
-            P.qc = A.at<float2>(off_qc[k]);
+            P.qc = A.at<double>(off_qc[k]);
         }
     }
     if (fp32) {
-        hp_df = hp;
+        hp64 = hp;
         for (int k = 0; k < count; k++) {
-            hp_df[k].B = round_buf(A, so_df[k]);
-            hp_df[k].q = A.at<char>(so_df[k].q);
+            hp64[k].B = round_buf(A, so64[k]);
+            hp64[k].q = A.at<char>(so64[k].q);
         }
     }
     BCtl hbc{0, 0, count, 0};
@@ -618,9 +617,9 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     PR_CK(cudaMemcpyAsync(bc, &hbc, sizeof(BCtl), cudaMemcpyHostToDevice, s));
     const BProb *d_probs = A.at<BProb>(off_probs);
     PR_CK(cudaMemcpyAsync(A.at<BProb>(off_probs), hp.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, s));
-    const BProb *d_probs_df = fp32 ? A.at<BProb>(off_probs_df) : nullptr;
+    const BProb *d_probs64 = fp32 ? A.at<BProb>(off_probs64) : nullptr;
     if (fp32)
-        PR_CK(cudaMemcpyAsync(A.at<BProb>(off_probs_df), hp_df.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice,
+        PR_CK(cudaMemcpyAsync(A.at<BProb>(off_probs64), hp64.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice,
                               s));
     const Tile *d_rt = A.at<Tile>(off_rt), *d_vt = A.at<Tile>(off_vt), *d_dt = A.at<Tile>(off_dt);
     PR_CK(cudaMemcpyAsync(A.at<Tile>(off_rt), rt.data(), sizeof(Tile) * rt.size(), cudaMemcpyHostToDevice, s));
@@ -656,16 +655,16 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
         PR_CK(cudaMemcpyAsync(mid.data(), d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
         for (int k = 0; k < count; k++) r32_rounds[k] = mid[k].round;
-        if (ifp2) k_batch_to_df<true><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs_df, d_vt, nvt);
-        else k_batch_to_df<false><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs_df, d_vt, nvt);
-        k_batch_correct<<<(int)std::min<int64_t>(nrt, (int64_t)sms * 16), kThreads, 0, s>>>(d_probs_df, d_rt, nrt);
-        k_batch_reset<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_probs_df, count, bc);
-        PR_TRY(batch_rounds<float2>(ifp2, s, cap, d_probs_df, d_rt, nrt, bc, sl, grid));
+        if (ifp2) k_batch_to_fp64<true><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs64, d_vt, nvt);
+        else k_batch_to_fp64<false><<<sgrid, kThreads, 0, s>>>(d_probs, d_probs64, d_vt, nvt);
+        k_batch_correct<<<(int)std::min<int64_t>(nrt, (int64_t)sms * 16), kThreads, 0, s>>>(d_probs64, d_rt, nrt);
+        k_batch_reset<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_probs64, count, bc);
+        PR_TRY(batch_rounds<double>(ifp2, s, cap, d_probs64, d_rt, nrt, bc, sl, grid));
     }
     // phase 2 and normalisation in the final format
-    const BProb *d_fin = fp32 ? d_probs_df : d_probs;
+    const BProb *d_fin = fp32 ? d_probs64 : d_probs;
     const int dgrid = (int)std::min<int64_t>(std::max(ndt, 1), (int64_t)sms * 16);
-    if (prec == PR_FP64) {
+    if (prec == PR_FP64 || fp32) {
         if (ifp2 && ndt) {
             k_batch_phase2_q<double><<<sgrid, kThreads, 0, s>>>(d_fin, d_vt, nvt);
             k_batch_phase2<double><<<dgrid, kThreads, 0, s>>>(d_fin, d_dt, ndt);
@@ -814,11 +813,11 @@ struct SReq {
     std::vector<int32_t> idx;
     std::vector<double> val;
     double p_scale = 1.0;
-    int stage = 0;                  // 0 queued, 1 rounds, 2 double-float rounds after correction, 3 done
+    int stage = 0;                  // 0 queued, 1 rounds, 2 FP64 rounds after correction, 3 done
     pr_status status = PR_OK;
     size_t bytes = 0;
     void *mem = nullptr;            // one stream-ordered allocation
-    StateOffsets s_main{}, s_df{};
+    StateOffsets s_main{}, s64{};  // s64: FP32 requests after the FP64 correction
     size_t off_ctl = 0, off_out = 0, off_qc = 0, off_p64 = 0, off_sidx = 0, off_sval = 0;
     int32_t rounds_first = 0;
     void *group = nullptr;          // column group holding the request's rounds (nullptr: tile engine)
@@ -858,8 +857,8 @@ size_t layout(SReq &q) {
     q.off_ctl = take(sizeof(Ctl));
     q.s_main = state(tb, vb);
     if (fp32) {
-        q.s_df = state(sizeof(float2), sizeof(float2));
-        q.off_qc = take(sizeof(float2) * n);
+        q.s64 = state(sizeof(double), sizeof(double));
+        q.off_qc = take(sizeof(double) * n);
         q.off_p64 = take(sizeof(double) * n);
     }
     q.off_sidx = take(sizeof(int32_t) * std::max(q.nnz, 1));
@@ -903,6 +902,11 @@ struct ServerImpl {
     Buf d_gctl, d_gstat;
     cudaStream_t s = nullptr;
     cudaStream_t ps = nullptr;  // copies of results to callers (pr_server_poll)
+    // The server's own memory pool.  It keeps what it has reserved until the
+    // server is destroyed: with the device's default pool, memory freed by a
+    // finished request went back to the driver at the next synchronisation and
+    // every admission mapped it again, a cost that grew with the requests in flight.
+    cudaMemPool_t pool = nullptr;
     int device = 0, sms = 0;
     size_t budget = 0, used = 0;
     std::mutex mu;
@@ -913,7 +917,9 @@ struct ServerImpl {
     size_t queue_cap = 1 << 16;
     std::deque<SReq *> queue;
     std::unordered_map<int64_t, SReq *> reqs;
-    std::vector<SReq *> act[2];  // [0] rounds in the request's format, [1] double-float after correction
+    // [0] FP32 requests in their FP32 rounds, [1] double-float requests, [2] FP32
+    // requests in their FP64 rounds after the correction
+    std::vector<SReq *> act[3];
     // per-graph tile templates (prob index filled in when a table is built)
     struct Tiles {
         std::vector<Tile> round, vert, dang;
@@ -921,9 +927,9 @@ struct ServerImpl {
     };
     std::unordered_map<uint64_t, Tiles> tiles;  // by pr_graph::uid
     // device tables of the current step (grow-only)
-    Buf d_probs[2], d_tiles[2], d_bc[2], d_slots, d_stat, d_fprobs, d_ftiles, d_fdtiles, d_fvtiles;
-    int ntiles[2] = {0, 0};
-    bool dirty[2] = {true, true};
+    Buf d_probs[3], d_tiles[3], d_bc[3], d_slots, d_stat, d_fprobs, d_ftiles, d_fdtiles, d_fvtiles;
+    int ntiles[3] = {0, 0, 0};
+    bool dirty[3] = {true, true, true};
     pr_status loop_error = PR_OK;
     std::string loop_msg;
 
@@ -940,18 +946,18 @@ struct ServerImpl {
         return tiles.emplace(g->uid, std::move(T)).first->second;
     }
 
-    // table entry of a request: act[0] holds FP32 requests in their FP32 rounds, act[1]
-    // double-float rounds (DF64 requests from the start, FP32 requests after correction)
+    // table entry of a request in the state of act[fmt]: 0 the FP32 rounds, 1 a
+    // double-float request, 2 the FP64 rounds of an FP32 request after correction
     BProb prob_of(SReq *q, int fmt) {
         BProb P{};
         P.G = q->g->G;
         P.ctl = q->at<Ctl>(q->off_ctl);
-        const StateOffsets &o = (fmt == 1 && q->prec == PR_FP32) ? q->s_df : q->s_main;
+        const StateOffsets &o = fmt == 2 ? q->s64 : q->s_main;
         P.B = req_buf(*q, o);
         P.q = q->at<char>(o.q);
         P.out = q->dout;
         if (q->prec == PR_FP32) {
-            P.qc = q->at<float2>(q->off_qc);
+            P.qc = q->at<double>(q->off_qc);
             P.pv = PVals{q->at<double>(q->off_p64), nullptr, nullptr};
         }
         return P;
@@ -984,8 +990,8 @@ struct ServerImpl {
             hp.push_back(P);
         }
         const size_t pb = sizeof(BProb) * std::max<size_t>(hp.size(), 1), tb = sizeof(Tile) * std::max<size_t>(ht.size(), 1);
-        if (dp.bytes < pb) PR_TRY(dp.alloc_async(pb * 2, s));
-        if (dt.bytes < tb) PR_TRY(dt.alloc_async(tb * 2, s));
+        if (dp.bytes < pb) PR_TRY(dp.alloc_async(pb * 2, s, pool));
+        if (dt.bytes < tb) PR_TRY(dt.alloc_async(tb * 2, s, pool));
         if (!hp.empty()) PR_CK(cudaMemcpyAsync(dp.p, hp.data(), sizeof(BProb) * hp.size(), cudaMemcpyHostToDevice, s));
         if (!ht.empty()) PR_CK(cudaMemcpyAsync(dt.p, ht.data(), sizeof(Tile) * ht.size(), cudaMemcpyHostToDevice, s));
         return PR_OK;
@@ -994,8 +1000,8 @@ struct ServerImpl {
     pr_status admit_one(SReq *q) {
         q->bytes = layout(*q);
         q->out_bytes = sizeof(double) * (size_t)q->g->G.n;
-        PR_CK(cudaMallocAsync(&q->mem, q->bytes, s));
-        PR_CK(cudaMallocAsync(reinterpret_cast<void **>(&q->dout), q->out_bytes, s));
+        PR_CK(cudaMallocFromPoolAsync(&q->mem, q->bytes, pool, s));
+        PR_CK(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&q->dout), q->out_bytes, pool, s));
         const DevGraph &G = q->g->G;
         Ctl h{};
         h.c = q->c;
@@ -1015,7 +1021,7 @@ struct ServerImpl {
         h.unref_active = 1;
         fill_formats(h);
         PR_CK(cudaMemcpyAsync(q->at<Ctl>(q->off_ctl), &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        for (const StateOffsets *o : {&q->s_main, &q->s_df})  // double-float inboxes start empty
+        for (const StateOffsets *o : {&q->s_main, &q->s64})  // double-float inboxes start empty
             if (o->din) PR_CK(cudaMemsetAsync(q->at<char>(o->din), 0, sizeof(double) * G.n, s));
         double *p64 = q->prec == PR_FP32 ? q->at<double>(q->off_p64) : nullptr;
         const int grid = (int)std::min<int64_t>((G.n + kThreads - 1) / kThreads, (int64_t)sms * 8);
@@ -1041,7 +1047,7 @@ struct ServerImpl {
         return PR_OK;
     }
 
-    // FP32 requests that stopped: FP64 correction, then double-float rounds
+    // FP32 requests that stopped: the IEEE FP64 correction, then FP64 rounds
     pr_status correct(const std::vector<SReq *> &set) {
         std::vector<BProb> hp;
         std::vector<Tile> hv, hr;
@@ -1055,22 +1061,22 @@ struct ServerImpl {
             hp[k].nt = hp2[k].nt;
         }
         PR_CK(cudaMemcpyAsync(d_fprobs.p, hp.data(), sizeof(BProb) * hp.size(), cudaMemcpyHostToDevice, s));
-        std::vector<BProb> hdf = hp;
+        std::vector<BProb> h64 = hp;
         for (size_t k = 0; k < set.size(); k++) {
-            hdf[k].B = req_buf(*set[k], set[k]->s_df);
-            hdf[k].q = set[k]->at<char>(set[k]->s_df.q);
+            h64[k].B = req_buf(*set[k], set[k]->s64);
+            h64[k].q = set[k]->at<char>(set[k]->s64.q);
         }
         Buf dfp;
-        PR_TRY(dfp.alloc_async(sizeof(BProb) * hdf.size(), s));
-        PR_CK(cudaMemcpyAsync(dfp.p, hdf.data(), sizeof(BProb) * hdf.size(), cudaMemcpyHostToDevice, s));
+        PR_TRY(dfp.alloc_async(sizeof(BProb) * h64.size(), s, pool));
+        PR_CK(cudaMemcpyAsync(dfp.p, h64.data(), sizeof(BProb) * h64.size(), cudaMemcpyHostToDevice, s));
         const int nv = (int)hv.size(), nr = (int)hr.size();
         const int g1 = (int)std::min<int64_t>(std::max(nv, 1), (int64_t)sms * 16);
         const int g2 = (int)std::min<int64_t>(std::max(nr, 1), (int64_t)sms * 16);
         const BProb *dp = d_fprobs.as<BProb>();
-        k_batch_to_df<true><<<g1, kThreads, 0, s>>>(dp, dfp.as<BProb>(), d_fvtiles.as<Tile>(), nv);
+        k_batch_to_fp64<true><<<g1, kThreads, 0, s>>>(dp, dfp.as<BProb>(), d_fvtiles.as<Tile>(), nv);
         k_batch_correct<<<g2, kThreads, 0, s>>>(dfp.as<BProb>(), d_ftiles.as<Tile>(), nr);
         Buf bcb;
-        PR_TRY(bcb.alloc_async(sizeof(BCtl), s));
+        PR_TRY(bcb.alloc_async(sizeof(BCtl), s, pool));
         k_batch_reset<<<((int)set.size() + kThreads - 1) / kThreads, kThreads, 0, s>>>(dfp.as<BProb>(), (int)set.size(),
                                                                                      bcb.as<BCtl>());
         PR_CK(cudaStreamSynchronize(s));
@@ -1078,13 +1084,24 @@ struct ServerImpl {
         return PR_OK;
     }
 
-    // stopped requests: phase 2, normalisation, copy out, release
+    // stopped requests: phase 2, normalisation, release; per state format
+    // (1 double-float, 2 FP64 after the correction of an FP32 request)
     pr_status finish(const std::vector<SReq *> &set, const std::vector<int> &fmt) {
+        for (int f = 1; f <= 2; f++) {
+            std::vector<SReq *> part;
+            for (size_t k = 0; k < set.size(); k++)
+                if (fmt[k] == f) part.push_back(set[k]);
+            if (!part.empty()) PR_TRY(finish_fmt(part, f));
+        }
+        return PR_OK;
+    }
+
+    pr_status finish_fmt(const std::vector<SReq *> &set, int fmt) {
         std::vector<BProb> hp;
         std::vector<Tile> hv, hd;
         // per-request format: build the table by hand
         for (size_t k = 0; k < set.size(); k++) {
-            BProb P = prob_of(set[k], fmt[k]);
+            BProb P = prob_of(set[k], fmt);
             const Tiles &T = tiles_of(set[k]->g);
             P.v0 = (int)hv.size();
             for (Tile t : T.vert) {
@@ -1100,24 +1117,30 @@ struct ServerImpl {
             P.nd = (int)T.dang.size();
             hp.push_back(P);
         }
-        if (d_fprobs.bytes < sizeof(BProb) * hp.size()) PR_TRY(d_fprobs.alloc_async(sizeof(BProb) * hp.size() * 2, s));
+        if (d_fprobs.bytes < sizeof(BProb) * hp.size()) PR_TRY(d_fprobs.alloc_async(sizeof(BProb) * hp.size() * 2, s, pool));
         if (d_fvtiles.bytes < sizeof(Tile) * std::max<size_t>(hv.size(), 1))
-            PR_TRY(d_fvtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hv.size(), 1) * 2, s));
+            PR_TRY(d_fvtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hv.size(), 1) * 2, s, pool));
         if (d_fdtiles.bytes < sizeof(Tile) * std::max<size_t>(hd.size(), 1))
-            PR_TRY(d_fdtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hd.size(), 1) * 2, s));
+            PR_TRY(d_fdtiles.alloc_async(sizeof(Tile) * std::max<size_t>(hd.size(), 1) * 2, s, pool));
         PR_CK(cudaMemcpyAsync(d_fprobs.p, hp.data(), sizeof(BProb) * hp.size(), cudaMemcpyHostToDevice, s));
         PR_CK(cudaMemcpyAsync(d_fvtiles.p, hv.data(), sizeof(Tile) * hv.size(), cudaMemcpyHostToDevice, s));
         if (!hd.empty()) PR_CK(cudaMemcpyAsync(d_fdtiles.p, hd.data(), sizeof(Tile) * hd.size(), cudaMemcpyHostToDevice, s));
         const int nv = (int)hv.size(), nd = (int)hd.size();
-        if (d_slots.bytes < sizeof(double) * std::max(nv, 1)) PR_TRY(d_slots.alloc_async(sizeof(double) * std::max(nv, 1) * 2, s));
+        if (d_slots.bytes < sizeof(double) * std::max(nv, 1)) PR_TRY(d_slots.alloc_async(sizeof(double) * std::max(nv, 1) * 2, s, pool));
         const int g1 = (int)std::min<int64_t>(std::max(nv, 1), (int64_t)sms * 16);
         const int g2 = (int)std::min<int64_t>(std::max(nd, 1), (int64_t)sms * 16);
         const BProb *dp = d_fprobs.as<BProb>();
-        // every request finishes in double-float state (FP32 requests were corrected into it)
-        k_batch_phase2_q<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv);
-        if (nd) k_batch_phase2<float2><<<g2, kThreads, 0, s>>>(dp, d_fdtiles.as<Tile>(), nd);
-        k_batch_fin_sum<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2, d_slots.as<double>());
-        k_batch_fin_write<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2);
+        if (fmt == 2) {
+            k_batch_phase2_q<double><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv);
+            if (nd) k_batch_phase2<double><<<g2, kThreads, 0, s>>>(dp, d_fdtiles.as<Tile>(), nd);
+            k_batch_fin_sum<double><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2, d_slots.as<double>());
+            k_batch_fin_write<double><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2);
+        } else {
+            k_batch_phase2_q<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv);
+            if (nd) k_batch_phase2<float2><<<g2, kThreads, 0, s>>>(dp, d_fdtiles.as<Tile>(), nd);
+            k_batch_fin_sum<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2, d_slots.as<double>());
+            k_batch_fin_write<float2><<<g1, kThreads, 0, s>>>(dp, d_fvtiles.as<Tile>(), nv, PR_IFP2);
+        }
         std::vector<Ctl> hc(set.size());
         for (size_t k = 0; k < set.size(); k++)  // results stay on the device until polled
             PR_CK(cudaMemcpyAsync(&hc[k], set[k]->at<Ctl>(set[k]->off_ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -1147,7 +1170,7 @@ struct ServerImpl {
     }
 
     bool any_active() const {
-        if (!act[0].empty() || !act[1].empty()) return true;
+        if (!act[0].empty() || !act[1].empty() || !act[2].empty()) return true;
         for (const Group *G : groups)
             if (G->live()) return true;
         return false;
@@ -1184,7 +1207,7 @@ struct ServerImpl {
             }
             G = new (std::nothrow) Group();
             void *mem = nullptr;
-            if (!G || cudaMallocAsync(&mem, gb, s) != cudaSuccess) {
+            if (!G || cudaMallocFromPoolAsync(&mem, gb, pool, s) != cudaSuccess) {
                 cudaGetLastError();
                 delete G;
                 std::lock_guard<std::mutex> lock(mu);
@@ -1255,8 +1278,8 @@ struct ServerImpl {
         }
         if (cols.empty()) return PR_OK;
         const int cnt = (int)cols.size();
-        if (d_gctl.bytes < sizeof(Ctl *) * cnt) PR_TRY(d_gctl.alloc_async(sizeof(Ctl *) * cnt * 2, s));
-        if (d_gstat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_gstat.alloc_async(sizeof(ReqStat) * cnt * 2, s));
+        if (d_gctl.bytes < sizeof(Ctl *) * cnt) PR_TRY(d_gctl.alloc_async(sizeof(Ctl *) * cnt * 2, s, pool));
+        if (d_gstat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_gstat.alloc_async(sizeof(ReqStat) * cnt * 2, s, pool));
         PR_CK(cudaMemcpyAsync(d_gctl.p, ptrs.data(), sizeof(Ctl *) * cnt, cudaMemcpyHostToDevice, s));
         k_gather_ctls<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_gctl.as<Ctl *>(), cnt,
                                                                            d_gstat.as<ReqStat>());
@@ -1298,9 +1321,9 @@ struct ServerImpl {
             add_ms(&pr_server_stats::ms_correct, t0);
             for (SReq *q : to_correct) {
                 q->stage = 2;
-                act[1].push_back(q);
+                act[2].push_back(q);
             }
-            dirty[1] = true;
+            dirty[2] = true;
         }
         if (!to_finish.empty()) {
             const auto t0 = Clock::now();
@@ -1327,10 +1350,20 @@ struct ServerImpl {
     }
 
     pr_status step_once() {
+        const auto t_step = Clock::now();
+        const pr_status st = step_body();
+        const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t_step).count();
+        std::lock_guard<std::mutex> lock(mu);
+        stats.ms_step_max = std::max(stats.ms_step_max, ms);
+        return st;
+    }
+
+    pr_status step_body() {
         // admit
         std::vector<SReq *> adm;
         {
             std::lock_guard<std::mutex> lock(mu);
+            stats.queued_sum += (int64_t)queue.size();
             while (!queue.empty()) {
                 SReq *q = queue.front();
                 const size_t need = layout(*q) + sizeof(double) * (size_t)q->g->G.n;
@@ -1351,24 +1384,29 @@ struct ServerImpl {
         }
         if (!adm.empty()) add_ms(&pr_server_stats::ms_admit, t_adm);
         {
+            int64_t running = (int64_t)(act[0].size() + act[1].size() + act[2].size());
+            for (const Group *G : groups) running += G->live();
             std::lock_guard<std::mutex> lock(mu);
             stats.steps++;
+            stats.running_sum += running;
         }
         // a few rounds of every request, per state format (groups first)
         constexpr int kPhases = 4;
         PR_TRY(step_groups(kPhases));
-        if (act[0].empty() && act[1].empty()) return PR_OK;
+        if (act[0].empty() && act[1].empty() && act[2].empty()) return PR_OK;
         std::vector<BProb> hp;
         std::vector<Tile> ht;
-        for (int f = 0; f < 2; f++) {
+        for (int f = 0; f < 3; f++) {
             if (act[f].empty()) continue;
             if (dirty[f]) {
+                const auto t_tab = Clock::now();
                 PR_TRY(upload(act[f], f, 0, d_probs[f], d_tiles[f], hp, ht));
+                add_ms(&pr_server_stats::ms_tables, t_tab);
                 ntiles[f] = (int)ht.size();
-                if (!d_bc[f].p) PR_TRY(d_bc[f].alloc_async(sizeof(BCtl), s));
+                if (!d_bc[f].p) PR_TRY(d_bc[f].alloc_async(sizeof(BCtl), s, pool));
                 PR_CK(cudaMemsetAsync(d_bc[f].p, 0, sizeof(BCtl), s));
                 const size_t sb = (sizeof(double) * 2 + sizeof(long long) * 2) * std::max(ntiles[f], 1);
-                if (d_slots.bytes < sb) PR_TRY(d_slots.alloc_async(sb * 2, s));
+                if (d_slots.bytes < sb) PR_TRY(d_slots.alloc_async(sb * 2, s, pool));
                 dirty[f] = false;
             }
             const int nt = ntiles[f];
@@ -1385,13 +1423,16 @@ struct ServerImpl {
                 if (f == 0)
                     k_batch_phase<float, true><<<grid, kThreads, 0, s>>>(d_probs[f].as<BProb>(), d_tiles[f].as<Tile>(),
                                                                          nt, d_bc[f].as<BCtl>(), sl);
-                else
+                else if (f == 1)
                     k_batch_phase<float2, true><<<grid, kThreads, 0, s>>>(d_probs[f].as<BProb>(), d_tiles[f].as<Tile>(),
+                                                                          nt, d_bc[f].as<BCtl>(), sl);
+                else
+                    k_batch_phase<double, true><<<grid, kThreads, 0, s>>>(d_probs[f].as<BProb>(), d_tiles[f].as<Tile>(),
                                                                           nt, d_bc[f].as<BCtl>(), sl);
             }
             // which requests stopped
             const int cnt = (int)act[f].size();
-            if (d_stat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_stat.alloc_async(sizeof(ReqStat) * cnt * 2, s));
+            if (d_stat.bytes < sizeof(ReqStat) * cnt) PR_TRY(d_stat.alloc_async(sizeof(ReqStat) * cnt * 2, s, pool));
             k_gather_status<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_probs[f].as<BProb>(), cnt,
                                                                                  d_stat.as<ReqStat>());
             std::vector<ReqStat> hs(cnt);
@@ -1423,9 +1464,9 @@ struct ServerImpl {
                 add_ms(&pr_server_stats::ms_correct, t0);
                 for (SReq *q : to_correct) {
                     q->stage = 2;
-                    act[1].push_back(q);
+                    act[2].push_back(q);
                 }
-                dirty[1] = true;
+                dirty[2] = true;
             }
             if (!to_finish.empty()) {
                 const auto t0 = Clock::now();
@@ -1454,7 +1495,7 @@ struct ServerImpl {
                 loop_msg = pr_last_error();
                 // fail every pending request; the server stays usable for polling
                 std::vector<SReq *> failed;
-                for (int f = 0; f < 2; f++) {
+                for (int f = 0; f < 3; f++) {
                     for (SReq *q : act[f]) failed.push_back(q);
                     act[f].clear();
                     dirty[f] = true;
@@ -1513,6 +1554,21 @@ extern "C" pr_status pr_server_create(size_t hbm_budget_bytes, void *cuda_stream
     if (e != cudaSuccess) {
         delete S;
         return cuda_fail(e, "pr_server_create (copy stream)");
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = I.device;
+    e = cudaMemPoolCreate(&I.pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(I.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e != cudaSuccess) {
+        if (I.pool) cudaMemPoolDestroy(I.pool);
+        cudaStreamDestroy(I.ps);
+        delete S;
+        return cuda_fail(e, "pr_server_create (memory pool)");
     }
     I.th = std::thread([&I] { I.loop(); });
     *out = S;
@@ -1653,7 +1709,17 @@ extern "C" void pr_server_destroy(pr_server *S) {
         if (kv.second->dout) cudaFreeAsync(kv.second->dout, I.s);
         delete kv.second;
     }
+    for (Buf *b : {&I.d_gctl, &I.d_gstat, &I.d_slots, &I.d_stat, &I.d_fprobs, &I.d_ftiles, &I.d_fdtiles,
+                   &I.d_fvtiles})
+        b->release();
+    for (int f = 0; f < 3; f++) {
+        I.d_probs[f].release();
+        I.d_tiles[f].release();
+        I.d_bc[f].release();
+    }
     cudaStreamSynchronize(I.s);
+    cudaStreamSynchronize(I.ps);
     if (I.ps) cudaStreamDestroy(I.ps);
+    if (I.pool) cudaMemPoolDestroy(I.pool);  // every allocation from it has been freed above
     delete S;
 }

@@ -92,11 +92,12 @@ void Buf::release() {
     stream_ordered = false;
 }
 
-pr_status Buf::alloc_async(size_t nbytes, cudaStream_t stream) {
+pr_status Buf::alloc_async(size_t nbytes, cudaStream_t stream, cudaMemPool_t pool) {
     release();
     s = stream;
     if (nbytes == 0) nbytes = 16;
-    if (cudaMallocAsync(&p, nbytes, stream) != cudaSuccess) {
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, nbytes, pool, stream) : cudaMallocAsync(&p, nbytes, stream);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
         return fail(PR_ENOMEM, "device allocation of " + std::to_string(nbytes) + " bytes failed");

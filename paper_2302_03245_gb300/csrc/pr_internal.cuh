@@ -42,9 +42,10 @@ struct Buf {
     void *fctx = nullptr;
     bool stream_ordered = false;  // made by alloc_async: freed with cudaFreeAsync on s
     pr_status alloc(size_t nbytes, cudaStream_t stream);
-    // cudaMallocAsync on `stream`, never the allocator hook: for the server's
-    // own thread, which must not call back into the host program
-    pr_status alloc_async(size_t nbytes, cudaStream_t stream);
+    // cudaMallocAsync on `stream` (from `pool` when given), never the allocator
+    // hook: for the server's own thread, which must not call back into the host
+    // program
+    pr_status alloc_async(size_t nbytes, cudaStream_t stream, cudaMemPool_t pool = nullptr);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
     void swap(Buf &o) noexcept {

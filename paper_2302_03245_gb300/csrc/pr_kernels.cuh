@@ -32,11 +32,13 @@
 // Number formats.  GB300's FP64 pipe retires a warp instruction in about 64
 // cycles of one SM sub-partition, even when a single lane executes it, so
 // the state type T is one of
-//   double  -- IEEE FP64 (reference form, PR_FP64);
-//   float   -- FP32 state (PR_FP32);
+//   double  -- IEEE FP64 throughout (the paper's arithmetic, PR_FP64): state,
+//              pushed mass, gathers, sums;
+//   float   -- FP32 state (PR_FP32), with FP64 scalars; its correction sweep
+//              and the rounds after it run in IEEE FP64;
 //   float2  -- double-float (hi, lo) pairs, value hi + lo, 48-bit significand,
 //              arithmetic on FP32 instructions only (PR_DF64).
-// The pushed mass is gathered as float (FP32) or double-float pairs, and the
+// The FP32 and double-float forms gather float / double-float values; their
 // residual-L1 and other sums run in double-float with a final FP64 sum.
 #pragma once
 
@@ -175,7 +177,7 @@ template <> struct GT<float2> {
 // R: the accumulator of sums (residual L1, Power deltas, normaliser)
 template <typename T> struct ST;
 template <> struct ST<double> {
-    using V = float2;  // pushed mass gathered as double-float pairs
+    using V = double;  // pushed mass gathered and summed in IEEE double
     using R = double;
     static __device__ __forceinline__ double zero() { return 0.0; }
     static __device__ __forceinline__ double add(double a, double b) { return a + b; }
@@ -192,8 +194,8 @@ template <> struct ST<double> {
         return k->p_dense ? P.p64[j] : k->pu;
     }
     static __device__ __forceinline__ double invdeg(const DevGraph &G, int i) { return G.inv_deg64[i]; }
-    static __device__ __forceinline__ double from_acc(float2 a) { return df_to_d(a); }
-    static __device__ __forceinline__ float2 pack(double v) { return df_from_d(v); }
+    static __device__ __forceinline__ double from_acc(double a) { return a; }
+    static __device__ __forceinline__ double pack(double v) { return v; }
     static __device__ __forceinline__ double to_d(double v) { return v; }
     static __device__ __forceinline__ double pack_from_d(double v) { return v; }
     static __device__ __forceinline__ R rval(double v) { return v; }
@@ -215,7 +217,7 @@ template <> struct ST<double> {
 };
 template <> struct ST<float> {
     using V = float;
-    using R = float2;
+    using R = double;  // the residual-L1 and other sums of FP32 state run in IEEE double
     static __device__ __forceinline__ float zero() { return 0.f; }
     static __device__ __forceinline__ float add(float a, float b) { return a + b; }
     static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
@@ -235,11 +237,11 @@ template <> struct ST<float> {
     static __device__ __forceinline__ float pack(float v) { return v; }
     static __device__ __forceinline__ double to_d(float v) { return (double)v; }
     static __device__ __forceinline__ float pack_from_d(double v) { return (float)v; }
-    static __device__ __forceinline__ R rval(float v) { return make_float2(v, 0.f); }
-    static __device__ __forceinline__ R radd(R a, R b) { return df_add(a, b); }
-    static __device__ __forceinline__ R rzero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ R rshfl(R a, int o) { return GT<float2>::shfl_down(a, o, 32); }
-    static __device__ __forceinline__ double r_to_d(R a) { return df_to_d(a); }
+    static __device__ __forceinline__ R rval(float v) { return (double)v; }
+    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R rzero() { return 0.0; }
+    static __device__ __forceinline__ R rshfl(R a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double r_to_d(R a) { return a; }
     static __device__ __forceinline__ void atomic_add(float *a, float v) { atomicAdd(a, v); }
     static __device__ __forceinline__ void push_to(float *r, double *, int j, float w) { atomicAdd(&r[j], w); }
     static __device__ __forceinline__ void commit_sub(float *r, int i, float v) { atomicAdd(&r[i], -v); }
@@ -1443,13 +1445,13 @@ __device__ __forceinline__ void sweep_epilogue_v(const DevGraph &G, const Ctl *c
         a.pi_next[j] = y;
         if (j < G.n_nd) a.q_next[j] = ST<T>::pack(ST<T>::mul(y, ST<T>::invdeg(G, j)));
     } else if constexpr (OP == OP_CORRECT) {
-        // r = p + c P~ s - s with s = x / (1-c): the exact residual of the current reserve,
-        // evaluated in double-float (FP32 instructions; a per-row FP64 divide would cost
-        // more than the whole gather on GB300's FP64 pipe)
-        static_assert(std::is_same<T, float2>::value, "the correction writes double-float state");
-        const float2 sj = df_mul(pre, ST<float2>::inv_om(ctl));
-        const float2 pj = ctl->p_dense ? df_from_d(a.pv.p64[j]) : ctl->pu_df;
-        a.r[j] = df_add(df_add(pj, df_mul(ST<float2>::c(ctl), in)), df_neg(sj));
+        // r = p + c P~ s - s with s = x / (1-c): the exact residual of the current
+        // reserve (for any s, (I - c P~)(y - s) = p + c P~ s - s, from Eq. 4), in IEEE
+        // double: the gathered values q_u = x_u / ((1-c) deg u), their sum and this
+        // epilogue.  1/(1-c) is applied as a multiply by its double reciprocal.
+        static_assert(std::is_same<T, double>::value, "the correction runs in IEEE double");
+        const double sj = pre * ctl->inv_om;
+        a.r[j] = (ST<double>::p(ctl, a.pv, j) + ctl->c * in) - sj;
     } else {  // OP_PHASE2: r_d = p_d + c sum_{u in S(d)} x_u / ((1-c) deg(u)); phase 1 never
               // touches a dangling residual, so r_d still holds p_d
         a.r[j] = ST<T>::add(pre, ST<T>::mul(ST<T>::c(ctl), in));

@@ -109,18 +109,16 @@ __global__ void k_power_init(DevGraph G, Ctl *ctl, Partials P, PVals pv, T *pi, 
     }
 }
 
-// FP32 reserve -> FP64: x64 = x32, q_u = x_u / ((1-c) deg(u)) packed for the
-// correction gather; IFP2: r64_d = p_d (dangling residual untouched in phase 1)
-// FP32 reserve -> double-float state (exactly) and the gather values
-// q_u = x_u / ((1-c) deg(u)) of the correction sweep; IFP2's dangling residual
-// is p (phase 1 never touches it), IFP1's comes from the sweep
-__global__ void k_to_df(DevGraph G, const Ctl *ctl, const float *x32, float2 *x, float2 *r, float2 *q, PVals pv,
-                        int ifp2) {
+// FP32 reserve -> IEEE double state (exactly) and the gather values
+// q_u = x_u / ((1-c) deg(u)) of the correction sweep, in double; IFP2's
+// dangling residual is p (phase 1 never touches it), IFP1's comes from the sweep
+__global__ void k_to_fp64(DevGraph G, const Ctl *ctl, const float *x32, double *x, double *r, double *q, PVals pv,
+                          int ifp2) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n; i += gridDim.x * blockDim.x) {
-        const float2 xv = make_float2(x32[i], 0.f);
+        const double xv = (double)x32[i];
         x[i] = xv;
-        if (i < G.n_nd) q[i] = df_mul(xv, df_mul(G.inv_degdf[i], ctl->inv_om_df));
-        else if (ifp2) r[i] = ctl->p_dense ? df_from_d(pv.p64[i]) : ctl->pu_df;
+        if (i < G.n_nd) q[i] = xv * (G.inv_deg64[i] * ctl->inv_om);
+        else if (ifp2) r[i] = ST<double>::p(ctl, pv, i);
     }
 }
 
@@ -360,11 +358,9 @@ static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
         g->ws = W;
     }
     Workspace &W = *static_cast<Workspace *>(g->ws);
-    if (prec == PR_FP64) PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(float2), n, nnd, s));
-    if (prec == PR_FP32) {
-        PR_TRY(alloc_state(W.s32, sizeof(float), sizeof(float), n, nnd, s));
-    }
-    if (prec == PR_FP32 || prec == PR_DF64) {
+    if (prec == PR_FP64 || prec == PR_FP32) PR_TRY(alloc_state(W.s64, sizeof(double), sizeof(double), n, nnd, s));
+    if (prec == PR_FP32) PR_TRY(alloc_state(W.s32, sizeof(float), sizeof(float), n, nnd, s));
+    if (prec == PR_DF64) {
         if (!W.sdf.din.p) PR_TRY(W.sdf.din.alloc(sizeof(double) * n, s));
         PR_TRY(alloc_state(W.sdf, sizeof(float2), sizeof(float2), n, nnd, s));
     }
@@ -861,32 +857,27 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         }
         finish_ifp<float2>(g, W, algo, dout, launches);
         launches += 1;
-    } else {  // FP32 rounds, FP64 correction sweep, double-float rounds to the end
+    } else {  // FP32 rounds, then the IEEE FP64 correction sweep and FP64 rounds to the end
         k_init_state<float><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s32.x.as<float>(), W.s32.r.as<float>());
         PR_TRY(ifp_phase1<float>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(0));
         const int32_t r32_rounds = W.hctl->round;
-        float2 *xdf = W.sdf.x.as<float2>(), *rdf = W.sdf.r.as<float2>();
-        k_to_df<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), xdf, rdf, W.sdf.q.as<float2>(), pv,
-                                         algo == PR_IFP2);
-        SweepArgs<float2> a{};
-        a.val = W.sdf.q.as<float2>();
-        a.r = rdf;
-        a.x = xdf;
+        double *x64 = W.s64.x.as<double>(), *r64 = W.s64.r.as<double>();
+        k_to_fp64<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), x64, r64, W.s64.q.as<double>(), pv,
+                                          algo == PR_IFP2);
+        SweepArgs<double> a{};
+        a.val = W.s64.q.as<double>();
+        a.r = r64;
+        a.x = x64;
         a.pv = pv;
-        const Plan &PL = algo == PR_IFP2 ? plan_nd_of<float2>(g) : plan_all_of<float2>(g);
+        const Plan &PL = algo == PR_IFP2 ? plan_nd_of<double>(g) : plan_all_of<double>(g);
         k_reset_run<<<1, 1, 0, s>>>(ctl);
-        k_sweep<float2, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
-        PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
-        PR_TRY(ifp_phase1<float2>(g, W, algo, use_graph, levels, prof));
+        k_sweep<double, OP_CORRECT><<<PL.nblocks, kThreads, 0, s>>>(G, PL, ctl, a);
+        PR_TRY(ifp_phase1<double>(g, W, algo, use_graph, levels, prof));
         PR_TRY(count_rounds(r32_rounds));
         fp64_rounds = W.hctl->round - r32_rounds;
-        if (algo == PR_IFP1 && G.n > G.n_nd) {
-            k_fold_inbox<<<gn, kThreads, 0, s>>>(W.sdf.r.as<float2>(), W.sdf.din.as<double>(), G.n_nd, G.n);
-            launches += 1;
-        }
-        finish_ifp<float2>(g, W, algo, dout, launches);
-        launches += 4;  // init, to double-float, reset, correction sweep
+        finish_ifp<double>(g, W, algo, dout, launches);
+        launches += 4;  // init, to FP64, reset, correction sweep
     }
     PR_CK(cudaEventRecord(e1, s));
     if (!out_is_device) PR_CK(cudaMemcpyAsync(out, dout, sizeof(double) * G.n, cudaMemcpyDeviceToHost, s));

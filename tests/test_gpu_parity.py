@@ -1,10 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances: FP64 solves must be within L1 1e-9 of the exact PageRank, FP32
-solves (FP32 rounds + FP64 correction) within L1 1e-6; closed forms are
-checked tighter where the arithmetic allows.  With xi_act ~ 0 every vertex
-with a nonzero residual is active, so the per-round frontier sizes and edge
-counts are integers the GPU must reproduce exactly.
+Two kinds of check.  (1) The same algorithm: the GPU's synchronous rounds
+against the oracle's (frontier sizes and edge counts exact, residuals to
+rounding), and the GPU result against the oracle's result at the same eps.
+(2) The exact PageRank (Eq. 2; the oracle's Power method run to 1e-13 or
+1e-15, or a closed form): every solve lies within its certified bound, and
+at the stopping thresholds the benchmark uses (IFP2 eps 5e-10 for FP64 and
+double-float, 5e-7 for the FP32 form) FP64 solves are within L1 1e-9 and
+FP32-form solves within L1 1e-6.  With xi_act ~ 0 every vertex with a
+nonzero residual is active, so the per-round frontier sizes and edge counts
+are integers the GPU must reproduce exactly.
 """
 import numpy as np
 import pytest
@@ -367,16 +372,23 @@ def test_torch_allocator_hook():
 
 
 # ------------------------------------------------------------ full size
+# the benchmark's stopping thresholds: IFP2 stops at an L1 error of about 1.2-1.35 x eps
+# on these R-MAT graphs, so half of each gate leaves a margin of about 1.5
+EPS_FP64 = 5e-10
+EPS_FP32 = 5e-7
+
+
 @pytest.fixture(scope="module")
 def rmat22():
     """R-MAT scale 22 (4,194,304 vertices, edge factor 16), 20% dangling, 10% unreferenced,
     randomly relabelled: the single-graph benchmark workload.  The oracle runs the same
-    algorithms at the same stopping thresholds, plus the Power method to 1e-13."""
+    algorithms at the same stopping thresholds, plus the Power method to 1e-13 (within
+    L1 c/(1-c) 1e-13 = 5.7e-13 of the exact PageRank)."""
     g = gg.rmat(22, 16, dangling=0.20, unref=0.10, seed=1)
     p = gg.p_uniform(g.n)
     truth, it, dl, st = oracle.power(g, C, p, tol=1e-13)
     assert st == 0
-    ref = {eps: oracle.ifp_rounds(IFP2, g, C, eps, p, trace=False) for eps in (1e-9, 1e-6)}
+    ref = {eps: oracle.ifp_rounds(IFP2, g, C, eps, p, trace=False) for eps in (EPS_FP64, EPS_FP32)}
     pw9 = oracle.power(g, C, p, tol=1e-9)[0]
     return g, truth, ref, pw9
 
@@ -386,19 +398,22 @@ def test_fullsize_rmat22_bench_configuration(rmat22):
     g, truth, ref, pw9 = rmat22
     p = gg.p_uniform(g.n)
     with gpu_graph(g) as G:
-        # the benchmark's solve: IFP2, double-float and FP64, eps 1e-9, default options
-        for prec in (pr.PR_DF64, pr.PR_FP64):
-            out, st, status = G.solve(C, 1e-9, pr.PR_IFP2, prec)
+        # the benchmark's solve: IFP2, IEEE FP64 and double-float, eps 5e-10, default options
+        for prec in (pr.PR_FP64, pr.PR_DF64):
+            out, st, status = G.solve(C, EPS_FP64, pr.PR_IFP2, prec)
             assert status == pr.PR_OK
-            assert abs(st["rounds"] - ref[1e-9]["rounds"]) <= 1
-            assert l1(out, ref[1e-9]["pi"]) <= 1e-9            # parity with the same algorithm
+            assert abs(st["rounds"] - ref[EPS_FP64]["rounds"]) <= 1
+            assert l1(out, ref[EPS_FP64]["pi"]) <= 1e-9         # parity with the same algorithm
             err = l1(out, truth)
+            assert err <= 1e-9, (prec, err)                     # the FP64 gate vs the exact PageRank
             assert err <= st["err_bound"] + 1e-12               # certified bound vs exact PageRank
             assert err <= oracle.eq2_residual(g, C, p, out) / (1 - C) + 1e-12
-        # FP32 form (FP32 rounds, FP64 correction) against the FP64 oracle at the same eps
-        out, st, status = G.solve(C, 1e-6, pr.PR_IFP2, pr.PR_FP32)
-        assert status == pr.PR_OK and l1(out, ref[1e-6]["pi"]) <= 1e-6
-        assert l1(out, truth) <= st["err_bound"] + 1e-9
+        # FP32 form (FP32 rounds, IEEE FP64 correction and rounds) at eps 5e-7
+        out, st, status = G.solve(C, EPS_FP32, pr.PR_IFP2, pr.PR_FP32)
+        assert status == pr.PR_OK and l1(out, ref[EPS_FP32]["pi"]) <= 1e-6
+        err = l1(out, truth)
+        assert err <= 1e-6, err                                 # the FP32 gate vs the exact PageRank
+        assert err <= st["err_bound"] + 1e-9
         # Power at the same tolerance as the oracle's Power
         for prec in (pr.PR_FP64, pr.PR_DF64):
             out, st, status = G.solve(C, 1e-9, pr.PR_POWER, prec)
@@ -406,5 +421,6 @@ def test_fullsize_rmat22_bench_configuration(rmat22):
             assert l1(out, truth) <= st["err_bound"] + 1e-12
         # push-only and pull-only delivery give the same result up to rounding
         for mode in (pr.PR_MODE_PUSH, pr.PR_MODE_PULL):
-            out2, st2, _ = G.solve(C, 1e-9, pr.PR_IFP2, pr.PR_DF64, opts=dict(mode=mode))
-            assert l1(out2, ref[1e-9]["pi"]) <= 1e-9
+            out2, st2, _ = G.solve(C, EPS_FP64, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=mode))
+            assert l1(out2, ref[EPS_FP64]["pi"]) <= 1e-9
+            assert l1(out2, truth) <= 1e-9

@@ -5,6 +5,8 @@ factors, personalization vectors, precisions, arrival times) must give the
 result of the same solve done alone with pr_solve, and be within its
 certified bound of the exact (personalized) PageRank from the FP64 oracle.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -134,14 +136,20 @@ def test_server_invalid_arguments(graphs):
         with pytest.raises(pr.PrError) as e:
             S.submit(hs[0], 0.85, 1e-9, pr.PR_DF64, p=np.array([1.0]), p_idx=np.array([gl[0].n], np.int32))
         assert e.value.status == pr.PR_EINVAL
-        with pytest.raises(pr.PrError) as e:
+        st = pr.pr_stats()
+        assert pr.lib().pr_server_poll(S.h, 12345, None, ctypes.byref(st)) == pr.PR_EINVAL  # unknown ticket
+        with pytest.raises(ValueError):
             pr.pr_server_poll(S.h, 12345, 1)
-        assert e.value.status == pr.PR_EINVAL
         t = S.submit(hs[3], 0.85, 1e-9, pr.PR_DF64)
+        # the output is checked against the request's graph, not a caller's n
+        with pytest.raises(ValueError):
+            pr.pr_server_poll(S.h, t, gl[3].n - 1, np.empty(gl[3].n - 1))
+        with pytest.raises(ValueError):
+            pr.pr_server_poll(S.h, t, None, np.empty(gl[3].n - 1))
         S.wait(t)
-        with pytest.raises(pr.PrError) as e:  # a ticket is released by the poll that returns it
+        assert pr.lib().pr_server_poll(S.h, t, None, ctypes.byref(st)) == pr.PR_EINVAL  # released by its poll
+        with pytest.raises(ValueError):
             pr.pr_server_poll(S.h, t, gl[3].n)
-        assert e.value.status == pr.PR_EINVAL
     with pr.Server(4096) as S:  # one request needs more than the whole budget
         with pytest.raises(pr.PrError) as e:
             S.submit(hs[0], 0.85, 1e-9, pr.PR_DF64)
@@ -202,3 +210,23 @@ def test_server_column_groups_match_alone(big, prec):
             alone_pull, st2, _ = h.solve(c, eps, pr.PR_IFP2, prec, p=p, p_idx=pi, opts=dict(mode=pr.PR_MODE_PULL))
             assert l1(out, alone_pull) <= 1e-12
             assert abs(st["rounds"] - st2["rounds"]) <= 1
+
+
+def test_server_fp32_requests_meet_the_gate(big):
+    """Served FP32-form requests (FP32 rounds, IEEE FP64 correction and rounds) at the
+    benchmark's eps 5e-7 are within L1 1e-6 of their exact (personalized) PageRank,
+    alone and in a mix of column-group and tile-engine requests."""
+    g, h = big
+    rng = np.random.default_rng(77)
+    reqs = [(None, None)]
+    for _ in range(9):
+        k = int(rng.integers(1, 65))
+        reqs.append((np.full(k, 1.0 / k), rng.choice(g.n, size=k, replace=False).astype(np.int32)))
+    with pr.Server(1 << 34) as S:
+        tickets = [S.submit(h, 0.85, 5e-7, pr.PR_FP32, p, pi) for p, pi in reqs]
+        results = [S.wait(t) for t in tickets]
+    for (p, pi), (out, st, status) in zip(reqs, results):
+        assert status == pr.PR_OK
+        assert st["fp64_rounds"] >= 0
+        err = l1(out, truth_of(g, 0.85, p, pi))
+        assert err <= 1e-6, err
