@@ -17,6 +17,15 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   ifp_rounds       pinned: cycle R_t = c^t round count, chain round count and
                    exact stop, mass invariant every round, closed forms, dense
                    solve within the bound 2cR/(1-c) (IFP1) / 2R/(1-c) (IFP2).
+  ifp2_levels      pinned: the 3-round chain, the level rule on a hand-made
+                   graph, identity and in-flight mass at any round cap, bound.
+  ifp_async        pinned: one round on a forward DAG and the chain, equal to
+                   ifp_rounds when every edge points down, the cycle's closed
+                   form, identity and mass at any cap, the certified bound.
+  ifp_scan         pinned: one scan on a forward DAG and the chain, equal to
+                   ifp_rounds when every edge points down, the cycle's closed
+                   form R_t = c^(n(t-1)) R_1, identity, mass and R <= Rub at any
+                   cap, the certified bound.
 """
 from __future__ import annotations
 
@@ -82,6 +91,7 @@ def _bind(lib):
     lib.orc_ifp_rounds.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32,
                                    P, P, P, P, P, P, P, P]
     lib.orc_ifp_async.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32, P, P, P, P, P, P]
+    lib.orc_ifp_scan.argtypes = [ctypes.c_int, i32, P, P, dbl, dbl, dbl, P, i32, P, P, P, P, P, P, P]
     lib.orc_ifp2_levels.argtypes = [i32, P, P, dbl, dbl, dbl, P, P, i32, i32,
                                     P, P, P, P, P, P, P, P]
     return lib
@@ -185,6 +195,29 @@ class Oracle:
             out.update(R=tR[:k + 1].copy(), F=tF[:k].copy())
         return out
 
+    def ifp_scan(self, algo, g, c, eps, p, xi_act=None, max_rounds=100000, trace=True):
+        """IFP1/IFP2 scans in id order with the (1-c) reserve (orc_ifp_scan).
+        Returns dict(pi, x, r, rounds, status, R, Rub, F), traces indexed by scan."""
+        off, dst = _csr(g)
+        p = _f64(p)
+        n = g.n
+        if xi_act is None:
+            n_nd = int((np.diff(off) > 0).sum())
+            xi_act = eps / max(n_nd, 1)
+        x, r, pi = np.empty(n), np.empty(n), np.empty(n)
+        T = max_rounds + 2
+        tR = np.zeros(T) if trace else None
+        tU = np.zeros(T) if trace else None
+        tF = np.zeros(T, np.int64) if trace else None
+        rounds = ctypes.c_int32()
+        st = self.L.orc_ifp_scan(algo, n, _p(off), _p(dst), c, eps, xi_act, _p(p), max_rounds, _p(x), _p(r),
+                                 _p(pi), ctypes.byref(rounds), _p(tR), _p(tU), _p(tF))
+        k = rounds.value
+        out = dict(pi=pi, x=x, r=r, rounds=k, status=st, xi_act=xi_act)
+        if trace:
+            out.update(R=tR[:k].copy(), Rub=tU[:k].copy(), F=tF[:k].copy())
+        return out
+
     def ifp2_levels(self, g, c, eps, p, levels, L, xi_act=None, max_rounds=100000, trace=True):
         """IFP2 in level-ordered rounds (orc_ifp2_levels).  levels[i] in [0, L]
         for non-dangling i (gs_levels gives the library's assignment rule).
@@ -272,6 +305,10 @@ def ifp2_levels(*a, **k):
 
 def ifp_async(*a, **k):
     return default().ifp_async(*a, **k)
+
+
+def ifp_scan(*a, **k):
+    return default().ifp_scan(*a, **k)
 
 
 def certified_l1_bound(algo: int, c: float, R: float) -> float:

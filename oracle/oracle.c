@@ -29,6 +29,11 @@
  *                       when its turn comes (Sec. 3.2's threads), the
  *                       frontier taken in id order: one schedule of the
  *                       GPU's asynchronous rounds.
+ *   orc_ifp_scan        IFP1 / IFP2 as full scans in id order with a (1-c)
+ *                       reserve: every non-dangling vertex, at its turn,
+ *                       pushes all it holds if that is above xi_act
+ *                       (Alg. 2/3 with K = 1): one schedule of the GPU's
+ *                       asynchronous pull rounds.
  *
  * Arrays: out_off[n+1] (int64), out_dst[m] (int32), vertex ids 0..n-1.
  * Every loop is the textbook one; nothing is blocked, fused or reordered.
@@ -555,5 +560,64 @@ int orc_ifp_rounds(int algo, int32_t n, const int64_t *out_off, const int32_t *o
     ifp_finalise(algo, n, out_off, out_dst, c, p, x, r, pi);
     free(v);
     free(active);
+    return status;
+}
+
+/*
+ * IFP1 / IFP2 in scans (Alg. 2 / Alg. 3 with one Calculation thread, in id
+ * order), with the (1-c) reserve and the stopping rule of the rounds.  At its
+ * turn each non-dangling vertex i looks at the residual it holds now -- its
+ * value at the scan's start plus everything pushed to it so far in this scan
+ * -- and, if |r_i| > xi_act, keeps (1-c) of it in x_i and pushes c/deg(i) of
+ * it to each out-neighbour (IFP2: non-dangling ones only), r_i = 0.
+ *
+ * After each scan: R_t = sum of |r| over non-dangling vertices (the exact
+ * residual at the scan's end), and the upper bound the GPU's concurrent scans
+ * stop on, which cannot know whether a target took a push in the same scan:
+ * the residual each vertex left at its turn plus c |v| n_i / deg(i) for every
+ * push v of i, n_i its pushes that can land on a non-dangling vertex.  The
+ * scans stop when R_t <= eps (status 0), at max_rounds (status 1), or when a
+ * scan pushed nothing while R_t > eps (status 2); ifp_finalise ends them.
+ */
+int orc_ifp_scan(int algo, int32_t n, const int64_t *out_off, const int32_t *out_dst, double c, double eps,
+                 double xi_act, const double *p, int32_t max_rounds, double *x, double *r, double *pi,
+                 int32_t *rounds_out, double *trace_R, double *trace_Rub, int64_t *trace_F) {
+    for (int32_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = p[i]; }
+    int32_t t = 0;
+    int status = 1;
+    for (;;) {
+        if (t >= max_rounds) { status = 1; break; }
+        int64_t nF = 0;
+        double Rub = 0.0;
+        for (int32_t i = 0; i < n; i++) {
+            int64_t deg = outdeg(out_off, i);
+            if (deg == 0) continue;
+            if (!(fabs(r[i]) > xi_act)) { Rub += fabs(r[i]); continue; }
+            double v = r[i]; /* everything i holds at its turn */
+            r[i] = 0.0;
+            x[i] = x[i] + (1.0 - c) * v;
+            nF++;
+            int64_t valid = 0;
+            for (int64_t e = out_off[i]; e < out_off[i + 1]; e++) {
+                int32_t j = out_dst[e];
+                if (outdeg(out_off, j) == 0) {
+                    if (algo == ORC_IFP2) continue; /* invalid edge */
+                } else {
+                    valid++;
+                }
+                r[j] = r[j] + c * v / (double)deg;
+            }
+            Rub += c * fabs(v) * (double)valid / (double)deg; /* may land after its target's turn */
+        }
+        double R = nd_residual(n, out_off, r);
+        if (trace_R) trace_R[t] = R;
+        if (trace_Rub) trace_Rub[t] = Rub;
+        if (trace_F) trace_F[t] = nF;
+        t++;
+        if (R <= eps) { status = 0; break; }
+        if (nF == 0) { status = 2; break; }
+    }
+    if (rounds_out) *rounds_out = t;
+    ifp_finalise(algo, n, out_off, out_dst, c, p, x, r, pi);
     return status;
 }

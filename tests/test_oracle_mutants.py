@@ -74,6 +74,18 @@ MUTANTS = {
     "async_scans_in_reverse_id_order": (
         "        for (int32_t i = 0; i < n; i++) {\n            if (!in_f[i]) continue;",
         "        for (int32_t i = n - 1; i >= 0; i--) {\n            if (!in_f[i]) continue;"),
+    "scan_in_reverse_id_order": (
+        "        for (int32_t i = 0; i < n; i++) {\n            int64_t deg = outdeg(out_off, i);\n            if (deg == 0) continue;\n            if (!(fabs(r[i]) > xi_act))",
+        "        for (int32_t i = n - 1; i >= 0; i--) {\n            int64_t deg = outdeg(out_off, i);\n            if (deg == 0) continue;\n            if (!(fabs(r[i]) > xi_act))"),
+    "scan_keeps_the_pushed_residual": (
+        "            r[i] = 0.0;\n            x[i] = x[i] + (1.0 - c) * v;",
+        "            x[i] = x[i] + (1.0 - c) * v;"),
+    "scan_bound_without_pushes": (
+        "            Rub += c * fabs(v) * (double)valid / (double)deg; /* may land after its target's turn */",
+        "            (void)valid;"),
+    "scan_reserve_unscaled": (
+        "            x[i] = x[i] + (1.0 - c) * v;",
+        "            x[i] = x[i] + v;"),
     "power_off_by_one_degree": (
         "next[out_dst[e]] += c * pi[i] / (double)deg;",
         "next[out_dst[e]] += c * pi[i] / (double)(deg + 1);"),

@@ -577,3 +577,107 @@ def test_async_cycle_closed_form(orc, n):
         assert list(o["F"]) == [n] + [1] * (o["rounds"] - 1)
         assert o["rounds"] == 1 + int(math.ceil(math.log(1e-12 / R1) / math.log(C)))
         assert l1(o["pi"], np.full(n, 1.0 / n)) < 1e-11
+
+
+# --------------------------------------- scans in id order (asynchronous pull rounds)
+@pytest.mark.parametrize("n", [2, 3, 40])
+def test_scan_chain_drains_in_one_scan(orc, n):
+    """Path 0->...->n-1 in id order: each vertex passes on at its turn all its
+    predecessor just gave it, so one scan carries every residual to the
+    dangling end, exactly."""
+    g = gg.chain(n)
+    y = (1 - C ** (np.arange(n) + 1)) / (n * (1 - C))
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_scan(algo, g, C, 0.0, gg.p_uniform(n), xi_act=0.0)
+        assert o["status"] == 0 and o["rounds"] == 1 and o["R"][-1] == 0.0
+        assert l1(o["pi"], y / y.sum()) < 1e-14
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_scan_forward_dag_drains_in_one_scan(orc, seed):
+    """Every edge runs to a higher id: one scan leaves no residual on a
+    non-dangling vertex and gives the exact PageRank."""
+    g = ordered_dag(120, 4.0, seed, forward=True)
+    p = gg.p_random(g.n, seed) / gg.p_random(g.n, seed).sum()
+    truth = eig_pagerank(g, C, p)
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_scan(algo, g, C, 0.0, p, xi_act=0.0)
+        assert o["status"] == 0 and o["rounds"] == 1 and o["R"][-1] == 0.0
+        assert l1(o["pi"], truth) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_scan_equals_synchronous_when_edges_point_down(orc, seed):
+    """Every edge runs to a lower or equal id: at its turn a vertex holds its
+    scan-start value, and every vertex holding more than xi_act pushes, so a
+    scan is one synchronous round: the same frontiers, residuals and result."""
+    g = ordered_dag(150, 4.0, seed, forward=False)
+    p = gg.p_random(g.n, seed + 10, zero_frac=0.3)
+    p /= p.sum()
+    for algo in (IFP1, IFP2):
+        a = orc.ifp_scan(algo, g, C, 1e-12, p)
+        s = orc.ifp_rounds(algo, g, C, 1e-12, p)
+        assert a["status"] == s["status"] == 0 and a["rounds"] == s["rounds"]
+        assert np.array_equal(a["F"], s["F"][:a["rounds"]])
+        # the rounds trace R at each round's start (R_0 = 1), the scans at each scan's end
+        assert np.allclose(a["R"], s["R"][1:a["rounds"] + 1], rtol=1e-13, atol=0)
+        assert l1(a["pi"], s["pi"]) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_scan_identity_mass_and_bound_at_any_stop(orc, seed):
+    """After any number of scans the state is one of the rounds' states: IFP1
+    keeps sum x + sum r = sum p; r = p + c P~ s - s (s = x/(1-c)) on the
+    non-dangling vertices; the exact residual R never exceeds the bound the
+    GPU stops on, and R never rises (p >= 0)."""
+    g = gg.random_small(200, avg_deg=5.0, dangling=0.2, unref=0.1, seed=seed, loops=True)
+    p = gg.p_random(g.n, seed, zero_frac=0.3)
+    p /= p.sum()
+    P = sparse_P(g)
+    nd = (g.outdeg > 0).astype(float)
+    Pt = sp.diags(nd) @ P
+    for cap in (1, 2, 5):
+        o = orc.ifp_scan(IFP1, g, C, 1e-30, p, max_rounds=cap)
+        assert o["status"] == 1 and o["rounds"] == cap
+        assert abs(o["x"].sum() + o["r"].sum() - 1.0) < 1e-14
+        s = o["x"] / (1 - C)
+        assert l1(o["r"], p + C * (P @ s) - s) < 1e-13
+        assert np.all(o["R"] <= o["Rub"] * (1 + 1e-14))
+        o = orc.ifp_scan(IFP2, g, C, 1e-30, p, max_rounds=cap)
+        s = o["x"] / (1 - C)
+        assert l1(o["r"] * nd, (p + C * (Pt @ s) - s) * nd) < 1e-13
+        assert np.all(o["R"] <= o["Rub"] * (1 + 1e-14))
+        assert np.all(np.diff(o["R"]) <= 0.0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("eps", [1e-5, 1e-11])
+def test_scan_within_certified_bound_and_faster(orc, seed, eps):
+    g = gg.random_small(150, avg_deg=4.0, dangling=0.2, unref=0.1, seed=seed)
+    p = gg.p_random(g.n, seed, zero_frac=0.5)
+    p /= p.sum()
+    truth = eig_pagerank(g, C, p)
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_scan(algo, g, C, eps, p)
+        assert o["status"] == 0 and o["R"][-1] <= eps
+        assert l1(o["pi"], truth) <= oracle.certified_l1_bound(algo, C, o["R"][-1]) + 1e-14
+        assert o["rounds"] < orc.ifp_rounds(algo, g, C, eps, p)["rounds"]
+
+
+@pytest.mark.parametrize("n", [2, 5, 30])
+def test_scan_cycle_closed_form(orc, n):
+    """Directed cycle 0->1->...->n-1->0, uniform p.  In scan 1 vertex k pushes
+    (1 - c^(k+1))/(n(1-c)), so only vertex 0 keeps c(1 - c^n)/(n(1-c)) = R_1.
+    In every later scan that mass goes once around the cycle: R_t = c^(n(t-1)) R_1,
+    with all n vertices pushing.  The bound the GPU stops on counts every
+    push as possibly in flight: c times the mass pushed."""
+    g = gg.cycle(n)
+    for algo in (IFP1, IFP2):
+        o = orc.ifp_scan(algo, g, C, 1e-12, gg.p_uniform(n), xi_act=0.0)
+        R1 = C * (1 - C ** n) / (n * (1 - C))
+        t = np.arange(1, o["rounds"] + 1)
+        assert np.allclose(o["R"], R1 * C ** (n * (t - 1)), rtol=1e-12, atol=0)
+        assert list(o["F"]) == [n] * o["rounds"]
+        pushed1 = sum((1 - C ** (k + 1)) / (n * (1 - C)) for k in range(n))
+        assert o["Rub"][0] == pytest.approx(C * pushed1, rel=1e-13)
+        assert l1(o["pi"], np.full(n, 1.0 / n)) < 1e-11
