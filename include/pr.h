@@ -44,7 +44,9 @@ typedef enum {
     PR_ETIMEOUT = 5, /* a bounded device-side wait ran out (reserved: no kernel of this
                         library waits on another block, rank or flag) */
     PR_EAGAIN = 6,   /* server: over the HBM budget and the queue is full */
-    PR_EBUSY = 7     /* server: request not finished yet */
+    PR_EBUSY = 7,    /* server: request not finished yet */
+    PR_ECHECK = 8    /* debug build only: an index or invariant check failed (see
+                        pr_debug_report_get); the accesses it guards were skipped */
 } pr_status;
 
 typedef enum {
@@ -84,7 +86,7 @@ typedef enum {
                           are those of the other modes.  PR_EINVAL with another
                           algorithm, on a graph without levels, and in
                           pr_solve_batch and the server */
-    PR_MODE_ASYNC = 4   /* IFP1/IFP2 push rounds in the concurrency of Sec. 3.2: the
+    PR_MODE_ASYNC = 4,  /* IFP1/IFP2 push rounds in the concurrency of Sec. 3.2: the
                           frontier is chosen at the round's start as in the other
                           modes, but each frontier vertex pushes all of its residual
                           at the moment it is processed (an atomic exchange), so mass
@@ -94,6 +96,22 @@ typedef enum {
                           mass conservation and the certified bound are unchanged.
                           PR_EINVAL with PR_POWER, and in pr_solve_batch and the
                           server */
+    PR_MODE_APULL = 5   /* IFP1/IFP2 asynchronous pull rounds, the concurrency of
+                          Sec. 3.2 without atomics: a round gathers over every
+                          non-dangling row, and each row recomputes what it holds
+                          now from the reserves by Eq. 4's identity,
+                          r_j = p_j + c sum_{i in S(j)} x_i/((1-c) deg i) - x_j/(1-c),
+                          which counts every push committed so far (this round's
+                          included when its source committed before the gather read
+                          it) and never a push twice; it commits all of r_j when
+                          |r_j| > xi_act.  The stop test uses a bound on the
+                          residual the round leaves (the commits' pushes counted as
+                          possibly not yet taken), so the certified bound holds.
+                          Fewer rounds than synchronous ones; the schedule varies
+                          from run to run.  PR_FP64 and PR_DF64 only (the recompute
+                          cancels to the state's precision: FP32 would stall near
+                          1e-7 of the mass); PR_EINVAL with PR_POWER, PR_FP32, and in
+                          pr_solve_batch and the server */
 } pr_mode;
 
 /*
@@ -426,6 +444,38 @@ typedef struct {
     double ms_step_max;               /* the longest step */
 } pr_server_stats;
 pr_status pr_server_get_stats(pr_server *s, pr_server_stats *st);
+
+/*
+ * Debug build (libpr_debug.so, compiled with -DPR_DEBUG; the paper has no
+ * counterpart).  Its kernels check every index they load from a graph array
+ * (in-list sources, out-list targets, frontier entries, the vertex
+ * permutation, tile bounds) before using it, and skip the access when it is
+ * out of range; after every round of a single solve (synchronous push, pull
+ * or asynchronous rounds; not the level-ordered ones) it checks on the device
+ * the two invariants of the rounds with a (1-c) reserve: the mass balance
+ * (IFP1 sum x + sum r = 1; IFP2 the same plus the mass deferred to phase 2)
+ * and the residual identity r = p + c P~ x/(1-c) - x/(1-c) (Sec. 3.1, Eq. 4),
+ * each within a tolerance of the state's arithmetic.  A solve or batch whose
+ * checks failed returns PR_ECHECK.
+ * pr_is_debug_build: 1 in the debug library, 0 in the release one.
+ * pr_debug_report_get: the checks run and failed since the last reset, the
+ *   first failure (site, value, bound; invariant deviations are scaled by
+ *   1e18) and the largest deviations seen; reset != 0 clears it.
+ * pr_debug_inject: a test hook: the checks at `site` (0 = none) fail from the
+ *   next solve on -- an index check sees half its bound, an invariant check
+ *   fails outright -- so the net itself can be tested with no invalid access.
+ * Both return PR_EINVAL in a release build.
+ */
+typedef struct {
+    int64_t checks, fails;           /* invariant checks run; failed checks of any kind */
+    int32_t first_site, pad;         /* 1 in-list source, 2 out-list target, 3 frontier entry,
+                                        4 permutation, 5 tile bounds, 16 mass, 17 identity */
+    int64_t first_value, first_bound;
+    double max_mass_dev, max_identity_dev;
+} pr_debug_report;
+int pr_is_debug_build(void);
+pr_status pr_debug_report_get(pr_debug_report *out, int reset);
+pr_status pr_debug_inject(int32_t site);
 
 /* Release a graph and its workspace (NULL is ignored). */
 void pr_destroy(pr_graph *g);

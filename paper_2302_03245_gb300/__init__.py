@@ -8,6 +8,9 @@ library's allocator) and streams.
 
 There is no CPU fallback: if libpr.so is missing or cannot be loaded the
 functions raise, and a CUDA-less machine can only inspect the library.
+With PR_LIBRARY=debug in the environment at first use, the debug build
+libpr_debug.so (index and invariant checks, see include/pr.h) is loaded
+instead.
 """
 from __future__ import annotations
 
@@ -17,19 +20,20 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpr.so")
+DEBUG = os.environ.get("PR_LIBRARY", "") == "debug"
+LIB_PATH = os.path.join(HERE, "libpr_debug.so" if DEBUG else "libpr.so")
 
-PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY = range(8)
+PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ENOTCONV, PR_ETIMEOUT, PR_EAGAIN, PR_EBUSY, PR_ECHECK = range(9)
 PR_POWER, PR_IFP1, PR_IFP2 = 0, 1, 2
 PR_FP64, PR_FP32, PR_DF64 = 0, 1, 2
-PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL, PR_MODE_LEVELS, PR_MODE_ASYNC = 0, 1, 2, 3, 4
+PR_MODE_AUTO, PR_MODE_PUSH, PR_MODE_PULL, PR_MODE_LEVELS, PR_MODE_ASYNC, PR_MODE_APULL = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = ["PR_OK", "PR_EINVAL", "PR_ENOMEM", "PR_ECUDA", "PR_ENOTCONV", "PR_ETIMEOUT", "PR_EAGAIN",
-                "PR_EBUSY"]
+                "PR_EBUSY", "PR_ECHECK"]
 
 
 class PrError(RuntimeError):
     def __init__(self, status: int, msg: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -111,9 +115,18 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_voi
 _lib = None
 
 
+class pr_debug_report(ctypes.Structure):
+    _fields_ = [("checks", ctypes.c_int64), ("fails", ctypes.c_int64), ("first_site", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("first_value", ctypes.c_int64), ("first_bound", ctypes.c_int64),
+                ("max_mass_dev", ctypes.c_double), ("max_identity_dev", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 def build(force: bool = False) -> str:
     from . import _build
-    return _build.build(force=force)
+    return _build.build(force=force, debug=DEBUG)
 
 
 def lib() -> ctypes.CDLL:
@@ -164,6 +177,11 @@ def lib() -> ctypes.CDLL:
         L.pr_version.restype = ctypes.c_char_p
         L.pr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
         L.pr_set_allocator.restype = ctypes.c_int
+        L.pr_is_debug_build.restype = ctypes.c_int
+        L.pr_debug_report_get.argtypes = [ctypes.POINTER(pr_debug_report), ctypes.c_int]
+        L.pr_debug_report_get.restype = ctypes.c_int
+        L.pr_debug_inject.argtypes = [i32]
+        L.pr_debug_inject.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -504,6 +522,23 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------ debug build
+def pr_is_debug_build() -> bool:
+    return bool(lib().pr_is_debug_build())
+
+
+def pr_debug_report_get(reset: bool = False) -> dict:
+    """The debug build's check report (raises PrError in a release build)."""
+    r = pr_debug_report()
+    _check(lib().pr_debug_report_get(ctypes.byref(r), 1 if reset else 0))
+    return r.as_dict()
+
+
+def pr_debug_inject(site: int) -> None:
+    """Test hook of the debug build: the checks at `site` fail from the next solve on (0 = none)."""
+    _check(lib().pr_debug_inject(int(site)))
 
 
 # ------------------------------------------------------- torch allocator hook

@@ -1,6 +1,9 @@
 """Compile the CUDA sources into the in-tree shared library libpr.so.
 
 nvcc, one -gencode for sm_103a, translation units compiled in parallel.
+build(debug=True) makes libpr_debug.so instead: the same sources with
+-DPR_DEBUG (index checks on every graph-array load and per-round invariant
+checks on the device; see csrc/pr_debug.cuh), objects kept apart.
 """
 from __future__ import annotations
 
@@ -14,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpr.so")
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libpr_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -33,16 +38,18 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
     srcs, hdrs = _inputs()
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
+    extra = list(extra or []) + (["-DPR_DEBUG"] if debug else [])
+    os.makedirs(obj_dir, exist_ok=True)
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(OBJ, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [NVCC, *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", o]
+            cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
             jobs.append(cmd)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
@@ -53,17 +60,17 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
                 print(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             print(" ".join(cmd))
             print(r.stdout + r.stderr)
-            raise RuntimeError("link of libpr.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed")
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

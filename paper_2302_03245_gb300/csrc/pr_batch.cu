@@ -28,6 +28,15 @@
 #ifndef PR_GROUP_MIN_INFLIGHT
 #define PR_GROUP_MIN_INFLIGHT 2
 #endif
+// column groups per (graph, format) at most.  Every group round is a full pass
+// over the graph's in-lists, so more groups on a graph do not serve more
+// requests per second: they only stretch every step.  Requests beyond the
+// free columns wait in the queue (continuous batching: they join as columns
+// free up) instead of running alone in the tile engine, where each costs a
+// full pass per round.
+#ifndef PR_SERVER_MAX_GROUPS
+#define PR_SERVER_MAX_GROUPS 4
+#endif
 
 namespace pr {
 
@@ -112,13 +121,17 @@ __device__ __forceinline__ void push_worker(const DevGraph &G, const Ctl *ctl, c
         const int32_t *bins = B.bins + (size_t)b * n_nd;
         if (b == 0) {  // a thread per vertex
             for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-                const int i = bins[k];
+                const int i = PR_IDX(bins[k], n_nd, DBG_BIN);
+                if (i < 0) continue;
                 const T v = vbuf[i];
                 push_commit<T>(ctl, x, r, i, v);
                 const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
                 const int e0 = G.out_off[i];
                 const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-                for (int e = e0; e < e1; e++) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
+                for (int e = e0; e < e1; e++) {
+                    const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
+                    if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
+                }
             }
         } else {  // a warp (bin 1) or the block (bin 2) per vertex
             const int lanes = b == 1 ? 32 : (int)blockDim.x;
@@ -126,13 +139,17 @@ __device__ __forceinline__ void push_worker(const DevGraph &G, const Ctl *ctl, c
             const int ngrp = b == 1 ? (int)(blockDim.x >> 5) : 1;
             const int lane = b == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
             for (int k = lo + gid; k < hi; k += ngrp) {
-                const int i = bins[k];
+                const int i = PR_IDX(bins[k], n_nd, DBG_BIN);  // the same for the whole group
+                if (i < 0) continue;
                 const T v = vbuf[i];
                 if (lane == 0) push_commit<T>(ctl, x, r, i, v);
                 const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
                 const int e0 = G.out_off[i];
                 const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-                for (int e = e0 + lane; e < e1; e += lanes) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
+                for (int e = e0 + lane; e < e1; e += lanes) {
+                    const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
+                    if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
+                }
             }
         }
     }
@@ -383,8 +400,10 @@ __global__ void k_batch_fin_write(const BProb *probs, const Tile *vt, int nvt, i
         const T *x = static_cast<const T *>(P.B.x);
         const T *r = static_cast<const T *>(P.B.r);
         const double inv = 1.0 / P.ctl->zsum;
-        for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x)
-            P.out[P.G.perm[i]] = ST<T>::to_d(zval<T>(P.G, P.ctl, kind, x, r, i)) * inv;
+        for (int i = tl.lo + threadIdx.x; i < tl.hi; i += blockDim.x) {
+            const int c = PR_IDX(P.G.perm[i], P.G.n, DBG_PERM);
+            if (c >= 0) P.out[c] = ST<T>::to_d(zval<T>(P.G, P.ctl, kind, x, r, i)) * inv;
+        }
     }
 }
 
@@ -720,13 +739,38 @@ using namespace pr;
 extern "C" pr_status pr_solve_batch(pr_graph *const *gs, int32_t count, const double *c, const double *eps,
                                     pr_algo a, pr_prec prec, const pr_pvec *ps, const pr_opts *opts,
                                     double *const *outs, int outs_are_device, pr_stats *sts) {
-    const pr_status s = solve_batch_impl(gs, count, c, eps, a, prec, ps, opts, outs, outs_are_device, sts);
-    if (s == PR_ECUDA && gs && count > 0 && gs[0]) {
-        cudaStreamSynchronize(gs[0]->stream);
+    cudaStream_t st0 = (gs && count > 0 && gs[0]) ? gs[0]->stream : nullptr;
+    dbg_begin(st0);
+    pr_status s = solve_batch_impl(gs, count, c, eps, a, prec, ps, opts, outs, outs_are_device, sts);
+    if (s == PR_ECUDA && st0) {
+        cudaStreamSynchronize(st0);
         cudaGetLastError();
     }
+    if (s == PR_OK || s == PR_ENOTCONV) s = dbg_end(st0, "pr_solve_batch", s);
     return s;
 }
+
+namespace pr {
+// host side of the debug record of this translation unit (batches, server)
+bool dbg_reset_batch(int inject) {
+#ifdef PR_DEBUG
+    DbgRec z{};
+    z.inject = inject;
+    return cudaMemcpyToSymbol(g_pr_dbg, &z, sizeof(z)) == cudaSuccess;
+#else
+    (void)inject;
+    return false;
+#endif
+}
+bool dbg_read_batch(DbgRec *out) {
+#ifdef PR_DEBUG
+    return cudaMemcpyFromSymbol(out, g_pr_dbg, sizeof(*out)) == cudaSuccess;
+#else
+    (void)out;
+    return false;
+#endif
+}
+}  // namespace pr
 
 // ============================================================== serving
 // pr_server: continuous batching of IFP2 requests (full PageRank or
@@ -1199,6 +1243,9 @@ struct ServerImpl {
             }
         }
         if (!G) {
+            int ng = 0;
+            for (const Group *gr : groups) ng += gr->g == q->g && gr->fmt == fmt;
+            if (ng >= PR_SERVER_MAX_GROUPS) return false;
             const size_t gb = group_bytes(q->g, fmt);
             {
                 std::lock_guard<std::mutex> lock(mu);
@@ -1364,11 +1411,38 @@ struct ServerImpl {
         {
             std::lock_guard<std::mutex> lock(mu);
             stats.queued_sum += (int64_t)queue.size();
-            while (!queue.empty()) {
-                SReq *q = queue.front();
+            // free group columns per (graph, format), counting the groups that may still be made
+            std::unordered_map<uint64_t, int> free_cols;
+            auto key_of = [](const SReq *q) { return (q->g->uid << 1) | (q->prec == PR_FP32 ? 0u : 1u); };
+            auto cols_of = [&](const SReq *q) -> int & {
+                const uint64_t key = key_of(q);
+                auto it = free_cols.find(key);
+                if (it != free_cols.end()) return it->second;
+                const int fmt = q->prec == PR_FP32 ? 0 : 1, K = group_columns(fmt);
+                int freec = 0, ng = 0;
+                for (const Group *G : groups)
+                    if (G->g == q->g && G->fmt == fmt) {
+                        ng++;
+                        freec += K - G->live();
+                    }
+                freec += std::max(0, PR_SERVER_MAX_GROUPS - ng) * K;
+                return free_cols.emplace(key, freec).first->second;
+            };
+            for (auto it = queue.begin(); it != queue.end();) {
+                SReq *q = *it;
                 const size_t need = layout(*q) + sizeof(double) * (size_t)q->g->G.n;
                 if (used + need > budget && (any_active() || !adm.empty())) break;
-                queue.pop_front();
+                // a request headed for a column group waits for a free column
+                const bool grouped = q->g->G.n_nd >= group_min_rows && inflight[q->g->uid] >= PR_GROUP_MIN_INFLIGHT;
+                if (grouped && (any_active() || !adm.empty())) {
+                    int &fc = cols_of(q);
+                    if (fc <= 0) {
+                        ++it;
+                        continue;
+                    }
+                    fc--;
+                }
+                it = queue.erase(it);
                 used += need;
                 adm.push_back(q);
             }

@@ -82,7 +82,7 @@ __device__ __forceinline__ void column_epilogue(const DevGraph &G, const ColPara
 // this lane's CPL columns summed over the in-list entries e = off[j] + slot,
 // + nslots, ... of row j, U entries in flight, in entry order
 template <typename T, int K, int U>
-__device__ __forceinline__ void slot_sum(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int j,
+__device__ __forceinline__ void slot_sum(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int nsrc, int j,
                                          const typename ST<T>::V *__restrict__ w, int part, int slot, int nslots,
                                          typename GT<typename ST<T>::V>::A *acc) {
     using V = typename ST<T>::V;
@@ -93,7 +93,7 @@ __device__ __forceinline__ void slot_sum(const int32_t *__restrict__ off, const 
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int ee = e + u * nslots;
-            idx[u] = ee < b ? __ldcs(&src[ee]) : -1;
+            idx[u] = ee < b ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -130,8 +130,8 @@ __device__ __forceinline__ void group_rows(const DevGraph &G, const Seg &S, int 
 #pragma unroll
         for (int c = 0; c < CPL; c++) acc[c] = GT<V>::zero();
         if (j < S.hi) {
-            slot_sum<T, K, U>(G.inr_off, G.inr_src, j, wprev, part, slot, NS, acc);
-            if (P.use_unref) slot_sum<T, K, U>(G.inu_off, G.inu_src, j, wprev, part, slot, NS, acc);
+            slot_sum<T, K, U>(G.inr_off, G.inr_src, G.n_nd, j, wprev, part, slot, NS, acc);
+            if (P.use_unref) slot_sum<T, K, U>(G.inu_off, G.inu_src, G.n_nd, j, wprev, part, slot, NS, acc);
         }
 #pragma unroll
         for (int o = L / 2; o >= LPE; o >>= 1)
@@ -216,9 +216,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_group_round(DevGraph G, Plan PL
                 A acc[CPL];
 #pragma unroll
                 for (int c = 0; c < CPL; c++) acc[c] = GT<V>::zero();
-                slot_sum<T, K, 4>(G.inr_off, G.inr_src, j, wprev, part, slot, kThreads / LPE, acc);
+                slot_sum<T, K, 4>(G.inr_off, G.inr_src, G.n_nd, j, wprev, part, slot, kThreads / LPE, acc);
                 if (P.use_unref)
-                    slot_sum<T, K, 4>(G.inu_off, G.inu_src, j, wprev, part, slot, kThreads / LPE, acc);
+                    slot_sum<T, K, 4>(G.inu_off, G.inu_src, G.n_nd, j, wprev, part, slot, kThreads / LPE, acc);
 #pragma unroll
                 for (int o = 16; o >= LPE; o >>= 1)
 #pragma unroll
@@ -422,4 +422,26 @@ pr_status group_extract(const pr_graph *g, const GroupDev &D, int fmt, int col, 
     return PR_OK;
 }
 
+}  // namespace pr
+
+namespace pr {
+// host side of the debug record of this translation unit (column groups)
+bool dbg_reset_group(int inject) {
+#ifdef PR_DEBUG
+    DbgRec z{};
+    z.inject = inject;
+    return cudaMemcpyToSymbol(g_pr_dbg, &z, sizeof(z)) == cudaSuccess;
+#else
+    (void)inject;
+    return false;
+#endif
+}
+bool dbg_read_group(DbgRec *out) {
+#ifdef PR_DEBUG
+    return cudaMemcpyFromSymbol(out, g_pr_dbg, sizeof(*out)) == cudaSuccess;
+#else
+    (void)out;
+    return false;
+#endif
+}
 }  // namespace pr

@@ -47,6 +47,7 @@
 
 #include <cmath>
 
+#include "pr_debug.cuh"
 #include "pr_internal.cuh"
 
 namespace pr {
@@ -54,6 +55,7 @@ namespace pr {
 enum { MODE_ACT = 0, MODE_PUSH = 1, MODE_PULL = 2 };
 constexpr int POLICY_LEVELS = 3;  // PR_MODE_LEVELS: level-ordered pull rounds
 constexpr int POLICY_ASYNC = 4;   // PR_MODE_ASYNC: push rounds that take r_i at push time
+constexpr int POLICY_APULL = 5;   // PR_MODE_APULL: pull rounds that recompute r_j from the reserves
 
 struct Ctl {
     // parameters (host-written per solve), in every format the kernels use
@@ -307,9 +309,16 @@ template <> struct ST<float2> {
 
 // |v| > xi_act, evaluated identically wherever an activation is decided.
 // FP32: xi_f is the largest float <= xi, so the test equals (double)|v| > xi.
+// FP64: non-negative doubles are ordered like their bit patterns, so |v| > xi
+// (xi >= 0) is an integer comparison, off the FP64 pipe.
 template <typename T> __device__ __forceinline__ bool is_active(T v, const Ctl *ctl) {
-    return ST<T>::gt(ST<T>::absv(v), ST<T>::xi(ctl));
+    if constexpr (std::is_same<T, double>::value) {
+        return (__double_as_longlong(v) & 0x7fffffffffffffffll) > __double_as_longlong(ctl->xi);
+    } else {
+        return ST<T>::gt(ST<T>::absv(v), ST<T>::xi(ctl));
+    }
 }
+
 
 // ------------------------------------------------------------ reductions
 template <typename V> __device__ __forceinline__ V warp_sum(V v) {
@@ -403,6 +412,14 @@ template <typename T> __device__ __forceinline__ void store_partial(double *slot
     memcpy(reinterpret_cast<char *>(slots) + 8 * (size_t)blockIdx.x, &v, 8);
 }
 
+// A gathered value: through the read-only (non-coherent) path when the array
+// is not written during the kernel (NC), else a plain load (asynchronous pull
+// rounds read values that other rows of the same launch update).
+template <bool NC, typename V> __device__ __forceinline__ V ldv(const V *p) {
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
 // Gathers of in-list sums.  A lane sums val[src[e]] over its entries
 // e = off[j] + start, + step, ... < off[j+1] strictly in that order (one
 // accumulator per row), so the result does not depend on how the loads are
@@ -410,39 +427,39 @@ template <typename T> __device__ __forceinline__ void store_partial(double *slot
 // stream from HBM once, evict-first), then the U gathered values (read-only
 // path; L2-resident in practice), so that U dependent load pairs per row are
 // in flight instead of one.
-template <typename V, int U>
-__device__ __forceinline__ void row_acc_u(const int32_t *__restrict__ src, const V *__restrict__ val, int &e, int b,
-                                          int step, typename GT<V>::A &acc) {
+template <typename V, int U, bool NC = true>
+__device__ __forceinline__ void row_acc_u(const int32_t *__restrict__ src, int nsrc, const V *__restrict__ val, int &e,
+                                          int b, int step, typename GT<V>::A &acc) {
     int idx[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int ee = e + u * step;
-        idx[u] = ee < b ? __ldcs(&src[ee]) : -1;
+        idx[u] = ee < b ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; u++)
-        if (idx[u] >= 0) acc = GT<V>::add(acc, __ldg(&val[idx[u]]));
+        if (idx[u] >= 0) acc = GT<V>::add(acc, ldv<NC>(&val[idx[u]]));
     e += U * step;
 }
 
 // one row, all of a block's threads (start = threadIdx.x, step = blockDim.x)
-template <typename V>
+template <typename V, bool NC = true>
 __device__ __forceinline__ typename GT<V>::A row_sum(const int32_t *__restrict__ off,
-                                                     const int32_t *__restrict__ src, int j,
+                                                     const int32_t *__restrict__ src, int nsrc, int j,
                                                      const V *__restrict__ val, int start, int step) {
     using A = typename GT<V>::A;
     const int b = __ldg(&off[j + 1]);
     int e = __ldg(&off[j]) + start;
     A acc = GT<V>::zero();
-    while (e < b) row_acc_u<V, 8>(src, val, e, b, step, acc);
+    while (e < b) row_acc_u<V, 8, NC>(src, nsrc, val, e, b, step, acc);
     return acc;
 }
 
 // The sums of ROWS rows at once (rows js[r], valid[r]), U entries per row per
 // step: the in-list entry loads and then the gathers of all rows are in flight
 // together.
-template <typename V, int ROWS, int U>
-__device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
+template <typename V, int ROWS, int U, bool NC = true>
+__device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src, int nsrc,
                                          const int *js, const bool *valid, const V *__restrict__ val, int start,
                                          int step, typename GT<V>::A *acc) {
     int e[ROWS], b[ROWS];
@@ -465,14 +482,14 @@ __device__ __forceinline__ void row_sums(const int32_t *__restrict__ off, const 
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int ee = e[r] + u * step;
-                idx[r][u] = ee < b[r] ? __ldcs(&src[ee]) : -1;
+                idx[r][u] = ee < b[r] ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
             }
         any = false;
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
 #pragma unroll
             for (int u = 0; u < U; u++)
-                if (idx[r][u] >= 0) acc[r] = GT<V>::add(acc[r], __ldg(&val[idx[r][u]]));
+                if (idx[r][u] >= 0) acc[r] = GT<V>::add(acc[r], ldv<NC>(&val[idx[r][u]]));
             e[r] += U * step;
             any |= e[r] < b[r];
         }
@@ -513,6 +530,12 @@ template <int LANES> struct EntriesInFlight {
 template <typename T> struct UseTiles {
     static constexpr bool value = PR_PULL_TILES && std::is_same<T, double>::value;
 };
+// rows per warp batch of the double-precision warp rows (see kWarpBatch), and
+// the shared doubles each warp parks their partials in
+#ifndef PR_WARP_BATCH
+#define PR_WARP_BATCH 4
+#endif
+constexpr int kWarpBatchPark = PR_WARP_BATCH * 9;
 // A tile's pending values (in-list order) and its rows' entry offsets relative
 // to the tile's first entry, in shared memory.
 template <typename V> struct TileSmem {
@@ -524,16 +547,32 @@ template <typename T> struct TileRows {
     T v[kTileRows];
 };
 
+// The shared memory of a double-precision segment: gather tiles, or the warp
+// rows' parked partials (a block serves one segment, so they never coexist).
+template <typename T, typename V> union SegSmem {
+    struct {
+        TileSmem<V> sm;
+        TileRows<T> rs;
+    } tile;
+    double park[(kThreads / 32) * kWarpBatchPark];
+};
+
 // Stages tile t: every thread first loads its kTileE / kThreads in-list
 // entries (coalesced, evict-first), then gathers their values (independent
 // loads), then the row offsets are copied.  Rows [ra, rb) of the tile.
-template <typename V, typename T = float>
+template <typename V, typename T = float, bool NC = true>
 __device__ __forceinline__ void tile_load(const DevGraph &G, int t, const V *__restrict__ val, TileSmem<V> &sm,
                                           int &ra, int &rb, const T *rowv = nullptr, TileRows<T> *rs = nullptr) {
     constexpr int U = kTileE / kThreads;
     constexpr int RU = (kTileRows + kThreads - 1) / kThreads;
     ra = __ldg(&G.tile_row[t]);
     rb = __ldg(&G.tile_row[t + 1]);
+#ifdef PR_DEBUG
+    if (ra < 0 || rb < ra || rb > G.n || rb - ra > kTileRows) {  // an empty tile: nothing is read
+        dbg_fail(DBG_TILE_ROW, ra, rb);
+        ra = rb = 0;
+    }
+#endif
     T pre[RU];
     if (rs) {  // the rows' state, in flight with the in-list loads and gathers below
 #pragma unroll
@@ -548,11 +587,11 @@ __device__ __forceinline__ void tile_load(const DevGraph &G, int t, const V *__r
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int k = (int)threadIdx.x + u * kThreads;
-        idx[u] = k < ne ? __ldcs(&G.inr_src[ea + k]) : -1;
+        idx[u] = k < ne ? PR_IDX(__ldcs(&G.inr_src[ea + k]), G.n_nd, DBG_IN_SRC) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; u++)
-        if (idx[u] >= 0) sm.val[threadIdx.x + u * kThreads] = __ldg(&val[idx[u]]);
+        if (idx[u] >= 0) sm.val[threadIdx.x + u * kThreads] = ldv<NC>(&val[idx[u]]);
     for (int i = threadIdx.x; i <= rb - ra; i += kThreads) sm.off[i] = __ldg(&G.inr_off[ra + i]) - ea;
     if (rs) {
 #pragma unroll
@@ -571,6 +610,90 @@ __device__ __forceinline__ typename GT<V>::A tile_row_sum(const TileSmem<V> &sm,
     const int e1 = sm.off[i + 1];
     for (int e = sm.off[i]; e < e1; e++) acc = GT<V>::add(acc, sm.val[e]);
     return acc;
+}
+
+// ------------------------------------------------------------ IEEE double warp rows
+// GB300's FP64 pipe takes as long for a warp instruction whatever lanes are
+// active (measured: one lane costs as much as 32).  A row served by a whole
+// warp pays each FP64 instruction of its lane reduction and of its epilogue
+// (run by one lane) for one row.  So double-precision warp rows go through in
+// batches of kWarpBatch rows per warp: every row's 32 lanes sum their entries
+// (lane l: entries l, l + 32, ... in order, kWarpU loads in flight), reduce to
+// 8 partials by two shuffle steps, and park them in shared memory; then lane k
+// adds the 8 partials of row k in a fixed tree and runs that row's epilogue,
+// so each FP64 instruction after the gather serves kWarpBatch rows.
+constexpr int kWarpBatch = PR_WARP_BATCH;  // 1 turns the batches off (shuffle-reduced lane bins)
+constexpr int kParkStride = 9;  // 8 partials + 1 pad per row (bank spread)
+constexpr int kParkPerWarp = kWarpBatch * kParkStride;
+static_assert(kParkPerWarp == kWarpBatchPark, "shared memory of the warp rows");
+static_assert(kWarpBatch <= 32, "a lane finishes each row of a batch");
+
+// lane's share of row j's sum: entries off[j] + lane, + 32, ... in order,
+// kWarpU of them per step.  The next step's in-list entries are loaded before
+// this step's values are added, so a busy FP64 pipe does not hold back the
+// loads; the adds of the last, partial step stop where the row ends (a
+// warp-uniform bound; lanes past the end add an exact 0.0).  Measured on
+// R-MAT scale 22, IEEE FP64 pull round: 0.254 ms with the shuffle-reduced
+// lane bins, 0.226 ms with batches of 4 rows, 0.207 ms with batches of 4 and
+// this pipelining (8 entries per step spill at the 40-register cap).
+constexpr int kWarpU = 4;
+template <bool NC = true>
+__device__ __forceinline__ double warp_row_part64(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
+                                                  int nsrc, int j, const double *__restrict__ val, int lane) {
+    const int b = __ldg(&off[j + 1]);
+    double acc = 0.0;
+    int base = __ldg(&off[j]);
+    int idx[kWarpU];
+#pragma unroll
+    for (int u = 0; u < kWarpU; u++) {
+        const int ee = base + lane + 32 * u;
+        idx[u] = ee < b ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
+    }
+    while (base < b) {
+        double v[kWarpU];
+#pragma unroll
+        for (int u = 0; u < kWarpU; u++) v[u] = idx[u] >= 0 ? ldv<NC>(&val[idx[u]]) : 0.0;
+        const int nu = min(kWarpU, (b - base + 31) >> 5);  // steps holding an entry of some lane
+        base += 32 * kWarpU;
+#pragma unroll
+        for (int u = 0; u < kWarpU; u++) {
+            const int ee = base + lane + 32 * u;
+            idx[u] = ee < b ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kWarpU; u++)
+            if (u < nu) acc += v[u];
+    }
+    return acc;
+}
+
+// The sums of rows j0 .. j0 + kWarpBatch - 1 (those below hi) by one warp: lane
+// k < kWarpBatch returns row j0 + k's sum.  off2/src2: an optional second
+// in-list segment, added to each lane's share before the reduction.
+template <bool NC = true>
+__device__ __forceinline__ double warp_batch_sums64(const int32_t *off, const int32_t *src, const int32_t *off2,
+                                                    const int32_t *src2, int nsrc, int j0, int hi, const double *val,
+                                                    double *park, int lane) {
+#pragma unroll 1
+    for (int k = 0; k < kWarpBatch; k++) {
+        const int j = j0 + k;
+        double a = 0.0;
+        if (j < hi) {  // warp-uniform
+            a = warp_row_part64<NC>(off, src, nsrc, j, val, lane);
+            if (off2) a += warp_row_part64<NC>(off2, src2, nsrc, j, val, lane);
+        }
+        a += __shfl_down_sync(0xffffffffu, a, 16);
+        a += __shfl_down_sync(0xffffffffu, a, 8);
+        if (lane < 8) park[k * kParkStride + lane] = a;
+    }
+    __syncwarp();
+    double s = 0.0;
+    if (lane < kWarpBatch) {
+        const double *p = park + lane * kParkStride;
+        s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    }
+    __syncwarp();  // park is rewritten by the next batch
+    return s;
 }
 
 // ------------------------------------------------------------ round decision
@@ -629,6 +752,7 @@ struct RoundBuf {
     void *w[2];          // ST<T>::V arrays; w[t & 1] written by the activation of round t
     int32_t *bins;
     double *din;         // [n] push-round inbox of double-float state (zero between rounds); else unused
+    PVals pv;            // asynchronous pull rounds: p at every row
 };
 
 // activation of one non-dangling vertex i with residual v (round t):
@@ -712,33 +836,42 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
     if (b < nb_thread) {
         const uint32_t c0 = cnt[0];
         for (uint32_t k = b * blockDim.x + threadIdx.x; k < c0; k += nb_thread * blockDim.x) {
-            const int i = bins[k];
+            const int i = PR_IDX(bins[k], n_nd, DBG_BIN);
+            if (i < 0) continue;
             const T v = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0; e < e1; e++) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
+            for (int e = e0; e < e1; e++) {
+                const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
+                if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
+            }
         }
     } else if (b < nb_thread + nb_warp) {
         const uint32_t c1 = cnt[1];
         const int lane = threadIdx.x & 31;
         const int wpb = blockDim.x >> 5;
         for (uint32_t k = (b - nb_thread) * wpb + (threadIdx.x >> 5); k < c1; k += nb_warp * wpb) {
-            const int i = bins[(size_t)n_nd + k];
+            const int i = PR_IDX(bins[(size_t)n_nd + k], n_nd, DBG_BIN);  // the same for the whole warp
+            if (i < 0) continue;
             T v = ST<T>::zero();
             if (lane == 0) v = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
             v = shfl0(v);
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + lane; e < e1; e += 32) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
+                if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
+            }
         }
     } else {
         const uint32_t c2 = cnt[2];
         const int nb_cta = gridDim.x - nb_thread - nb_warp;
         __shared__ T vsh;
         for (uint32_t k = b - nb_thread - nb_warp; k < c2; k += nb_cta) {
-            const int i = bins[(size_t)2 * n_nd + k];
+            const int i = PR_IDX(bins[(size_t)2 * n_nd + k], n_nd, DBG_BIN);  // the same for the whole block
+            if (i < 0) continue;
             if (threadIdx.x == 0) vsh = push_mass<T>(ctl, async, x, r, B.din, vbuf, i);
             __syncthreads();
             const T v = vsh;
@@ -746,7 +879,10 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) ST<T>::push_to(r, B.din, G.out_dst[e], wi);
+            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
+                if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
+            }
         }
     }
 }
@@ -783,10 +919,68 @@ __device__ __forceinline__ bool pull_row_epilogue(const DevGraph &G, const Ctl *
                                         El, ul);
 }
 
+// ------------------------------------------------------------ asynchronous pull rounds
+// PR_MODE_APULL (the asynchronous scans of Sec. 3.2, in pull form).  The state
+// is the reserve x and, per non-dangling source i, q_i = x_i / ((1-c) deg i)
+// (w[0], updated in place), with U_j = sum of q_i over j's unreferenced
+// in-neighbours (w[1]; they push once, in round 0).  A row recomputes what it
+// holds now from Eq. 4's identity,
+//   r_j = p_j + c (sum_{i in S(j), referenced} q_i + U_j) - x_j / (1-c),
+// which counts every push made so far -- this round's included, whenever the
+// source has committed before the gather reads it -- and never a push twice.
+// If |r_j| > xi_act it commits: x_j += (1-c) r_j, q_j follows, r_j = 0.  The
+// round's R is a bound on the residual the round leaves: what rows left
+// behind, plus c |r_j| ndeg_j / deg_j for every commit, whose pushes may have
+// reached their targets after those gathered.  IFP2's dangling rows are never
+// touched (phase 2 fills them); IFP1's get their residual at the end.
+template <typename T, bool IFP2>
+__device__ __forceinline__ bool apull_row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B, int j,
+                                                   T xj, T in, int &pd, typename ST<T>::R &Rl, long long &Fl,
+                                                   long long &El) {
+    using V = typename ST<T>::V;
+    static_assert(std::is_same<V, T>::value, "gathered values in the state's format");
+    T *x = static_cast<T *>(B.x);
+    T *r = static_cast<T *>(B.r);
+    V *q = static_cast<V *>(B.w[0]);
+    const V *U = static_cast<const V *>(B.w[1]);
+    const T inflow = ST<T>::mul(ST<T>::c(ctl), ST<T>::add(in, U[j]));
+    const T rj = ST<T>::add(ST<T>::add(ST<T>::p(ctl, B.pv, j), inflow), ST<T>::neg(ST<T>::mul(xj, ST<T>::inv_om(ctl))));
+    pd = IFP2 ? G.ndeg[j] : (G.out_off[j + 1] - G.out_off[j]);
+    if (is_active(rj, ctl)) {
+        const T xn = ST<T>::add(xj, ST<T>::mul(ST<T>::om(ctl), rj));
+        x[j] = xn;
+        r[j] = ST<T>::zero();
+        q[j] = ST<T>::mul(xn, ST<T>::mul(ST<T>::invdeg(G, j), ST<T>::inv_om(ctl)));
+        const T share = ST<T>::mul(ST<T>::c(ctl), ST<T>::mul(ST<T>::pack_from_d((double)G.ndeg[j]), ST<T>::invdeg(G, j)));
+        Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::mul(ST<T>::absv(rj), share)));
+        Fl++;
+        El += pd;
+        return true;
+    }
+    r[j] = rj;
+    Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(rj)));
+    return false;
+}
+
+// the epilogue of a gathered row: synchronous rounds (EPI 0) or asynchronous
+// pull rounds (EPI 1; pre = x_j, no frontier bins)
+template <typename T, bool IFP2, int EPI>
+__device__ __forceinline__ bool row_epilogue(const DevGraph &G, const Ctl *ctl, const RoundBuf &B,
+                                             typename ST<T>::V *wnext, int j, T pre, T in, int want, int &pd,
+                                             typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+    if constexpr (EPI == 0) return pull_row_epilogue_v<T, IFP2>(G, ctl, B, wnext, j, pre, in, want, pd, Rl, Fl, El, ul);
+    else return apull_row_epilogue<T, IFP2>(G, ctl, B, j, pre, in, pd, Rl, Fl, El);
+}
+// the row state an epilogue starts from: r_j (synchronous), x_j (asynchronous pull)
+template <typename T, int EPI>
+__device__ __forceinline__ const T *epi_state(const RoundBuf &B) {
+    return static_cast<const T *>(EPI == 0 ? B.r : B.x);
+}
+
 // Rows of a plan segment handled by groups of LANES threads, ROWS rows per
 // group at a time; the loop bound is uniform across the block so the
 // width-LANES shuffles always see full warps.
-template <typename T, bool IFP2, int LANES>
+template <typename T, bool IFP2, int LANES, int EPI = 0>
 __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
                                            const RoundBuf &B, const typename ST<T>::V *wprev,
                                            typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
@@ -806,10 +1000,12 @@ __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int 
             js[r] = base + r * stride + grp;
             valid[r] = js[r] < S.hi;
         }
-        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inr_off, G.inr_src, js, valid, wprev, lane, LANES, acc);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value, EPI == 0>(G.inr_off, G.inr_src, G.n_nd, js, valid, wprev, lane,
+                                                                   LANES, acc);
         if (use_unref) {
             A extra[ROWS];
-            row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inu_off, G.inu_src, js, valid, wprev, lane, LANES, extra);
+            row_sums<V, ROWS, EntriesInFlight<LANES>::value, EPI == 0>(G.inu_off, G.inu_src, G.n_nd, js, valid, wprev,
+                                                                       lane, LANES, extra);
 #pragma unroll
             for (int r = 0; r < ROWS; r++) acc[r] = GT<V>::add(acc[r], extra[r]);
         }
@@ -820,10 +1016,35 @@ __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int 
             bool act = false;
             int pd = 0;
             if (valid[r] && lane == 0)
-                act = pull_row_epilogue<T, IFP2>(G, ctl, B, wnext, js[r], ST<T>::from_acc(acc[r]), want, pd, Rl,
-                                                 Fl, El, ul);
+                act = row_epilogue<T, IFP2, EPI>(G, ctl, B, wnext, js[r], epi_state<T, EPI>(B)[js[r]],
+                                                 ST<T>::from_acc(acc[r]), want, pd, Rl, Fl, El, ul);
             if (want) bins_append(act, pd, js[r], bcnt, B.bins, G.n_nd);
         }
+    }
+}
+
+// Double-precision warp rows of a pull round's segment, in batches of
+// kWarpBatch rows per warp (batch i of the segment goes to warp i mod the
+// segment's warps); lane k finishes row k of a batch.
+template <bool IFP2, int EPI = 0>
+__device__ __forceinline__ void round_warp_rows64(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                                  const RoundBuf &B, const double *wprev, double *wnext,
+                                                  bool use_unref, int want, uint32_t *bcnt, double &Rl, long long &Fl,
+                                                  long long &El, int &ul, double *park) {
+    constexpr int WPB = kThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int nbatch = (S.hi - S.lo + kWarpBatch - 1) / kWarpBatch;
+    for (int bt = lb * WPB + (int)(threadIdx.x >> 5); bt < nbatch; bt += S.nblk * WPB) {
+        const int j0 = S.lo + bt * kWarpBatch;
+        const double sum = warp_batch_sums64<EPI == 0>(G.inr_off, G.inr_src, use_unref ? G.inu_off : nullptr, G.inu_src, G.n_nd, j0,
+                                             S.hi, wprev, park, lane);
+        const int j = j0 + lane;
+        bool act = false;
+        int pd = 0;
+        if (lane < kWarpBatch && j < S.hi)
+            act = row_epilogue<double, IFP2, EPI>(G, ctl, B, wnext, j, epi_state<double, EPI>(B)[j], sum, want, pd,
+                                                  Rl, Fl, El, ul);
+        if (want) bins_append(act, pd, j, bcnt, B.bins, G.n_nd);
     }
 }
 
@@ -831,18 +1052,17 @@ __device__ __forceinline__ void round_rows(const DevGraph &G, const Seg &S, int 
 // nblk, ...; one thread per row sums it from shared memory (plus the
 // unreferenced sources' segment from global memory while it can be nonzero)
 // and runs the row's epilogue.
-template <typename T, bool IFP2>
+template <typename T, bool IFP2, int EPI = 0>
 __device__ __forceinline__ void round_tiles(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
                                             const RoundBuf &B, const typename ST<T>::V *wprev,
                                             typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
-                                            typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul) {
+                                            typename ST<T>::R &Rl, long long &Fl, long long &El, int &ul,
+                                            TileSmem<typename ST<T>::V> &sm, TileRows<T> &rs) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    __shared__ TileSmem<V> sm;
-    __shared__ TileRows<T> rs;
     for (int t = S.t0 + lb; t < S.t0 + S.nt; t += S.nblk) {
         int ra, rb;
-        tile_load<V, T>(G, t, wprev, sm, ra, rb, static_cast<const T *>(B.r), &rs);
+        tile_load<V, T, EPI == 0>(G, t, wprev, sm, ra, rb, epi_state<T, EPI>(B), &rs);
         const int nrow = rb - ra;
         for (int base = 0; base < nrow; base += kThreads) {
             const int i = base + (int)threadIdx.x;
@@ -851,9 +1071,9 @@ __device__ __forceinline__ void round_tiles(const DevGraph &G, const Seg &S, int
             int pd = 0;
             if (i < nrow) {
                 A acc = tile_row_sum<V>(sm, i);
-                if (use_unref) acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, wprev, 0, 1));
-                act = pull_row_epilogue_v<T, IFP2>(G, ctl, B, wnext, j, rs.v[i], ST<T>::from_acc(acc), want, pd, Rl,
-                                                   Fl, El, ul);
+                if (use_unref) acc = GT<V>::add(acc, row_sum<V, EPI == 0>(G.inu_off, G.inu_src, G.n_nd, j, wprev, 0, 1));
+                act = row_epilogue<T, IFP2, EPI>(G, ctl, B, wnext, j, rs.v[i], ST<T>::from_acc(acc), want, pd, Rl,
+                                                 Fl, El, ul);
             }
             if (want) bins_append(act, pd, j, bcnt, B.bins, G.n_nd);
         }
@@ -863,7 +1083,7 @@ __device__ __forceinline__ void round_tiles(const DevGraph &G, const Seg &S, int
 
 // One segment (or tile) of a pull round: rows [S.lo, S.hi) with S.lanes threads per
 // row (0: the whole block per row); block lb of S.nblk.
-template <typename T, bool IFP2>
+template <typename T, bool IFP2, int EPI = 0>
 __device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
                                               const RoundBuf &B, const typename ST<T>::V *wprev,
                                               typename ST<T>::V *wnext, bool use_unref, int want, uint32_t *bcnt,
@@ -871,29 +1091,37 @@ __device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, i
                                               typename GT<typename ST<T>::V>::A *sha) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    if constexpr (UseTiles<T>::value) {
-        if (S.lanes == kTileLanes) {
-            round_tiles<T, IFP2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul);
+    if constexpr (std::is_same<T, double>::value) {
+        __shared__ SegSmem<T, V> smu;
+        if (UseTiles<T>::value && S.lanes == kTileLanes) {
+            round_tiles<T, IFP2, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul,
+                                      smu.tile.sm, smu.tile.rs);
+            return;
+        }
+        if (kWarpBatch > 1 && S.lanes == 32) {
+            round_warp_rows64<IFP2, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul,
+                                         smu.park + (threadIdx.x >> 5) * kParkPerWarp);
             return;
         }
     }
     switch (S.lanes) {
-        case 1: round_rows<T, IFP2, 1>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
-        case 2: round_rows<T, IFP2, 2>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
-        case 4: round_rows<T, IFP2, 4>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
-        case 8: round_rows<T, IFP2, 8>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
-        case 16: round_rows<T, IFP2, 16>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
-        case 32: round_rows<T, IFP2, 32>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 1: round_rows<T, IFP2, 1, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 2: round_rows<T, IFP2, 2, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 4: round_rows<T, IFP2, 4, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 8: round_rows<T, IFP2, 8, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 16: round_rows<T, IFP2, 16, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
+        case 32: round_rows<T, IFP2, 32, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul); break;
         default:  // one block per row
             for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
-                A acc = row_sum<V>(G.inr_off, G.inr_src, j, wprev, threadIdx.x, blockDim.x);
+                A acc = row_sum<V, EPI == 0>(G.inr_off, G.inr_src, G.n_nd, j, wprev, threadIdx.x, blockDim.x);
                 if (use_unref)
-                    acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, wprev, threadIdx.x, blockDim.x));
+                    acc = GT<V>::add(acc, row_sum<V, EPI == 0>(G.inu_off, G.inu_src, G.n_nd, j, wprev, threadIdx.x,
+                                                               blockDim.x));
                 acc = block_sum_gt<V>(acc, sha);
                 if (threadIdx.x == 0) {
                     int pd = 0;
-                    const bool act = pull_row_epilogue<T, IFP2>(G, ctl, B, wnext, j, ST<T>::from_acc(acc), want,
-                                                                pd, Rl, Fl, El, ul);
+                    const bool act = row_epilogue<T, IFP2, EPI>(G, ctl, B, wnext, j, epi_state<T, EPI>(B)[j],
+                                                                ST<T>::from_acc(acc), want, pd, Rl, Fl, El, ul);
                     if (want && act) {
                         const int bin = pd <= kWarpRowMin ? 0 : (pd <= kCtaRowMin ? 1 : 2);
                         const unsigned pos = atomicAdd(&bcnt[bin], 1u);
@@ -1027,6 +1255,146 @@ __global__ void __launch_bounds__(kThreads, PR_PULL_MIN_BLOCKS) k_round_pull(Dev
     if (threadIdx.x == 0) round_decision(ctl, t, Rsum, F, E, u, want, tr);
 }
 
+// ------------------------------------------------------------ asynchronous pull rounds
+// The decision after round t of PR_MODE_APULL (thread 0 of the last block):
+// R is the bound on the residual the round left, F and E its commits.
+__device__ __forceinline__ void apull_decision(Ctl *ctl, int t, double R, long long F, long long E, const Trace &tr) {
+    ctl->ticket = 0;
+    ctl->R = R;
+    ctl->F = F;
+    ctl->E = E;
+    if (t < ctl->trace_cap) {
+        tr.R[t] = R;
+        tr.F[t] = F;
+        tr.E[t] = E;
+        tr.mode[t] = (int8_t)MODE_PULL;
+    }
+    ctl->pushes += F;
+    ctl->edges_pushed += E;
+    if (t > 0) {
+        ctl->edges_scanned += ctl->scan_ref;
+        ctl->rounds_pull++;
+    }
+    ctl->cur = t;
+    ctl->round = t + 1;
+    ctl->mode = MODE_PULL;
+    if (R <= ctl->eps) {
+        ctl->done = 1;
+        ctl->status = 0;
+    } else if (F == 0) {
+        ctl->done = 1;
+        ctl->status = 2;
+    } else if (t + 1 >= ctl->max_rounds) {
+        ctl->done = 1;
+        ctl->status = 1;
+    }
+}
+
+// the block partials of R, F, E, and the last block's decision
+template <typename T>
+__device__ __forceinline__ void apull_reduce(Ctl *ctl, const Partials &P, const Trace &tr, int t,
+                                             typename ST<T>::R Rl, long long Fl, long long El,
+                                             typename ST<T>::R *shr, double *shd, long long *shl) {
+    using R = typename ST<T>::R;
+    const R Rb = block_sum_r<T>(Rl, shr);
+    const long long Fb = block_sum(Fl, shl);
+    const long long Eb = block_sum(El, shl);
+    if (threadIdx.x == 0) {
+        store_partial<T>(P.a, Rb);
+        P.F[blockIdx.x] = Fb;
+        P.E[blockIdx.x] = Eb;
+    }
+    if (!last_block(&ctl->ticket)) return;
+    const double Rsum = final_sum<T>(P.a, shd);
+    long long F = 0, E = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        F += __ldcg(&P.F[k]);
+        E += __ldcg(&P.E[k]);
+    }
+    F = block_sum(F, shl);
+    E = block_sum(E, shl);
+    if (threadIdx.x == 0) apull_decision(ctl, t, Rsum, F, E, tr);
+}
+
+// Round 0: every non-dangling vertex holds p_i and commits it if above xi_act;
+// q_i = x_i / ((1-c) deg i) for all of them (0 when nothing is committed).
+template <typename T, bool IFP2>
+__global__ void __launch_bounds__(kThreads) k_apull_init(DevGraph G, Ctl *ctl, Partials P, RoundBuf B, Trace tr) {
+    using R = typename ST<T>::R;
+    using V = typename ST<T>::V;
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    __shared__ R shr[32];
+    if (ctl->done) return;
+    T *x = static_cast<T *>(B.x);
+    T *r = static_cast<T *>(B.r);
+    V *q = static_cast<V *>(B.w[0]);
+    R Rl = ST<T>::rzero();
+    long long Fl = 0, El = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n_nd; i += gridDim.x * blockDim.x) {
+        const T v = r[i];
+        if (is_active(v, ctl)) {
+            const T xn = ST<T>::mul(ST<T>::om(ctl), v);
+            x[i] = xn;
+            r[i] = ST<T>::zero();
+            q[i] = ST<T>::mul(xn, ST<T>::mul(ST<T>::invdeg(G, i), ST<T>::inv_om(ctl)));
+            const T share = ST<T>::mul(ST<T>::c(ctl), ST<T>::mul(ST<T>::pack_from_d((double)G.ndeg[i]), ST<T>::invdeg(G, i)));
+            Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::mul(ST<T>::absv(v), share)));
+            Fl++;
+            El += IFP2 ? G.ndeg[i] : (G.out_off[i + 1] - G.out_off[i]);
+        } else {
+            q[i] = ST<T>::zero();
+            Rl = ST<T>::radd(Rl, ST<T>::rval(ST<T>::absv(v)));
+        }
+    }
+    apull_reduce<T>(ctl, P, tr, 0, Rl, Fl, El, shr, shd, shl);
+}
+
+// U_j = sum of q_i over the unreferenced in-neighbours of non-dangling row j:
+// they hold p and nothing else, commit in round 0 and never again.  A warp per
+// row, lanes in entry order, a fixed shuffle tree.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apull_unref(DevGraph G, RoundBuf B) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    const V *q = static_cast<const V *>(B.w[0]);
+    V *U = static_cast<V *>(B.w[1]);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < G.n_nd; j += warps) {
+        A acc = row_sum<V>(G.inu_off, G.inu_src, G.n_nd, j, q, lane, 32);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = GT<V>::add(acc, GT<V>::shfl_down(acc, o, 32));
+        if (lane == 0) U[j] = ST<T>::from_acc(acc);
+    }
+}
+
+// One asynchronous pull round over the non-dangling rows (the IFP2 plan): the
+// referenced in-neighbours' q by the plan's gathers, then apull_row_epilogue.
+template <typename T, bool IFP2>
+__global__ void __launch_bounds__(kThreads, PR_PULL_MIN_BLOCKS) k_round_apull(DevGraph G, Plan PL, Ctl *ctl, Partials P,
+                                                                             RoundBuf B, Trace tr) {
+    using V = typename ST<T>::V;
+    using A = typename GT<V>::A;
+    using R = typename ST<T>::R;
+    if (ctl->done) return;
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    __shared__ A sha[32];
+    __shared__ R shr[32];
+    const int t = ctl->round;
+    int s = 0;
+    while (s + 1 < PL.nseg && (int)blockIdx.x >= PL.seg[s + 1].blk0) s++;
+    const Seg S = PL.seg[s];
+    const int lb = blockIdx.x - S.blk0;
+    R Rl = ST<T>::rzero();
+    long long Fl = 0, El = 0;
+    int ul = 0;
+    round_segment<T, IFP2, 1>(G, S, lb, ctl, B, static_cast<const V *>(B.w[0]), nullptr, false, 0, nullptr, Rl, Fl,
+                              El, ul, sha);
+    apull_reduce<T>(ctl, P, tr, t, Rl, Fl, El, shr, shd, shl);
+}
+
 // ------------------------------------------------------------ level-ordered rounds (IFP2)
 // One launch serves one level's rows (plan of the level); the launches of a
 // round run in level order, the rows without in-edges last, and the last
@@ -1052,7 +1420,7 @@ struct LevelLaunch {
 // per row are in flight at once, as in row_sums.
 template <typename V, int ROWS, int U>
 __device__ __forceinline__ void level_row_sums(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
-                                               const int *js, const bool *valid, const V *__restrict__ wcur,
+                                               int nsrc, const int *js, const bool *valid, const V *__restrict__ wcur,
                                                const V *__restrict__ wprev, int split, bool both, int start,
                                                int step, typename GT<V>::A *acc) {
     int e[ROWS], b[ROWS];
@@ -1074,7 +1442,7 @@ __device__ __forceinline__ void level_row_sums(const int32_t *__restrict__ off, 
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int ee = e[r] + u * step;
-                idx[r][u] = ee < b[r] ? __ldcs(&src[ee]) : -1;
+                idx[r][u] = ee < b[r] ? PR_IDX(__ldcs(&src[ee]), nsrc, DBG_IN_SRC) : -1;
             }
         any = false;
 #pragma unroll
@@ -1154,9 +1522,9 @@ __device__ __forceinline__ void level_rows(const DevGraph &G, const Seg &S, int 
             valid[r] = js[r] < S.hi;
             acc[r] = GT<V>::zero();
         }
-        level_row_sums<V, ROWS, U>(G.inr_off, G.inr_src, js, valid, wcur, wprev, split, both, lane, LANES, acc);
+        level_row_sums<V, ROWS, U>(G.inr_off, G.inr_src, G.n_nd, js, valid, wcur, wprev, split, both, lane, LANES, acc);
         if (phase == 0)
-            level_row_sums<V, ROWS, U>(G.inu_off, G.inu_src, js, valid, wcur, wprev, split, both, lane, LANES, acc);
+            level_row_sums<V, ROWS, U>(G.inu_off, G.inu_src, G.n_nd, js, valid, wcur, wprev, split, both, lane, LANES, acc);
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
 #pragma unroll
@@ -1198,9 +1566,9 @@ __device__ __forceinline__ void level_cluster_row(const DevGraph &G, const Seg &
     const bool ok = j < S.hi;
     A acc = GT<V>::zero();
     const int start = rank * (int)blockDim.x + (int)threadIdx.x, step = kLevelCluster * (int)blockDim.x;
-    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, &j, &ok, wcur, wprev, split, phase == 1, start, step, &acc);
+    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, G.n_nd, &j, &ok, wcur, wprev, split, phase == 1, start, step, &acc);
     if (phase == 0)
-        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, &j, &ok, wcur, wprev, split, false, start, step, &acc);
+        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, G.n_nd, &j, &ok, wcur, wprev, split, false, start, step, &acc);
     acc = block_sum_gt<V>(acc, sha);
     if (threadIdx.x == 0) part = acc;
     cl.sync();
@@ -1340,10 +1708,10 @@ __global__ void __launch_bounds__(kThreads, PR_LEVEL_MIN_BLOCKS) k_round_levels(
                 for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
                     const bool ok = true;
                     A acc = GT<V>::zero();
-                    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, &j, &ok, wcur, wprev, split, phase == 1,
+                    level_row_sums<V, 1, 8>(G.inr_off, G.inr_src, G.n_nd, &j, &ok, wcur, wprev, split, phase == 1,
                                             threadIdx.x, blockDim.x, &acc);
                     if (phase == 0)
-                        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, &j, &ok, wcur, wprev, split, false,
+                        level_row_sums<V, 1, 8>(G.inu_off, G.inu_src, G.n_nd, &j, &ok, wcur, wprev, split, false,
                                                 threadIdx.x, blockDim.x, &acc);
                     acc = block_sum_gt<V>(acc, sha);
                     if (threadIdx.x == 0) {
@@ -1446,12 +1814,12 @@ __device__ __forceinline__ void sweep_epilogue_v(const DevGraph &G, const Ctl *c
         if (j < G.n_nd) a.q_next[j] = ST<T>::pack(ST<T>::mul(y, ST<T>::invdeg(G, j)));
     } else if constexpr (OP == OP_CORRECT) {
         // r = p + c P~ s - s with s = x / (1-c): the exact residual of the current
-        // reserve (for any s, (I - c P~)(y - s) = p + c P~ s - s, from Eq. 4), in IEEE
-        // double: the gathered values q_u = x_u / ((1-c) deg u), their sum and this
-        // epilogue.  1/(1-c) is applied as a multiply by its double reciprocal.
-        static_assert(std::is_same<T, double>::value, "the correction runs in IEEE double");
-        const double sj = pre * ctl->inv_om;
-        a.r[j] = (ST<double>::p(ctl, a.pv, j) + ctl->c * in) - sj;
+        // reserve (for any s, (I - c P~)(y - s) = p + c P~ s - s, from Eq. 4), from the
+        // gathered values q_u = x_u / ((1-c) deg u); 1/(1-c) is applied as a multiply by
+        // its reciprocal.  The FP32 form's correction runs it in IEEE double; the end of
+        // asynchronous pull rounds (IFP1) in the rounds' format.
+        const T sj = ST<T>::mul(pre, ST<T>::inv_om(ctl));
+        a.r[j] = ST<T>::add(ST<T>::add(ST<T>::p(ctl, a.pv, j), ST<T>::mul(ST<T>::c(ctl), in)), ST<T>::neg(sj));
     } else {  // OP_PHASE2: r_d = p_d + c sum_{u in S(d)} x_u / ((1-c) deg(u)); phase 1 never
               // touches a dangling residual, so r_d still holds p_d
         a.r[j] = ST<T>::add(pre, ST<T>::mul(ST<T>::c(ctl), in));
@@ -1483,8 +1851,8 @@ __device__ __forceinline__ void sweep_rows(const DevGraph &G, const Seg &S, int 
             js[r] = base + r * stride + grp;
             valid[r] = js[r] < S.hi;
         }
-        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inr_off, G.inr_src, js, valid, a.val, lane, LANES, acc);
-        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inu_off, G.inu_src, js, valid, a.val, lane, LANES, extra);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inr_off, G.inr_src, G.n_nd, js, valid, a.val, lane, LANES, acc);
+        row_sums<V, ROWS, EntriesInFlight<LANES>::value>(G.inu_off, G.inu_src, G.n_nd, js, valid, a.val, lane, LANES, extra);
 #pragma unroll
         for (int r = 0; r < ROWS; r++) {
             acc[r] = GT<V>::add(acc[r], extra[r]);
@@ -1498,11 +1866,10 @@ __device__ __forceinline__ void sweep_rows(const DevGraph &G, const Seg &S, int 
 // The gather tiles of a sweep's segment (see round_tiles)
 template <typename T, int OP>
 __device__ __forceinline__ void sweep_tiles(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl, SweepArgs<T> &a,
-                                            typename ST<T>::R &s1, typename ST<T>::R &s2, typename ST<T>::R &s3) {
+                                            typename ST<T>::R &s1, typename ST<T>::R &s2, typename ST<T>::R &s3,
+                                            TileSmem<typename ST<T>::V> &sm, TileRows<T> &rs) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    __shared__ TileSmem<V> sm;
-    __shared__ TileRows<T> rs;
     for (int t = S.t0 + lb; t < S.t0 + S.nt; t += S.nblk) {
         int ra, rb;
         tile_load<V, T>(G, t, a.val, sm, ra, rb, sweep_state_array<T, OP>(a), &rs);
@@ -1510,10 +1877,27 @@ __device__ __forceinline__ void sweep_tiles(const DevGraph &G, const Seg &S, int
         for (int i = threadIdx.x; i < nrow; i += kThreads) {
             const int j = ra + i;
             A acc = tile_row_sum<V>(sm, i);
-            acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, a.val, 0, 1));
+            acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, G.n_nd, j, a.val, 0, 1));
             sweep_epilogue_v<T, OP>(G, ctl, a, j, rs.v[i], ST<T>::from_acc(acc), s1, s2, s3);
         }
         __syncthreads();
+    }
+}
+
+// Double-precision warp rows of a sweep, in batches of kWarpBatch rows per
+// warp (see round_warp_rows64); both in-list segments are always read.
+template <int OP>
+__device__ __forceinline__ void sweep_warp_rows64(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
+                                                  SweepArgs<double> &a, double &s1, double &s2, double &s3,
+                                                  double *park) {
+    constexpr int WPB = kThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int nbatch = (S.hi - S.lo + kWarpBatch - 1) / kWarpBatch;
+    for (int bt = lb * WPB + (int)(threadIdx.x >> 5); bt < nbatch; bt += S.nblk * WPB) {
+        const int j0 = S.lo + bt * kWarpBatch;
+        const double sum = warp_batch_sums64(G.inr_off, G.inr_src, G.inu_off, G.inu_src, G.n_nd, j0, S.hi, a.val, park, lane);
+        const int j = j0 + lane;
+        if (lane < kWarpBatch && j < S.hi) sweep_epilogue<double, OP>(G, ctl, a, j, sum, s1, s2, s3);
     }
 }
 
@@ -1524,9 +1908,14 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
                                               typename ST<T>::R &s3, typename GT<typename ST<T>::V>::A *sha) {
     using V = typename ST<T>::V;
     using A = typename GT<V>::A;
-    if constexpr (UseTiles<T>::value) {
-        if (S.lanes == kTileLanes) {
-            sweep_tiles<T, OP>(G, S, lb, ctl, a, s1, s2, s3);
+    if constexpr (std::is_same<T, double>::value) {
+        __shared__ SegSmem<T, V> smu;
+        if (UseTiles<T>::value && S.lanes == kTileLanes) {
+            sweep_tiles<T, OP>(G, S, lb, ctl, a, s1, s2, s3, smu.tile.sm, smu.tile.rs);
+            return;
+        }
+        if (kWarpBatch > 1 && S.lanes == 32) {
+            sweep_warp_rows64<OP>(G, S, lb, ctl, a, s1, s2, s3, smu.park + (threadIdx.x >> 5) * kParkPerWarp);
             return;
         }
     }
@@ -1539,8 +1928,8 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
         case 32: sweep_rows<T, OP, 32>(G, S, lb, ctl, a, s1, s2, s3); break;
         default:
             for (int j = S.lo + lb; j < S.hi; j += S.nblk) {
-                A acc = row_sum<V>(G.inr_off, G.inr_src, j, a.val, threadIdx.x, blockDim.x);
-                acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, j, a.val, threadIdx.x, blockDim.x));
+                A acc = row_sum<V>(G.inr_off, G.inr_src, G.n_nd, j, a.val, threadIdx.x, blockDim.x);
+                acc = GT<V>::add(acc, row_sum<V>(G.inu_off, G.inu_src, G.n_nd, j, a.val, threadIdx.x, blockDim.x));
                 acc = block_sum_gt<V>(acc, sha);
                 if (threadIdx.x == 0) sweep_epilogue<T, OP>(G, ctl, a, j, ST<T>::from_acc(acc), s1, s2, s3);
             }

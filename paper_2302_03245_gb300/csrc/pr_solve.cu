@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "pr_kernels.cuh"
@@ -169,8 +171,105 @@ __global__ void k_dangling_mass(DevGraph G, Ctl *ctl, Partials P, const T *r) {
 template <typename T>
 __global__ void k_fin_write(DevGraph G, const Ctl *ctl, int kind, const T *x, const T *r, double *out) {
     const double inv = 1.0 / ctl->zsum;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n; i += gridDim.x * blockDim.x)
-        out[G.perm[i]] = ST<T>::to_d(zval<T>(G, ctl, kind, x, r, i)) * inv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n; i += gridDim.x * blockDim.x) {
+        const int c = PR_IDX(G.perm[i], G.n, DBG_PERM);
+        if (c >= 0) out[c] = ST<T>::to_d(zval<T>(G, ctl, kind, x, r, i)) * inv;
+    }
+}
+
+// ------------------------------------------------------------ debug-build invariants
+// After every round of a single solve (debug build), the state (x, r) must
+// satisfy what the rounds preserve (Sec. 3.1, Eq. 4, with the (1-c) reserve;
+// p sums to 1):
+//   mass      IFP1: sum x + sum r = 1.  IFP2: sum x + sum r + Delta = 1, where
+//             Delta = sum_i c x_i (deg_i - ndeg_i) / ((1-c) deg_i) is the mass
+//             pushed toward dangling vertices and deferred to phase 2;
+//   identity  r_j = p_j + c sum_{u in S~(j)} x_u / ((1-c) deg u) - x_j / (1-c),
+//             P~ = P (IFP1), P restricted to non-dangling targets (IFP2: a
+//             dangling r_j stays p_j).
+// Double-float state adds the push-round inbox to r.  One thread per row with a
+// serial in-list loop (small graphs only), FP64 atomics into acc[0] (mass) and
+// acc[1] (largest identity deviation relative to the row's magnitudes).
+#ifdef PR_DEBUG
+template <typename T>
+__global__ void k_dbg_invariants(DevGraph G, const Ctl *ctl, const T *x, const T *r, const double *din, PVals pv,
+                                 int ifp2, double *acc) {
+    const double c = ctl->c, om = ctl->one_minus_c;
+    double mass = 0.0, dev = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G.n; j += gridDim.x * blockDim.x) {
+        const double xj = ST<T>::to_d(x[j]);
+        const double rj = ST<T>::to_d(r[j]) + (din ? din[j] : 0.0);
+        const double pj = ST<double>::p(ctl, pv, j);
+        mass += xj + rj;
+        if (ifp2 && j < G.n_nd) {
+            const int deg = G.out_off[j + 1] - G.out_off[j];
+            mass += c * xj * (double)(deg - G.ndeg[j]) / (om * (double)deg);
+        }
+        double in = 0.0, mag = 0.0;
+        if (!ifp2 || j < G.n_nd) {
+            for (int pass = 0; pass < 2; pass++) {
+                const int32_t *off = pass ? G.inu_off : G.inr_off;
+                const int32_t *src = pass ? G.inu_src : G.inr_src;
+                for (int e = off[j]; e < off[j + 1]; e++) {
+                    const int u = PR_IDX(src[e], G.n_nd, DBG_IN_SRC);
+                    if (u >= 0) in += ST<T>::to_d(x[u]) * G.inv_deg64[u] / om;
+                }
+            }
+        }
+        const double want = (ifp2 && j >= G.n_nd) ? pj : pj + c * in - xj / om;
+        mag = fabs(pj) + c * in + xj / om + fabs(rj) + 1e-300;
+        dev = fmax(dev, fabs(rj - want) / mag);
+    }
+    atomicAdd(&acc[0], mass);
+    atomicMax(reinterpret_cast<unsigned long long *>(&acc[1]), (unsigned long long)__double_as_longlong(dev));
+}
+
+// the verdict on one round's sums (one thread): tolerances of the state's
+// arithmetic, then the accumulators are cleared for the next round
+__global__ void k_dbg_judge(double *acc, double tol_mass, double tol_identity) {
+    const double dm = fabs(acc[0] - 1.0), di = acc[1];
+    g_pr_dbg.checks++;
+    g_pr_dbg.max_mass_dev = fmax(g_pr_dbg.max_mass_dev, dm);
+    g_pr_dbg.max_identity_dev = fmax(g_pr_dbg.max_identity_dev, di);
+    const bool force = g_pr_dbg.inject == DBG_MASS;
+    if (dm > tol_mass || force) dbg_fail(DBG_MASS, (long long)(dm * 1e18), (long long)(tol_mass * 1e18));
+    if (di > tol_identity || g_pr_dbg.inject == DBG_IDENTITY)
+        dbg_fail(DBG_IDENTITY, (long long)(di * 1e18), (long long)(tol_identity * 1e18));
+    acc[0] = 0.0;
+    acc[1] = 0.0;
+}
+
+// tolerances per state format (p sums to 1; rounds of at most a few hundred)
+template <typename T> struct DbgTol;
+template <> struct DbgTol<double> {
+    static constexpr double mass = 1e-11, identity = 1e-11;
+};
+template <> struct DbgTol<float2> {
+    static constexpr double mass = 1e-10, identity = 1e-9;
+};
+template <> struct DbgTol<float> {
+    static constexpr double mass = 1e-4, identity = 1e-3;
+};
+#endif
+
+// host side of the debug record of this translation unit
+bool dbg_reset_solve(int inject) {
+#ifdef PR_DEBUG
+    DbgRec z{};
+    z.inject = inject;
+    return cudaMemcpyToSymbol(g_pr_dbg, &z, sizeof(z)) == cudaSuccess;
+#else
+    (void)inject;
+    return false;
+#endif
+}
+bool dbg_read_solve(DbgRec *out) {
+#ifdef PR_DEBUG
+    return cudaMemcpyFromSymbol(out, g_pr_dbg, sizeof(*out)) == cudaSuccess;
+#else
+    (void)out;
+    return false;
+#endif
 }
 
 // ------------------------------------------------------------ profiling
@@ -261,6 +360,7 @@ struct StateBufs {
 
 struct Workspace {
     Buf ctl, part, p64, p32, pdf, outbuf, pstage, pstage2, bins, tR, tF, tE, tM;
+    Buf dbg;                  // debug build: the invariant sums of a round (2 doubles)
     StateBufs s64, s32, sdf;  // FP64 (reference), FP32, double-float
     Ctl *hctl = nullptr;      // pinned host mirror
     int32_t trace_len = 0;
@@ -270,7 +370,7 @@ struct Workspace {
     struct CG {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-    } graphs[16];
+    } graphs[17];
     void drop_graphs() {
         for (auto &g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -346,6 +446,10 @@ static pr_status ensure_ws(pr_graph *g, pr_prec prec, int32_t trace_len) {
             PR_TRY(W->outbuf.alloc(sizeof(double) * n, s));
             PR_TRY(W->bins.alloc(sizeof(int32_t) * 3 * nnd, s));
             PR_CK(cudaMallocHost(&W->hctl, sizeof(Ctl)));
+#ifdef PR_DEBUG
+            PR_TRY(W->dbg.alloc(2 * sizeof(double), s));
+            PR_CK(cudaMemsetAsync(W->dbg.p, 0, 2 * sizeof(double), s));
+#endif
             PR_CK(cudaMemsetAsync(W->ctl.p, 0, sizeof(Ctl), s));
             PR_CK(cudaMemsetAsync(W->part.p, 0, W->part.bytes, s));
             return PR_OK;
@@ -403,6 +507,9 @@ template <typename T> static int power_key();
 template <> int power_key<float>() { return 10; }
 template <> int power_key<double>() { return 11; }
 template <> int power_key<float2>() { return 12; }
+template <typename T> static int apull_key();  // 2 per format (IFP1, IFP2)
+template <> int apull_key<double>() { return 13; }
+template <> int apull_key<float2>() { return 15; }
 
 // ------------------------------------------------------------ plans
 // The plans of a kernel instantiation: the tiled ones where its kernels carry
@@ -437,6 +544,12 @@ static void launch_round(pr_graph *g, Workspace &W, cudaStream_t s, Prof *prof) 
     k_push<T, IFP2><<<nbt + nbw + nbc, kThreads, 0, s>>>(G, ctl, B, nbt, nbw);
     const size_t e2 = prof ? prof->mark(s) : 0;
     k_activate<T, IFP2><<<grid_n(G.n_nd, sms, 8), kThreads, 0, s>>>(G, ctl, P, B, tr);
+#ifdef PR_DEBUG
+    k_dbg_invariants<T><<<grid_n(G.n, sms, 8), kThreads, 0, s>>>(G, ctl, static_cast<const T *>(B.x),
+                                                                 static_cast<const T *>(B.r), B.din, pvals_of(W),
+                                                                 IFP2 ? 1 : 0, W.dbg.as<double>());
+    k_dbg_judge<<<1, 1, 0, s>>>(W.dbg.as<double>(), DbgTol<T>::mass, DbgTol<T>::identity);
+#endif
     if (prof) {
         const size_t e3 = prof->mark(s);
         prof->add(PR_K_PULL, e0, e1);
@@ -703,6 +816,76 @@ static pr_status setup_p(pr_graph *g, Workspace &W, const pr_pvec *p, Ctl &h, do
     return PR_OK;
 }
 
+// ------------------------------------------------------------ asynchronous pull rounds
+// PR_MODE_APULL: round 0 (every vertex commits p), the unreferenced sources'
+// constant share U, then pull rounds until the stop flag, inside a CUDA-graph
+// while node (kUnroll rounds per body) or host-driven.
+template <typename T, bool IFP2>
+static pr_status run_apull(pr_graph *g, Workspace &W, bool use_graph, Prof *prof) {
+    const DevGraph &G = g->G;
+    cudaStream_t s = g->stream;
+    Ctl *ctl = W.ctl.as<Ctl>();
+    const Partials P = partials_of(W);
+    const Trace tr = trace_of(W);
+    RoundBuf B = round_bufs<T>(W);
+    B.pv = pvals_of(W);
+    const Plan &PL = plan_nd_of<T>(g);
+    const int sms = g->num_sms;
+    {
+        const size_t e0 = prof ? prof->mark(s) : 0;
+        k_apull_init<T, IFP2><<<grid_n(G.n_nd, sms, 8), kThreads, 0, s>>>(G, ctl, P, B, tr);
+        if (prof) prof->add(PR_K_ACTIVATE, e0, prof->mark(s));
+    }
+    k_apull_unref<T><<<grid_n((int64_t)G.n_nd * 32, sms, 8), kThreads, 0, s>>>(G, B);
+    auto round = [&](cudaStream_t cs, Prof *pf) {
+        const size_t e0 = pf ? pf->mark(cs) : 0;
+        k_round_apull<T, IFP2><<<PL.nblocks, kThreads, 0, cs>>>(G, PL, ctl, P, B, tr);
+        if (pf) pf->add(PR_K_PULL, e0, pf->mark(cs));
+    };
+    if (use_graph && !prof)
+        return while_graph(W, apull_key<T>() + (IFP2 ? 1 : 0), ctl, [&](cudaStream_t cs) {
+            for (int k = 0; k < kUnroll; k++) round(cs, nullptr);
+        }, s);
+    if (prof) {
+        prof->mode = MODE_ACT;
+        prof->next_round = 0;
+        prof->finished = false;
+    }
+    int chunk = 2;
+    std::vector<int8_t> modes;
+    for (;;) {
+        for (int k = 0; k < chunk; k++) round(s, prof);
+        PR_CK(cudaGetLastError());
+        PR_CK(cudaMemcpyAsync(&W.hctl->done, &ctl->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        const int done = W.hctl->done, last = W.hctl->round;
+        if (prof) {
+            const int hi = std::min(last, W.trace_len);
+            modes.assign(std::max(hi, 0), (int8_t)MODE_PULL);
+            prof->settle_rounds(modes, 0, last, done != 0);
+        }
+        if (done) break;
+        chunk = std::min(chunk * 2, 32);
+    }
+    return PR_OK;
+}
+
+// IFP1 after asynchronous pull rounds: the residual of every row, dangling ones
+// included, from the reserves (the rounds keep only what rows left behind)
+template <typename T>
+static void apull_final_residual(pr_graph *g, Workspace &W) {
+    using V = typename ST<T>::V;
+    StateBufs &S = state_of<T>(W);
+    SweepArgs<T> a{};
+    a.val = S.w[0].as<V>();
+    a.r = S.r.as<T>();
+    a.x = S.x.as<T>();
+    a.pv = pvals_of(W);
+    const Plan &PL = plan_all_of<T>(g);
+    k_sweep<T, OP_CORRECT><<<PL.nblocks, kThreads, 0, g->stream>>>(g->G, PL, W.ctl.as<Ctl>(), a);
+}
+
 // ------------------------------------------------------------ solve
 template <typename T>
 static pr_status ifp_phase1(pr_graph *g, Workspace &W, int algo, bool use_graph, bool levels, Prof *prof) {
@@ -770,8 +953,12 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
     if (opt.pull_ratio <= 0) opt.pull_ratio = g->pull_ratio;
-    if (opt.mode < 0 || opt.mode > PR_MODE_ASYNC) return fail(PR_EINVAL, "unknown mode");
+    if (opt.mode < 0 || opt.mode > PR_MODE_APULL) return fail(PR_EINVAL, "unknown mode");
     if (opt.mode == PR_MODE_ASYNC && algo == PR_POWER) return fail(PR_EINVAL, "PR_MODE_ASYNC runs IFP1 and IFP2");
+    const bool apull = opt.mode == PR_MODE_APULL;
+    if (apull && algo == PR_POWER) return fail(PR_EINVAL, "PR_MODE_APULL runs IFP1 and IFP2");
+    if (apull && prec == PR_FP32)
+        return fail(PR_EINVAL, "PR_MODE_APULL needs PR_FP64 or PR_DF64 (its recompute cancels to the state's precision)");
     const bool levels = opt.mode == PR_MODE_LEVELS;
     if (levels && algo != PR_IFP2) return fail(PR_EINVAL, "PR_MODE_LEVELS runs IFP2 only");
     if (levels && g->levels <= 0) return fail(PR_EINVAL, "PR_MODE_LEVELS needs a graph created with levels");
@@ -836,10 +1023,42 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         launches += (use_graph && !prof) ? bodies * (kUnroll * per_round + 1) : acts * per_round;
         return PR_OK;
     };
+    // asynchronous pull rounds: launches of round 0, the unreferenced share, the
+    // rounds (kUnroll per graph body) and the finish
+    auto apull_launches = [&]() -> pr_status {
+        PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        const int64_t rr = std::max(W.hctl->round - 1, 0);
+        launches += 2 + ((use_graph && !prof) ? ((rr + kUnroll - 1) / kUnroll + 1) * (kUnroll + 1) : rr);
+        return PR_OK;
+    };
     if (algo == PR_POWER) {
         if (prec == PR_FP64) PR_TRY(solve_power<double>(g, W, use_graph, prof, dout, launches));
         else if (prec == PR_FP32) PR_TRY(solve_power<float>(g, W, use_graph, prof, dout, launches));
         else PR_TRY(solve_power<float2>(g, W, use_graph, prof, dout, launches));
+    } else if (apull && prec == PR_FP64) {
+        k_init_state<double><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s64.x.as<double>(), W.s64.r.as<double>());
+        if (algo == PR_IFP2) PR_TRY((run_apull<double, true>(g, W, use_graph, prof)));
+        else PR_TRY((run_apull<double, false>(g, W, use_graph, prof)));
+        PR_TRY(apull_launches());
+        if (algo == PR_IFP1) {
+            apull_final_residual<double>(g, W);
+            launches += 1;
+        }
+        finish_ifp<double>(g, W, algo, dout, launches);
+        launches += 1;
+    } else if (apull) {  // double-float
+        PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
+        k_init_state<float2><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());
+        if (algo == PR_IFP2) PR_TRY((run_apull<float2, true>(g, W, use_graph, prof)));
+        else PR_TRY((run_apull<float2, false>(g, W, use_graph, prof)));
+        PR_TRY(apull_launches());
+        if (algo == PR_IFP1) {
+            apull_final_residual<float2>(g, W);
+            launches += 1;
+        }
+        finish_ifp<float2>(g, W, algo, dout, launches);
+        launches += 1;
     } else if (prec == PR_FP64) {
         k_init_state<double><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s64.x.as<double>(), W.s64.r.as<double>());
         PR_TRY(ifp_phase1<double>(g, W, algo, use_graph, levels, prof));
@@ -924,18 +1143,102 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     return PR_OK;
 }
 
+// ------------------------------------------------------------ debug record (host)
+// The records of the translation units are collected after every single and
+// batched solve into one report; pr_debug_inject names a site that the next
+// solves force to fail (a test of the net itself, with no invalid access).
+static std::mutex g_dbg_mu;
+static pr_debug_report g_dbg_acc{};
+static int g_dbg_inject = 0;
+
+static void dbg_merge(const DbgRec &d) {
+    g_dbg_acc.checks += (int64_t)d.checks;
+    if (d.fails && !g_dbg_acc.fails) {
+        g_dbg_acc.first_site = d.site;
+        g_dbg_acc.first_value = d.value;
+        g_dbg_acc.first_bound = d.bound;
+    }
+    g_dbg_acc.fails += (int64_t)d.fails;
+    g_dbg_acc.max_mass_dev = std::max(g_dbg_acc.max_mass_dev, d.max_mass_dev);
+    g_dbg_acc.max_identity_dev = std::max(g_dbg_acc.max_identity_dev, d.max_identity_dev);
+}
+
+void dbg_begin(cudaStream_t s) {
+#ifdef PR_DEBUG
+    cudaStreamSynchronize(s);
+    std::lock_guard<std::mutex> lock(g_dbg_mu);
+    dbg_reset_solve(g_dbg_inject);
+    dbg_reset_batch(g_dbg_inject);
+    dbg_reset_group(g_dbg_inject);
+#else
+    (void)s;
+#endif
+}
+
+pr_status dbg_end(cudaStream_t s, const char *what, pr_status st) {
+#ifdef PR_DEBUG
+    cudaStreamSynchronize(s);
+    DbgRec a{}, b{}, c{};
+    std::lock_guard<std::mutex> lock(g_dbg_mu);
+    dbg_read_solve(&a);
+    dbg_read_batch(&b);
+    dbg_read_group(&c);
+    dbg_merge(a);
+    dbg_merge(b);
+    dbg_merge(c);
+    const unsigned long long fails = a.fails + b.fails + c.fails;
+    if (fails) {
+        const DbgRec &f = a.fails ? a : (b.fails ? b : c);
+        return fail(PR_ECHECK, std::string(what) + ": debug check failed at site " + std::to_string(f.site) +
+                                   " (value " + std::to_string(f.value) + ", bound " + std::to_string(f.bound) +
+                                   "; " + std::to_string(fails) + " failures)");
+    }
+#else
+    (void)s;
+    (void)what;
+#endif
+    return st;
+}
+
 }  // namespace pr
 
 using namespace pr;
 
+extern "C" int pr_is_debug_build(void) {
+#ifdef PR_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" pr_status pr_debug_report_get(pr_debug_report *out, int reset) {
+    if (!out) return fail(PR_EINVAL, "pr_debug_report_get: out is NULL");
+    if (!pr_is_debug_build()) return fail(PR_EINVAL, "pr_debug_report_get: not a debug build (PR_DEBUG)");
+    std::lock_guard<std::mutex> lock(g_dbg_mu);
+    *out = g_dbg_acc;
+    if (reset) g_dbg_acc = pr_debug_report{};
+    return PR_OK;
+}
+
+extern "C" pr_status pr_debug_inject(int32_t site) {
+    if (!pr_is_debug_build()) return fail(PR_EINVAL, "pr_debug_inject: not a debug build (PR_DEBUG)");
+    if (site < 0) return fail(PR_EINVAL, "pr_debug_inject: site must be >= 0");
+    std::lock_guard<std::mutex> lock(g_dbg_mu);
+    g_dbg_inject = site;
+    return PR_OK;
+}
+
 extern "C" pr_status pr_solve_ex(pr_graph *g, double c, double eps, pr_algo a, pr_prec prec, const pr_pvec *p,
                                  const pr_opts *opts, double *out, int out_is_device, pr_stats *st) {
     if (!g) return fail(PR_EINVAL, "graph is NULL");
-    const pr_status s = solve_impl(g, c, eps, a, prec, p, opts, out, out_is_device, st);
+    dbg_begin(g->stream);
+    pr_status s = solve_impl(g, c, eps, a, prec, p, opts, out, out_is_device, st);
     if (s == PR_ECUDA) {
         cudaStreamSynchronize(g->stream);
         cudaGetLastError();
     }
+    if (s == PR_OK || s == PR_ENOTCONV) s = dbg_end(g->stream, "pr_solve", s);
     return s;
 }
 

@@ -62,6 +62,7 @@ int main(void){
  printf("%zu %zu %zu\n", offsetof(pr_stats, ms), offsetof(pr_opts, trace_mode), offsetof(pr_graph_info, device_bytes));
  printf("%zu %zu %zu %zu\n", sizeof(pr_tuning), offsetof(pr_tuning, pull_ratio), offsetof(pr_tuning, bin_rows), offsetof(pr_tuning, pull_blocks));
  printf("%zu %zu %zu\n", sizeof(pr_server_stats), offsetof(pr_server_stats, groups), offsetof(pr_server_stats, ms_finish));
+ printf("%zu %zu %zu\n", sizeof(pr_debug_report), offsetof(pr_debug_report, first_value), offsetof(pr_debug_report, max_identity_dev));
  return 0;}'''
     exe = os.path.join(ROOT, "tests", ".layout_probe")
     r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-x", "c", "-", "-o", exe], input=src,
@@ -81,6 +82,8 @@ int main(void){
                                                 T.pull_blocks.offset]
     S = prlib.pr_server_stats
     assert list(map(int, lines[3].split())) == [ctypes.sizeof(S), S.groups.offset, S.ms_finish.offset]
+    D = prlib.pr_debug_report
+    assert list(map(int, lines[4].split())) == [ctypes.sizeof(D), D.first_value.offset, D.max_identity_dev.offset]
 
 
 @pytest.mark.parametrize("case", ["dup_free_but_bad_offsets", "range", "negative_n", "off0", "offn"])
@@ -131,3 +134,14 @@ def test_output_arrays_checked_before_any_call(prlib):
         on_device(np.empty(4), 5)
     with pytest.raises(ValueError):
         on_device(torch.empty(4, dtype=torch.float64), 5)
+
+
+def test_release_build_has_no_debug_checks(prlib):
+    """libpr.so is the release build: the debug-build calls exist and refuse (no GPU needed)."""
+    L = prlib.lib()
+    if prlib.DEBUG:
+        pytest.skip("PR_LIBRARY=debug loads the debug build")
+    assert L.pr_is_debug_build() == 0
+    assert L.pr_debug_inject(1) == prlib.PR_EINVAL
+    rep = prlib.pr_debug_report()
+    assert L.pr_debug_report_get(ctypes.byref(rep), 0) == prlib.PR_EINVAL
