@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--serve-max", type=int, default=400, help="requests per rate at most")
     ap.add_argument("--algo", default="ifp2", choices=["ifp2", "ifp1", "power"],
                     help="algorithm of the timed steps (ifp2 = the headline)")
+    ap.add_argument("--apull", action="store_true",
+                    help="run the timed IFP steps in asynchronous pull rounds (PR_MODE_APULL) instead of the "
+                         "synchronous push/pull rounds (the headline)")
     ap.add_argument("--levels", type=int, default=0,
                     help="prepare the graph with this many levels and run the timed IFP2 steps in "
                          "level-ordered rounds (PR_MODE_LEVELS); 0 = synchronous rounds (the headline)")
@@ -92,13 +95,16 @@ PREC_LABEL = {"fp64": "IEEE FP64 (state, gathers and sums in double)",
               "fp32": "FP32 state and gathers, FP64 sums, IEEE FP64 correction sweep and rounds after it"}
 
 
-def workload(scale, algo="ifp2", levels=0, prec="fp64", eps=EPS_FP64):
+def workload(scale, algo="ifp2", levels=0, prec="fp64", eps=EPS_FP64, apull=False):
     lv = f"_levels{levels}" if levels and algo == "ifp2" else ""
-    return dict(workload=f"rmat{scale}_{algo}{lv}_{prec}", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
+    ap = "_apull" if apull and algo != "power" else ""
+    rounds = ("level-ordered, %d levels" % levels if lv else
+              "asynchronous pull (rows recompute their residual from the reserves)" if ap else "synchronous")
+    return dict(workload=f"rmat{scale}_{algo}{lv}{ap}_{prec}", graph="R-MAT (0.57,0.19,0.19,0.05)", scale=scale,
                 vertices=1 << scale, edge_factor=16, sampled_edges=16 << scale, dangling_deleted=0.20,
                 unref_deleted=0.10, relabel="seeded random permutation", seed=1, c=C, p="uniform",
                 algo=algo.upper() if algo != "power" else "Power", precision=PREC_LABEL[prec], eps=eps,
-                rounds="level-ordered, %d levels" % levels if lv else "synchronous")
+                rounds=rounds)
 
 
 def make_graph(scale):
@@ -329,6 +335,7 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
     if "k_round_pull" in prof:
         res["roofline"] = pull_roofline(G.info, st, prof["k_round_pull"]["ms"], 4, 8, st["fp64_rounds"], hbm_peak,
                                         peak_src)
+        res["roofline"]["traffic"] = recorded_traffic("k_round_pull", "rmat24_dag70_ifp2_fp32")
     # Power at equal L1, in the arithmetic of the IFP2 solve it is compared with; the
     # FP32 form (FP64 correction and finish) is compared with Power in FP64
     for pname, pprec, vs in (("fp64", pr.PR_FP64, "ifp2_fp64_auto"), ("df64", pr.PR_DF64, "ifp2_df64_auto"),
@@ -830,6 +837,8 @@ def main():
             opts.setdefault("use_graph", -1)
         if args.levels and algo == pr.PR_IFP2:
             opts.setdefault("mode", pr.PR_MODE_LEVELS)
+        if args.apull and algo != pr.PR_POWER:
+            opts.setdefault("mode", pr.PR_MODE_APULL)
         _, st, status = G.solve(C, eps, algo, prec, out=out, opts=opts)
         assert status == pr.PR_OK, st
         return st
@@ -871,7 +880,7 @@ def main():
             "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "df64", "fp32": "f32+f64"}[args.prec],
             "dtype_detail": PREC_LABEL[args.prec],
             "data": "synthetic",
-            "config": dict(workload(args.scale, args.algo, args.levels, args.prec, args.eps),
+            "config": dict(workload(args.scale, args.algo, args.levels, args.prec, args.eps, args.apull),
                            l2="512 MB buffer written between timed steps",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "gpu_launches": int(launches), "clocks": clk,
@@ -932,7 +941,7 @@ def main():
                         "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (copy bandwidth)",
                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                         "traffic": recorded_traffic(dom, workload(args.scale, args.algo, args.levels, args.prec,
-                                                                  args.eps)["workload"]),
+                                                                  args.eps, args.apull)["workload"]),
                         "timing": "CUDA events around every launch on the graph's stream, instrumented pass"}
     line["kernels"] = kernels
 

@@ -146,10 +146,7 @@ __device__ __forceinline__ void push_worker(const DevGraph &G, const Ctl *ctl, c
                 const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
                 const int e0 = G.out_off[i];
                 const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-                for (int e = e0 + lane; e < e1; e += lanes) {
-                    const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
-                    if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
-                }
+                push_list<T, IFP2>(G, r, B.din, e0, e1, wi, lane, lanes);
             }
         }
     }
@@ -526,8 +523,8 @@ static pr_status solve_batch_impl(pr_graph *const *gs, int32_t count, const doub
     pr_opts opt{};
     if (o) opt = *o;
     if (opt.max_rounds <= 0) opt.max_rounds = 100000;
-    if (opt.mode == PR_MODE_LEVELS || opt.mode == PR_MODE_ASYNC)
-        return fail(PR_EINVAL, "PR_MODE_LEVELS and PR_MODE_ASYNC run in pr_solve only");
+    if (opt.mode == PR_MODE_LEVELS || opt.mode == PR_MODE_ASYNC || opt.mode == PR_MODE_APULL)
+        return fail(PR_EINVAL, "PR_MODE_LEVELS, PR_MODE_ASYNC and PR_MODE_APULL run in pr_solve only");
     if (opt.mode < 0 || opt.mode > 2) return fail(PR_EINVAL, "unknown mode");
     for (int k = 0; k < count; k++) {
         if (!gs[k]) return fail(PR_EINVAL, "pr_solve_batch: graph " + std::to_string(k) + " is NULL");

@@ -814,6 +814,36 @@ __device__ __forceinline__ T push_mass(const Ctl *ctl, bool async, T *x, T *r, d
     return v;
 }
 
+// The pushes of one out-list [e0, e1) by `lanes` threads (this one is `lane`):
+// the entries up to the first multiple of 4 one by one, then four targets per
+// 16-byte load, then the tail.  (The push itself is an atomic read-modify-write
+// per target; the loads only feed it.)
+template <typename T, bool IFP2>
+__device__ __forceinline__ void push_list(const DevGraph &G, T *r, double *din, int e0, int e1, T wi, int lane,
+                                          int lanes) {
+    const int bound = IFP2 ? G.n_nd : G.n;
+    const int a = min(e1, (e0 + 3) & ~3);
+    for (int e = e0 + lane; e < a; e += lanes) {
+        const int t = PR_IDX(G.out_dst[e], bound, DBG_OUT_DST);
+        if (t >= 0) ST<T>::push_to(r, din, t, wi);
+    }
+    const int nv = (e1 - a) >> 2;
+    const int4 *v4 = reinterpret_cast<const int4 *>(G.out_dst + a);
+    for (int k = lane; k < nv; k += lanes) {
+        const int4 q = __ldcs(&v4[k]);
+        const int ts[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int t = PR_IDX(ts[u], bound, DBG_OUT_DST);
+            if (t >= 0) ST<T>::push_to(r, din, t, wi);
+        }
+    }
+    for (int e = a + 4 * nv + lane; e < e1; e += lanes) {
+        const int t = PR_IDX(G.out_dst[e], bound, DBG_OUT_DST);
+        if (t >= 0) ST<T>::push_to(r, din, t, wi);
+    }
+}
+
 __device__ __forceinline__ double shfl0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
 __device__ __forceinline__ float shfl0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
 __device__ __forceinline__ float2 shfl0(float2 v) {
@@ -860,10 +890,7 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + lane; e < e1; e += 32) {
-                const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
-                if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
-            }
+            push_list<T, IFP2>(G, r, B.din, e0, e1, wi, lane, 32);
         }
     } else {
         const uint32_t c2 = cnt[2];
@@ -879,10 +906,7 @@ __global__ void __launch_bounds__(kThreads) k_push(DevGraph G, const Ctl *ctl, R
             const T wi = ST<T>::mul(v, ST<T>::mul(cT, ST<T>::invdeg(G, i)));
             const int e0 = G.out_off[i];
             const int e1 = IFP2 ? e0 + G.ndeg[i] : G.out_off[i + 1];
-            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-                const int t = PR_IDX(G.out_dst[e], IFP2 ? n_nd : G.n, DBG_OUT_DST);
-                if (t >= 0) ST<T>::push_to(r, B.din, t, wi);
-            }
+            push_list<T, IFP2>(G, r, B.din, e0, e1, wi, threadIdx.x, blockDim.x);
         }
     }
 }

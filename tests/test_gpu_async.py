@@ -132,5 +132,5 @@ def test_async_refused_where_it_does_not_apply():
         with pytest.raises(pr.PrError) as e:
             pr.pr_solve_batch([G], C, 1e-8, pr.PR_IFP2, opts=dict(mode=pr.PR_MODE_ASYNC))
         assert e.value.status == pr.PR_EINVAL
-        _, _, s = G.solve(C, 1e-8, pr.PR_IFP2, opts=dict(mode=5), check=False)
+        _, _, s = G.solve(C, 1e-8, pr.PR_IFP2, opts=dict(mode=6), check=False)
         assert s == pr.PR_EINVAL
