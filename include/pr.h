@@ -232,6 +232,11 @@ pr_status pr_set_allocator(pr_alloc_fn alloc, pr_free_fn free_fn, void *ctx);
  * = m are checked on the host before the copy, the rest of the checks run on
  * the device on the copies before any kernel indexes by them, and if the
  * device fails before that (no device, no memory) they run on the host.
+ * Device memory: the graph itself through the allocator of pr_set_allocator
+ * (else cudaMalloc); the temporaries of the build (sort keys, about 16 bytes
+ * per edge) through that allocator too when one is installed, else from a
+ * stream-ordered pool of the library that keeps up to 2 GiB of them mapped
+ * for the next creation on the device.
  * Errors: PR_EINVAL (bad size, offsets, ids, duplicate edge, CSC mismatch;
  * reported ahead of any device error), PR_ENOMEM, PR_ECUDA.
  */

@@ -12,15 +12,16 @@
 //   * in-lists split into a "ref" segment (sources with in-edges) and an
 //     "unref" segment (unreferenced sources), both sorted.
 // Sorting uses CUB's device radix sort; everything else is hand-written.
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cstring>
 #include <thread>
 #include <vector>
 
 #include "pr_internal.cuh"
+#include "pr_sort.cuh"
 
 namespace pr {
 
@@ -134,9 +135,10 @@ static __global__ void k_indeg(int64_t m, const int32_t *dst, int32_t *indeg) {
 }
 
 // Level of every non-dangling vertex with in-edges (level-ordered rounds):
-// ranked by q = floor(2^31 (indeg + 1) / (indeg + outdeg + 2)), ascending,
-// ties by id (the key packs both); the others sort after them.
-static __global__ void k_level_keys(int32_t n, const int32_t *off, const int32_t *indeg, uint64_t *keys,
+// ranked by q = floor(2^31 (indeg + 1) / (indeg + outdeg + 2)) < 2^31,
+// ascending, ties by id (the key packs q << B | id); the others sort after
+// them (all ones in the 31 + B bits sorted).
+static __global__ void k_level_keys(int32_t n, const int32_t *off, const int32_t *indeg, int B, uint64_t *keys,
                                     unsigned int *n_ref) {
     __shared__ unsigned int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -146,7 +148,7 @@ static __global__ void k_level_keys(int32_t n, const int32_t *off, const int32_t
         const int64_t deg = off[i + 1] - off[i], id = indeg[i];
         if (deg > 0 && id > 0) {
             const uint64_t q = ((uint64_t)(id + 1) << 31) / (uint64_t)(id + deg + 2);
-            keys[i] = (q << 32) | (uint64_t)(uint32_t)i;
+            keys[i] = (q << B) | (uint64_t)(uint32_t)i;
             c++;
         } else {
             keys[i] = ~0ULL;
@@ -158,9 +160,10 @@ static __global__ void k_level_keys(int32_t n, const int32_t *off, const int32_t
 }
 
 // rank r of n_ref (sorted keys) -> level floor(r L / n_ref)
-static __global__ void k_assign_levels(const uint64_t *sorted, int32_t n_ref, int32_t L, int32_t *level) {
+static __global__ void k_assign_levels(const uint64_t *sorted, int32_t n_ref, int32_t L, int B, int32_t *level) {
+    const uint64_t id_mask = (1ULL << B) - 1;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_ref; r += gridDim.x * blockDim.x)
-        level[(int32_t)(sorted[r] & 0xFFFFFFFFu)] = (int32_t)(((int64_t)r * L) / n_ref);
+        level[(int32_t)(sorted[r] & id_mask)] = (int32_t)(((int64_t)r * L) / n_ref);
 }
 
 // valid out-edges of each non-dangling row into its own or a lower level (the
@@ -190,9 +193,13 @@ static __global__ void k_level_back(int32_t n_ref, int32_t n_nd, const int32_t *
     }
 }
 
-// class 0: deg>0 & indeg>0, class 1: deg>0 & indeg==0, class 2: deg==0
+// class 0: deg>0 & indeg>0, class 1: deg>0 & indeg==0, class 2: deg==0.
+// key = class << (LB + IB) | level << IB | (2^IB - 1 - indeg), with indeg <=
+// m < 2^IB and LB = 4 level bits on level-ordered graphs (else 0): a stable
+// sort on the low 2 + LB + IB bits orders by class, level, in-degree
+// descending, then id.
 static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_t *indeg, const int32_t *level,
-                                     uint64_t *keys, int32_t *vals, unsigned int *class_cnt) {
+                                     int IB, int LB, uint64_t *keys, int32_t *vals, unsigned int *class_cnt) {
     __shared__ unsigned int cnt[3];
     if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -203,7 +210,7 @@ static __global__ void k_vertex_keys(int32_t n, const int32_t *off, const int32_
         int32_t id = indeg[i];
         uint32_t cls = deg == 0 ? 2u : (id == 0 ? 1u : 0u);
         const uint64_t lev = (cls == 0 && level) ? (uint64_t)level[i] : 0;  // level-ordered graphs
-        keys[i] = ((uint64_t)cls << 40) | (lev << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
+        keys[i] = ((uint64_t)cls << (LB + IB)) | (lev << IB) | (((1ULL << IB) - 1) - (uint64_t)(uint32_t)id);
         vals[i] = i;
         local[cls]++;
     }
@@ -222,18 +229,28 @@ static __global__ void k_invert(int32_t n, const int32_t *perm, int32_t *inv) {
 // flag = (src >= n_ref): the source is unreferenced.  off/ent are caller
 // lists: row v holds the entries ent[off[v] .. off[v+1]), and row_is_src says
 // whether the row is the source end (out-lists) or the target end (in-lists).
+// With pos (the internal out-list offsets), entry e of row v is written to
+// pos[inv[v]] + (e - off[v]), which groups the keys by internal source;
+// without it, to index e.  With counts, the keys' digits of a radix sort on
+// bits [cbegin, cend) are counted on the way (radix_count_key).
+//
 // A warp takes chunks of 32 * kEdgeChunk consecutive entries, lane l the
-// entries base + l + 32 j; a lane finds the row of its first entry by binary
-// search and then walks forward through the offsets, so the row lookup costs
-// about one cached offset read per entry (a binary search per entry cost
-// 0.8 ms on 47M edges).  With pos (the internal out-list offsets), entry e of
-// row v is written to pos[inv[v]] + (e - off[v]), which groups the keys by
-// internal source; without it, to index e.  The offsets are validated before
-// this runs: off[0] = 0, non-decreasing, off[n] = m.
+// entries base + l + 32 j.  A lane finds the row of its first entry by binary
+// search and then walks forward through the offsets, about one cached offset
+// read per entry (a binary search per entry cost 0.8 ms on 47M edges); a walk
+// that passes more than kWalk rows (a run of empty rows) finishes by binary
+// search.  The offsets are validated before this runs: off[0] = 0,
+// non-decreasing, off[n] = m.
 constexpr int kEdgeChunk = 16;
+constexpr int kWalk = 4;
 static __global__ void k_edge_keys(int32_t n, int64_t m, const int32_t *off, const int32_t *ent,
                                    const int32_t *inv, int B, int32_t n_ref, int row_is_src,
-                                   const int32_t *pos, uint64_t *keys) {
+                                   const int32_t *pos, uint64_t *keys, int cbegin, int cend, uint32_t *counts) {
+    __shared__ uint32_t h[kRadixMaxPasses][kRadixDigits];
+    if (counts) {
+        for (int k = threadIdx.x; k < kRadixMaxPasses * kRadixDigits; k += blockDim.x) (&h[0][0])[k] = 0;
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -249,29 +266,62 @@ static __global__ void k_edge_keys(int32_t n, int64_t m, const int32_t *off, con
         }
         int32_t row = lo;
         for (int j = 0; j < kEdgeChunk && e < m; j++, e += 32) {
-            while ((int64_t)off[row + 1] <= e) row++;
+            for (int w = 0; (int64_t)off[row + 1] <= e; w++) {
+                if (w == kWalk) {  // off[row + 1] <= e < off[n]: search (row + 1, n)
+                    lo = row + 1;
+                    hi = n;
+                    while (hi - lo > 1) {
+                        const int32_t mid = lo + ((hi - lo) >> 1);
+                        if ((int64_t)off[mid] <= e) lo = mid;
+                        else hi = mid;
+                    }
+                    row = lo;
+                    break;
+                }
+                row++;
+            }
             const uint64_t r = (uint64_t)inv[row], c = (uint64_t)inv[ent[e]];
             const uint64_t src = row_is_src ? r : c, dst = row_is_src ? c : r;
             const uint64_t key = (src << (B + 1)) | ((src >= (uint64_t)n_ref ? 1ULL : 0ULL) << B) | dst;
             keys[pos ? (int64_t)pos[r] + (e - (int64_t)off[row]) : e] = key;
+            if (counts) radix_count_key(h, key, cbegin, cend);
         }
+    }
+    if (counts) {
+        __syncthreads();
+        radix_count_flush(h, cbegin, cend, counts);
     }
 }
 
-// deg[i] = out-degree of internal vertex i (caller vertex perm[i]); deg[n] = 0.
-// Its exclusive sum is the internal out-list offsets.
-static __global__ void k_new_degrees(int32_t n, const int32_t *off, const int32_t *perm, int32_t *deg) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
-        deg[i] = i < n ? off[perm[i] + 1] - off[perm[i]] : 0;
-}
-
-static __global__ void k_count_dups(int64_t m, const uint64_t *keys, unsigned long long *cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+// One pass over the keys sorted by (flag, dst, src): the source of entry e
+// goes to inr_src[e] (e < m_ref, referenced sources) or inu_src[e - m_ref];
+// each run of equal (flag, dst) adds its length to cnt[flag * (n + 1) + dst]
+// (its first entry adds -e, its last e + 1); equal neighbours are repeated
+// edges; the digits of the sort on the source bits [B+1, 2B+1) are counted
+// (radix_count_key).
+static __global__ void k_in_lists(int64_t m, const uint64_t *keys, int B, int32_t n, int64_t m_ref,
+                                  int32_t *inr_src, int32_t *inu_src, int32_t *cnt, unsigned long long *dups,
+                                  uint32_t *counts) {
+    __shared__ uint32_t h[kRadixMaxPasses][kRadixDigits];
+    for (int k = threadIdx.x; k < kRadixMaxPasses * kRadixDigits; k += blockDim.x) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const uint64_t low_mask = (1ULL << (B + 1)) - 1, id_mask = (1ULL << B) - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long c = 0;
-    for (int64_t e = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
-        c += keys[e] == keys[e - 1];
-    if (c) atomicAdd(cnt, c);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint64_t k = keys[e], f = k & low_mask;
+        const int32_t src = (int32_t)((k >> (B + 1)) & id_mask);
+        if (e < m_ref) inr_src[e] = src;
+        else inu_src[e - m_ref] = src;
+        int32_t *row = cnt + (int64_t)(f >> B) * (n + 1) + (int64_t)(f & id_mask);
+        if (e == 0 || (keys[e - 1] & low_mask) != f) atomicAdd(row, (int32_t)-e);
+        if (e + 1 == m || (keys[e + 1] & low_mask) != f) atomicAdd(row, (int32_t)(e + 1));
+        c += e > 0 && keys[e - 1] == k;
+        radix_count_key(h, k, B + 1, 2 * B + 1);
+    }
+    if (c) atomicAdd(dups, c);
+    __syncthreads();
+    radix_count_flush(h, B + 1, 2 * B + 1, counts);
 }
 
 // a field of every key: col[e] = (keys[e] >> shift) & mask
@@ -281,32 +331,20 @@ static __global__ void k_field(int64_t m, const uint64_t *keys, int shift, uint6
         col[e] = (int32_t)((keys[e] >> shift) & mask);
 }
 
-// keys[lo, hi) ordered by the field f(k) = (k >> shift) & mask:
-// off[r] = (first e in [lo, hi) with f(keys[e]) >= base + r) - lo, r in [0, n]
-static __global__ void k_row_offsets(int32_t n, const uint64_t *keys, int64_t lo, int64_t hi, uint64_t base,
-                                     int shift, uint64_t mask, int32_t *off) {
-    int stride = gridDim.x * blockDim.x;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += stride) {
-        const uint64_t target = base + (uint64_t)r;
-        int64_t a = lo, b = hi;
-        while (a < b) {
-            int64_t mid = a + ((b - a) >> 1);
-            if (((keys[mid] >> shift) & mask) < target) a = mid + 1;
-            else b = mid;
-        }
-        off[r] = (int32_t)(a - lo);
-    }
+// positions where two key arrays differ
+static __global__ void k_count_diff(int64_t m, const uint64_t *a, const uint64_t *b, unsigned long long *cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) c += a[e] != b[e];
+    if (c) atomicAdd(cnt, c);
 }
 
-// first index e with (keys[e] & mask) >= target, keys ordered by that field (single thread)
-static __global__ void k_lower_bound(const uint64_t *keys, int64_t m, uint64_t mask, uint64_t target, int64_t *out) {
-    int64_t a = 0, b = m;
-    while (a < b) {
-        int64_t mid = a + ((b - a) >> 1);
-        if ((keys[mid] & mask) < target) a = mid + 1;
-        else b = mid;
-    }
-    *out = a;
+// deg[i] = out-degree of internal vertex i (caller vertex perm[i]); deg[n] = 0.
+// Its exclusive sum is the internal out-list offsets.
+static __global__ void k_new_degrees(int32_t n, const int32_t *off, const int32_t *perm, int32_t *deg) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
+        deg[i] = i < n ? off[perm[i] + 1] - off[perm[i]] : 0;
 }
 
 static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const int32_t *dst,
@@ -329,9 +367,9 @@ static __global__ void k_vertex_arrays(int32_t n_nd, const int32_t *off, const i
     }
 }
 
-// internal in-degree (total, both in-list segments), m_d, n_u, max degrees (block-aggregated)
+// m_d, n_u and the maximum out- and in-degrees (block-aggregated)
 static __global__ void k_degree_facts(int32_t n, int32_t n_nd, const int32_t *perm, const int32_t *indeg_ext,
-                                      const int32_t *off_int, int32_t *indeg_int, unsigned int *n_u,
+                                      const int32_t *off_int, unsigned int *n_u,
                                       int *maxes, unsigned long long *m_d) {
     __shared__ unsigned int s_u;
     __shared__ int s_max[2];
@@ -349,7 +387,6 @@ static __global__ void k_degree_facts(int32_t n, int32_t n_nd, const int32_t *pe
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         int32_t id = indeg_ext[perm[i]];
         int32_t od = off_int[i + 1] - off_int[i];
-        indeg_int[i] = id;
         if (i >= n_nd) md += (unsigned long long)id;
         u += id == 0;
         mo = max(mo, od);
@@ -391,16 +428,6 @@ static __global__ void k_range_edges(const int32_t *inr_off, const int32_t *inu_
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nrows) return;
     edges[k] = (long long)inr_off[rows[k]] + inu_off[rows[k]];
-}
-
-// (hi << B | lo) -> (lo << B | hi)
-static __global__ void k_count_diff(int64_t m, const uint64_t *a, const uint64_t *b,
-                                    unsigned long long *cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long c = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
-        c += a[e] != b[e];
-    if (c) atomicAdd(cnt, c);
 }
 
 static int grid_for(int64_t items, int num_sms) {
@@ -870,30 +897,39 @@ static std::string check_host_lists(int32_t n, int64_t m, const int32_t *off, co
     return "";
 }
 
-namespace {
-// CUB helper that takes temporary storage from the library allocator
-struct Temp {
-    Buf b;
-    pr_status need(size_t bytes, cudaStream_t s) {
-        if (bytes <= b.bytes) return PR_OK;
-        return b.alloc(bytes, s);
-    }
-};
+static bool allocator_hooked() { return g_alloc != nullptr; }
 
-// Stable LSD radix sort of keys on bits [begin_bit, end_bit): keys equal in
-// those bits keep their order.
-pr_status sort_keys(Temp &tmp, uint64_t *&keys, uint64_t *&alt, int64_t m, int begin_bit, int end_bit,
-                    cudaStream_t s) {
-    if (m <= 1) return PR_OK;
-    cub::DoubleBuffer<uint64_t> db(keys, alt);
-    size_t bytes = 0;
-    PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, db, (int)m, begin_bit, end_bit, s));
-    PR_TRY(tmp.need(bytes, s));
-    PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, db, (int)m, begin_bit, end_bit, s));
-    if (db.Current() != keys) std::swap(keys, alt);
-    return PR_OK;
+// Temporaries of graph creation without an allocator hook: one stream-ordered
+// pool per device, owned by the library.  Freed temporaries are reused without
+// the device-wide synchronisation that cudaFree takes, and up to
+// kCreationCache bytes of them stay mapped for the next creation (mapping new
+// device memory is a large part of a creation's cost); above that the pool
+// returns memory at the stream synchronisations.
+constexpr uint64_t kCreationCache = 2ull << 30;
+static cudaMemPool_t creation_pool(int dev) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = kCreationCache;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
 }
 
+namespace {
 pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_t *out_dst,
                       const int32_t *in_off, const int32_t *in_src, int mem_is_device,
                       cudaStream_t s, int32_t levels, pr_graph *g) {
@@ -904,6 +940,11 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     g->device = dev;
     g->num_sms = sms;
     g->stream = s;
+    Scratch sc;  // the hook, when one is installed, serves the temporaries too
+    if (!allocator_hooked()) {
+        sc.pool = creation_pool(dev);
+        if (!sc.pool) return fail(PR_ECUDA, "cannot create the memory pool of graph creation");
+    }
     cudaEvent_t e0, e1;
     PR_CK(cudaEventCreate(&e0));
     PR_CK(cudaEventCreate(&e1));
@@ -913,15 +954,15 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     Buf c_off, c_dst, c_ioff, c_isrc;
     const int32_t *d_off = out_off, *d_dst = out_dst, *d_ioff = in_off, *d_isrc = in_src;
     if (!mem_is_device) {
-        PR_TRY(c_off.alloc(sizeof(int32_t) * (n + 1), s));
-        PR_TRY(c_dst.alloc(sizeof(int32_t) * m, s));
+        PR_TRY(sc.get(c_off, sizeof(int32_t) * (n + 1), s));
+        PR_TRY(sc.get(c_dst, sizeof(int32_t) * m, s));
         PR_CK(cudaMemcpyAsync(c_off.p, out_off, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
         if (m) PR_CK(cudaMemcpyAsync(c_dst.p, out_dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
         d_off = c_off.as<int32_t>();
         d_dst = c_dst.as<int32_t>();
         if (in_off) {
-            PR_TRY(c_ioff.alloc(sizeof(int32_t) * (n + 1), s));
-            PR_TRY(c_isrc.alloc(sizeof(int32_t) * m, s));
+            PR_TRY(sc.get(c_ioff, sizeof(int32_t) * (n + 1), s));
+            PR_TRY(sc.get(c_isrc, sizeof(int32_t) * m, s));
             PR_CK(cudaMemcpyAsync(c_ioff.p, in_off, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
             if (m) PR_CK(cudaMemcpyAsync(c_isrc.p, in_src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
             d_ioff = c_ioff.as<int32_t>();
@@ -930,7 +971,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     }
     // small device scratch: [0..1] validation, [2] dup count, [3] m_d, class counts, facts
     Buf scratch;
-    PR_TRY(scratch.alloc(256, s));
+    PR_TRY(sc.get(scratch, 256, s));
     PR_CK(cudaMemsetAsync(scratch.p, 0, 256, s));
     unsigned long long *bad = scratch.as<unsigned long long>();         // [0],[1]
     unsigned long long *dups = bad + 2;                                 // [2]
@@ -938,8 +979,15 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     unsigned int *class_cnt = reinterpret_cast<unsigned int *>(bad + 4);// 3 entries
     unsigned int *fact_cnt = class_cnt + 4;                             // 5 entries
     int *maxes = reinterpret_cast<int *>(fact_cnt + 6);                 // 2 entries
-    int64_t *lb = reinterpret_cast<int64_t *>(bad + 12);                // lower bounds
+    int *sort_err = reinterpret_cast<int *>(bad + 12);                  // radix_sort's flag
 
+    // waits for the stream; PR_ECUDA if a radix sort so far gave up (its output is incomplete)
+    auto sort_check = [&]() -> pr_status {
+        int h = 0;
+        PR_CK(cudaMemcpyAsync(&h, sort_err, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PR_CK(cudaStreamSynchronize(s));
+        return h ? fail(PR_ECUDA, "graph creation: a radix sort pass gave up waiting for an earlier tile") : PR_OK;
+    };
     const int gm = grid_for(std::max<int64_t>(m, n + 1), sms), gn = grid_for(n + 1, sms);
     {  // the caller's lists, on the device (host arrays: the copies), before any kernel indexes by them
         k_validate<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, bad);
@@ -953,52 +1001,46 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     const int B = bits_for(n);
     // degrees and classes
     Buf indeg;
-    PR_TRY(indeg.alloc(sizeof(int32_t) * n, s));
+    PR_TRY(sc.get(indeg, sizeof(int32_t) * n, s));
     PR_CK(cudaMemsetAsync(indeg.p, 0, sizeof(int32_t) * n, s));
     if (m) k_indeg<<<gm, kThreads, 0, s>>>(m, d_dst, indeg.as<int32_t>());
-    Buf vk, vk2, vv, vv2;
-    PR_TRY(vk.alloc(sizeof(uint64_t) * n, s));
-    PR_TRY(vk2.alloc(sizeof(uint64_t) * n, s));
-    PR_TRY(vv.alloc(sizeof(int32_t) * n, s));
-    PR_TRY(vv2.alloc(sizeof(int32_t) * n, s));
-    Temp tmp;
+    Buf vk, vk2, vv2;
+    PR_TRY(sc.get(vk, sizeof(uint64_t) * n, s));
+    PR_TRY(sc.get(vk2, sizeof(uint64_t) * n, s));
     Buf level;
     if (levels > 0) {  // levels of the referenced class (level-ordered rounds)
-        PR_TRY(level.alloc(sizeof(int32_t) * n, s));
+        PR_TRY(sc.get(level, sizeof(int32_t) * n, s));
         unsigned int *lvl_cnt = class_cnt + 3;
-        k_level_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), vk.as<uint64_t>(), lvl_cnt);
-        size_t bytes = 0;
-        PR_CK(cub::DeviceRadixSort::SortKeys(nullptr, bytes, vk.as<uint64_t>(), vk2.as<uint64_t>(), n, 0, 64, s));
-        PR_TRY(tmp.need(bytes, s));
-        PR_CK(cub::DeviceRadixSort::SortKeys(tmp.b.p, bytes, vk.as<uint64_t>(), vk2.as<uint64_t>(), n, 0, 64, s));
+        k_level_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), B, vk.as<uint64_t>(), lvl_cnt);
+        PR_TRY(radix_sort(vk.as<uint64_t>(), nullptr, n, 0, 31 + B, vk2.as<uint64_t>(), nullptr, nullptr, sort_err, sc,
+                          s));
         unsigned int h_ref = 0;
         PR_CK(cudaMemcpyAsync(&h_ref, lvl_cnt, sizeof(h_ref), cudaMemcpyDeviceToHost, s));
-        PR_CK(cudaStreamSynchronize(s));
+        PR_TRY(sort_check());
         if (h_ref)
-            k_assign_levels<<<grid_for(h_ref, sms), kThreads, 0, s>>>(vk2.as<uint64_t>(), (int32_t)h_ref, levels,
+            k_assign_levels<<<grid_for(h_ref, sms), kThreads, 0, s>>>(vk.as<uint64_t>(), (int32_t)h_ref, levels, B,
                                                                     level.as<int32_t>());
     }
-    k_vertex_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(), levels > 0 ? level.as<int32_t>() : nullptr,
-                                          vk.as<uint64_t>(), vv.as<int32_t>(), class_cnt);
+    // the renumbering: a stable sort of the vertex keys, carrying the ids
+    PR_TRY(g->perm.alloc(sizeof(int32_t) * n, s));
+    PR_TRY(sc.get(vv2, sizeof(int32_t) * n, s));
     {
-        cub::DoubleBuffer<uint64_t> dk(vk.as<uint64_t>(), vk2.as<uint64_t>());
-        cub::DoubleBuffer<int32_t> dv(vv.as<int32_t>(), vv2.as<int32_t>());
-        size_t bytes = 0;
-        PR_CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, dk, dv, n, 0, 42, s));
-        PR_TRY(tmp.need(bytes, s));
-        PR_CK(cub::DeviceRadixSort::SortPairs(tmp.b.p, bytes, dk, dv, n, 0, 42, s));
-        PR_TRY(g->perm.alloc(sizeof(int32_t) * n, s));
-        PR_CK(cudaMemcpyAsync(g->perm.p, dv.Current(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        const int IB = bits_for(m + 1), LB = levels > 0 ? 4 : 0;
+        k_vertex_keys<<<gn, kThreads, 0, s>>>(n, d_off, indeg.as<int32_t>(),
+                                              levels > 0 ? level.as<int32_t>() : nullptr, IB, LB, vk.as<uint64_t>(),
+                                              g->perm.as<int32_t>(), class_cnt);
+        PR_TRY(radix_sort(vk.as<uint64_t>(), g->perm.as<int32_t>(), n, 0, 2 + LB + IB, vk2.as<uint64_t>(),
+                          vv2.as<int32_t>(), nullptr, sort_err, sc, s));
     }
-    vk2.release();
-    vv.release();
-    vv2.release();
     vk.release();
-    PR_TRY(g->inv.alloc(sizeof(int32_t) * n, s));
-    k_invert<<<gn, kThreads, 0, s>>>(n, g->perm.as<int32_t>(), g->inv.as<int32_t>());
+    vk2.release();
+    vv2.release();
+    level.release();
     unsigned int hc[3];
     PR_CK(cudaMemcpyAsync(hc, class_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaStreamSynchronize(s));
+    PR_TRY(sort_check());  // perm is complete before anything indexes by it
+    PR_TRY(g->inv.alloc(sizeof(int32_t) * n, s));
+    k_invert<<<gn, kThreads, 0, s>>>(n, g->perm.as<int32_t>(), g->inv.as<int32_t>());
     const int32_t n_ref = (int32_t)hc[0], n_nd = (int32_t)(hc[0] + hc[1]);
     g->levels = levels;
     for (int l = 0; l <= levels; l++)  // level l holds the ranks [ceil(l n_ref / L), ceil((l+1) n_ref / L))
@@ -1016,62 +1058,71 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_TRY(g->out_dst.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
     {
         Buf deg;
-        PR_TRY(deg.alloc(sizeof(int32_t) * (n + 1), s));
+        PR_TRY(sc.get(deg, sizeof(int32_t) * (n + 1), s));
         k_new_degrees<<<gn, kThreads, 0, s>>>(n, d_off, g->perm.as<int32_t>(), deg.as<int32_t>());
-        size_t bytes = 0;
-        PR_CK(cub::DeviceScan::ExclusiveSum(nullptr, bytes, deg.as<int32_t>(), g->out_off.as<int32_t>(), n + 1, s));
-        PR_TRY(tmp.need(bytes, s));
-        PR_CK(cub::DeviceScan::ExclusiveSum(tmp.b.p, bytes, deg.as<int32_t>(), g->out_off.as<int32_t>(), n + 1, s));
+        PR_TRY(scan_i32(deg.as<int32_t>(), g->out_off.as<int32_t>(), n + 1, nullptr, sc, s));
     }
-    Buf ek, ek2;
-    PR_TRY(ek.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
-    PR_TRY(ek2.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    Buf ek, ek2, dc;
+    PR_TRY(sc.get(ek, sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    PR_TRY(sc.get(ek2, sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+    PR_TRY(sc.get(dc, sizeof(uint32_t) * 2 * kRadixMaxPasses * kRadixDigits, s));  // digit counts of the two sorts
+    PR_CK(cudaMemsetAsync(dc.p, 0, sizeof(uint32_t) * 2 * kRadixMaxPasses * kRadixDigits, s));
+    uint32_t *counts_in = dc.as<uint32_t>(), *counts_out = counts_in + kRadixMaxPasses * kRadixDigits;
     uint64_t *keys = ek.as<uint64_t>(), *alt = ek2.as<uint64_t>();
     if (m)
         k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_off, d_dst, g->inv.as<int32_t>(), B, n_ref, 1,
-                                            g->out_off.as<int32_t>(), keys);
-    // in-lists
-    PR_TRY(sort_keys(tmp, keys, alt, m, 0, B + 1, s));
-    if (m > 1) k_count_dups<<<gm, kThreads, 0, s>>>(m, keys, dups);  // a repeated edge is a repeated key
-    k_lower_bound<<<1, 1, 0, s>>>(keys, m, low_mask, 1ULL << B, lb);
-    int64_t m_ref = 0;
-    unsigned long long hdup = 0;
-    PR_CK(cudaMemcpyAsync(&m_ref, lb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaMemcpyAsync(&hdup, dups, sizeof(hdup), cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaStreamSynchronize(s));
-    if (hdup) return fail(PR_EINVAL, std::to_string(hdup) + " repeated edge(s): the adjacency is 0/1");
-    const int64_t m_unref = m - m_ref;
+                                            g->out_off.as<int32_t>(), keys, 0, B + 1, counts_in);
+    // in-lists: sorted by (flag, dst, src), the first m_ref keys are the
+    // edges from referenced sources (internal ids below n_ref: the first
+    // out_off[n_ref] out-list entries)
+    bool swapped = false;
+    PR_TRY(radix_sort(keys, nullptr, m, 0, B + 1, alt, nullptr, counts_in, sort_err, sc, s, &swapped));
+    if (swapped) std::swap(keys, alt);
+    int32_t h_mref = 0;
+    PR_CK(cudaMemcpyAsync(&h_mref, g->out_off.as<int32_t>() + n_ref, sizeof(h_mref), cudaMemcpyDeviceToHost, s));
+    PR_TRY(sort_check());  // the keys are complete before their fields index anything
+    const int64_t m_ref = h_mref, m_unref = m - m_ref;
     PR_TRY(g->inr_off.alloc(sizeof(int32_t) * (n + 1), s));
     PR_TRY(g->inu_off.alloc(sizeof(int32_t) * (n + 1), s));
     PR_TRY(g->inr_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_ref, 1), s));
     PR_TRY(g->inu_src.alloc(sizeof(int32_t) * std::max<int64_t>(m_unref, 1), s));
-    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, 0, m_ref, 0, 0, low_mask, g->inr_off.as<int32_t>());
-    k_row_offsets<<<gn, kThreads, 0, s>>>(n, keys, m_ref, m, 1ULL << B, 0, low_mask, g->inu_off.as<int32_t>());
-    if (m_ref) k_field<<<gm, kThreads, 0, s>>>(m_ref, keys, B + 1, id_mask, g->inr_src.as<int32_t>());
-    if (m_unref) k_field<<<gm, kThreads, 0, s>>>(m_unref, keys + m_ref, B + 1, id_mask, g->inu_src.as<int32_t>());
+    {
+        Buf cnt;
+        PR_TRY(sc.get(cnt, sizeof(int32_t) * 2 * (size_t)(n + 1), s));
+        PR_CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * 2 * (size_t)(n + 1), s));
+        int32_t *cnt_ref = cnt.as<int32_t>(), *cnt_unref = cnt_ref + (n + 1);
+        if (m)
+            k_in_lists<<<gm, kThreads, 0, s>>>(m, keys, B, n, m_ref, g->inr_src.as<int32_t>(),
+                                               g->inu_src.as<int32_t>(), cnt_ref, dups, counts_out);
+        PR_TRY(scan_i32(cnt_ref, g->inr_off.as<int32_t>(), n + 1, nullptr, sc, s));
+        PR_TRY(scan_i32(cnt_unref, g->inu_off.as<int32_t>(), n + 1, nullptr, sc, s));
+    }
     // out-lists (offsets from the scan above)
-    PR_TRY(sort_keys(tmp, keys, alt, m, B + 1, 2 * B + 1, s));
+    PR_TRY(radix_sort(keys, nullptr, m, B + 1, 2 * B + 1, alt, nullptr, counts_out, sort_err, sc, s, &swapped));
+    if (swapped) std::swap(keys, alt);
     if (m) k_field<<<gm, kThreads, 0, s>>>(m, keys, 0, id_mask, g->out_dst.as<int32_t>());
     // optional caller in-lists: the same edge set?  Their keys, sorted whole,
     // must equal the out-list keys, which are now in ascending order.
     if (d_ioff) {
         Buf ck;
-        PR_TRY(ck.alloc(sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
+        PR_TRY(sc.get(ck, sizeof(uint64_t) * std::max<int64_t>(m, 1), s));
         uint64_t *ckeys = ck.as<uint64_t>();
         if (m)
             k_edge_keys<<<gm, kThreads, 0, s>>>(n, m, d_ioff, d_isrc, g->inv.as<int32_t>(), B, n_ref, 0, nullptr,
-                                                ckeys);
-        uint64_t *calt = alt;  // the spare buffer of the sorts
-        PR_TRY(sort_keys(tmp, ckeys, calt, m, 0, 2 * B + 1, s));
+                                                ckeys, 0, 0, nullptr);
+        PR_TRY(radix_sort(ckeys, nullptr, m, 0, 2 * B + 1, alt, nullptr, nullptr, sort_err, sc, s, &swapped));
+        if (swapped) ckeys = alt;  // alt is free: the out-list keys are in keys
         if (m) k_count_diff<<<gm, kThreads, 0, s>>>(m, keys, ckeys, bad + 1);
         unsigned long long hb = 0;
         PR_CK(cudaMemcpyAsync(&hb, bad + 1, sizeof(hb), cudaMemcpyDeviceToHost, s));
-        PR_CK(cudaStreamSynchronize(s));
+        PR_TRY(sort_check());
         if (hb) return fail(PR_EINVAL, "in_off/in_src do not describe the same edges as out_off/out_dst");
     }
     ek.release();
     ek2.release();
-    tmp.b.release();
+    // the degree facts
+    k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, g->perm.as<int32_t>(), indeg.as<int32_t>(),
+                                           g->out_off.as<int32_t>(), fact_cnt, maxes, m_d);
     // per-vertex arrays
     PR_TRY(g->ndeg.alloc(sizeof(int32_t) * std::max(n_nd, 1), s));
     PR_TRY(g->inv_deg64.alloc(sizeof(double) * std::max(n_nd, 1), s));
@@ -1093,11 +1144,6 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
                                                                   g->gs_back.as<int32_t>());
         PR_CK(cudaStreamSynchronize(s));  // d_lo is freed at the end of this scope
     }
-    Buf indeg_int;
-    PR_TRY(indeg_int.alloc(sizeof(int32_t) * n, s));
-    k_degree_facts<<<gn, kThreads, 0, s>>>(n, n_nd, g->perm.as<int32_t>(), indeg.as<int32_t>(),
-                                           g->out_off.as<int32_t>(), indeg_int.as<int32_t>(), fact_cnt, maxes,
-                                           m_d);
     int32_t hnd[2] = {0, 0};
     PR_CK(cudaMemcpyAsync(&hnd[0], g->inr_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(&hnd[1], g->inu_off.as<int32_t>() + n_nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1107,7 +1153,10 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     PR_CK(cudaMemcpyAsync(&hu, fact_cnt, sizeof(hu), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
     PR_CK(cudaMemcpyAsync(&hmd, m_d, sizeof(hmd), cudaMemcpyDeviceToHost, s));
-    PR_CK(cudaStreamSynchronize(s));
+    unsigned long long hdup = 0;
+    PR_CK(cudaMemcpyAsync(&hdup, dups, sizeof(hdup), cudaMemcpyDeviceToHost, s));
+    PR_TRY(sort_check());
+    if (hdup) return fail(PR_EINVAL, std::to_string(hdup) + " repeated edge(s): the adjacency is 0/1");
 
     DevGraph &G = g->G;
     G.n = n;
@@ -1184,6 +1233,13 @@ extern "C" pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out
     G->uid = ++serial;
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
                                (cudaStream_t)cuda_stream, levels, G);
+    if (!allocator_hooked()) {  // keep at most kCreationCache bytes of freed temporaries mapped
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            if (cudaMemPool_t pool = creation_pool(dev)) cudaMemPoolTrimTo(pool, kCreationCache);
+        cudaGetLastError();
+    }
     if (st != PR_OK && st != PR_EINVAL && !mem_is_device) {
         // the device failed before it could check the lists (no device, no memory): check
         // host arrays here, so that invalid arguments are reported as such on any machine

@@ -3,15 +3,14 @@
 //   scan_i32       exclusive prefix sum of int32 counts (three passes: tile
 //                  sums, one block scans them, tiles add their base);
 //   radix_sort     stable LSD radix sort of 64-bit keys with optional int32
-//                  values, 8-bit digits: per tile a digit histogram, one scan
-//                  of all histograms (digit-major), then a stable scatter in
-//                  which every key's rank among equal digits of its tile comes
-//                  from warp matches and per-warp counts;
-//   sort_rows      each row of a CSR-like int32 array sorted ascending: rows
-//                  of up to kSmallRow entries by one thread (insertion sort),
-//                  longer rows by one block each (the same stable LSD scheme,
-//                  in place through a scratch copy of the row).
-// All three are deterministic: results do not depend on scheduling.
+//                  values, 8-bit digits: the digit counts of all passes from
+//                  one read of the keys, then one kernel per pass that orders
+//                  each tile by digit in shared memory (warp ballots and
+//                  per-warp counts give the ranks), finds the tile's global
+//                  offsets by decoupled look-back and writes every digit's run
+//                  of the tile as one contiguous piece.
+// The results do not depend on scheduling.
+
 #include <algorithm>
 
 #include "pr_internal.cuh"
@@ -22,8 +21,7 @@ namespace pr {
 namespace {
 
 constexpr int kScanTile = 2048;   // int32 per scan tile (256 threads x 8)
-constexpr int kSortTile = 2048;   // keys per radix tile (8 rounds of 256)
-constexpr int kDigits = 256;
+constexpr int kDigits = kRadixDigits;
 constexpr int kWarps = kThreads / 32;
 
 // exclusive block scan of one int per thread (block of kThreads); returns the
@@ -104,181 +102,236 @@ __global__ void __launch_bounds__(kThreads) k_scan_tiles(const int32_t *in, int6
 }
 
 // ------------------------------------------------------------ radix sort
+// Stable LSD radix sort with 8-bit digits, one kernel per digit pass (the
+// "one-sweep" arrangement): the digit counts of every pass come from one read
+// of the keys before the first pass; in a pass each tile ranks its keys in
+// shared memory and finds how many keys of each digit the tiles before it
+// hold by looking back through their published counts (decoupled look-back),
+// so no per-pass histogram kernel or scan is needed.
 __device__ __forceinline__ int digit_of(uint64_t k, int shift, int nbits) {
     return (int)((k >> shift) & ((1ull << nbits) - 1ull));
 }
 
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint64_t *keys, int64_t n, int shift, int nbits,
-                                                        int64_t ntiles, int32_t *hist) {
-    __shared__ int h[kDigits];
-    for (int d = threadIdx.x; d < kDigits; d += kThreads) h[d] = 0;
+constexpr int kMaxPasses = kRadixMaxPasses;
+// digit counts of every pass, one read of the keys
+__global__ void __launch_bounds__(kThreads) k_radix_counts(const uint64_t *keys, int64_t n, int begin_bit,
+                                                          int end_bit, uint32_t *counts) {
+    __shared__ uint32_t h[kMaxPasses][kDigits];
+    for (int k = threadIdx.x; k < kMaxPasses * kDigits; k += kThreads) (&h[0][0])[k] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int k = threadIdx.x; k < kSortTile; k += kThreads) {
-        const int64_t i = base + k;
-        if (i < n) atomicAdd(&h[digit_of(keys[i], shift, nbits)], 1);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        radix_count_key(h, keys[i], begin_bit, end_bit);
     __syncthreads();
-    for (int d = threadIdx.x; d < (1 << nbits); d += kThreads) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+    radix_count_flush(h, begin_bit, end_bit, counts);
 }
 
-// The stable scatter of one tile: the tile's keys in rounds of kThreads (key
-// r * kThreads + t is thread t's in round r); a key's destination is the
-// digit's global base for this tile + the keys of that digit in earlier
-// rounds + those of earlier warps in this round + those of earlier lanes of
-// its warp (a warp match).
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint64_t *keys, const int32_t *vals, int64_t n,
-                                                           int shift, int nbits, int64_t ntiles,
-                                                           const int32_t *offs, uint64_t *keys_out,
-                                                           int32_t *vals_out) {
-    __shared__ int run[kDigits];
-    __shared__ int wcnt[kWarps][kDigits];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kDigits; d += kThreads)
-        run[d] = d < (1 << nbits) ? offs[(int64_t)d * ntiles + blockIdx.x] : 0;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < kSortTile / kThreads; r++) {
-        for (int k = threadIdx.x; k < kWarps * kDigits; k += kThreads) (&wcnt[0][0])[k] = 0;
-        __syncthreads();
-        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
-        const bool ok = i < n;
-        const uint64_t key = ok ? keys[i] : 0;
-        const int d = ok ? digit_of(key, shift, nbits) : -1;
-        const unsigned same = __match_any_sync(0xffffffffu, d);
-        const int wrank = __popc(same & lt);
-        if (ok && wrank == 0) wcnt[wid][d] = __popc(same);
-        __syncthreads();
-        int before = 0;
-        if (ok)
-            for (int w = 0; w < wid; w++) before += wcnt[w][d];
-        const int pos = ok ? run[d] + before + wrank : 0;
-        __syncthreads();  // every thread has read run[] for this round
-        for (int dd = threadIdx.x; dd < kDigits; dd += kThreads) {
-            int t = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; w++) t += wcnt[w][dd];
-            run[dd] += t;
-        }
-        if (ok) {
-            keys_out[pos] = key;
-            if (vals) vals_out[pos] = vals[i];
-        }
-        __syncthreads();  // wcnt[] and run[] are read above before the next round rewrites them
-    }
-}
-
-// ------------------------------------------------------------ row sorts
-constexpr int kSmallRow = 32;
-
-// rows of at most kSmallRow entries: one thread each, insertion sort in place
-__global__ void k_rows_small(int32_t *data, const int32_t *off, int32_t nrows) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrows; j += gridDim.x * blockDim.x) {
-        const int a = off[j], b = off[j + 1];
-        if (b - a < 2 || b - a > kSmallRow) continue;
-        for (int e = a + 1; e < b; e++) {
-            const int32_t v = data[e];
-            int k = e - 1;
-            while (k >= a && data[k] > v) {
-                data[k + 1] = data[k];
-                k--;
-            }
-            data[k + 1] = v;
-        }
-    }
-}
-
-// rows above kSmallRow entries: flag (1) or not (0), for the compaction
-__global__ void k_rows_big_flag(const int32_t *off, int32_t nrows, int32_t *flag) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrows; j += gridDim.x * blockDim.x)
-        flag[j] = off[j + 1] - off[j] > kSmallRow;
-}
-
-__global__ void k_rows_big_list(const int32_t *flag, const int32_t *pos, int32_t nrows, int32_t *list) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrows; j += gridDim.x * blockDim.x)
-        if (flag[j]) list[pos[j]] = j;
-}
-
-// One block per long row: stable LSD radix sort of its entries (values in
-// [0, 2^bits)) by 8-bit digits, ping-ponging between the row and its place in
-// a scratch array of the same layout; an odd pass count ends with a copy back.
-__global__ void __launch_bounds__(kThreads) k_rows_big(int32_t *data, int32_t *scratch, const int32_t *off,
-                                                      const int32_t *list, const int32_t *count, int bits) {
-    __shared__ int hist[kDigits];
-    __shared__ int run[kDigits];
-    __shared__ int wcnt[kWarps][kDigits];
+// per pass (block p): exclusive sum over the digits, in place
+__global__ void __launch_bounds__(kThreads) k_radix_starts(uint32_t *counts) {
     __shared__ int sh[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int nbig = *count;
-    for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
-        const int j = list[q];
-        const int a = off[j], len = off[j + 1] - a;
-        int32_t *src = data + a, *dst = scratch + a;
-        int passes = 0;
-        for (int shift = 0; shift < bits; shift += 8, passes++) {
-            const int nb = bits - shift < 8 ? bits - shift : 8;
-            const int mask = (1 << nb) - 1;
-            for (int d = threadIdx.x; d < kDigits; d += kThreads) hist[d] = 0;
-            __syncthreads();
-            for (int e = threadIdx.x; e < len; e += kThreads) atomicAdd(&hist[(src[e] >> shift) & mask], 1);
-            __syncthreads();
-            int total;
-            const int ex = block_exscan(hist[threadIdx.x], sh, &total);  // kThreads == kDigits
-            run[threadIdx.x] = ex;
-            for (int r = 0; r * kThreads < len; r++) {
-                for (int k = threadIdx.x; k < kWarps * kDigits; k += kThreads) (&wcnt[0][0])[k] = 0;
-                __syncthreads();
-                const int e = r * kThreads + threadIdx.x;
-                const bool ok = e < len;
-                const int32_t v = ok ? src[e] : 0;
-                const int d = ok ? (v >> shift) & mask : -1;
-                const unsigned same = __match_any_sync(0xffffffffu, d);
-                const int wrank = __popc(same & lt);
-                if (ok && wrank == 0) wcnt[wid][d] = __popc(same);
-                __syncthreads();
-                int before = 0;
-                if (ok)
-                    for (int w = 0; w < wid; w++) before += wcnt[w][d];
-                const int pos = ok ? run[d] + before + wrank : 0;
-                __syncthreads();
-                {
-                    int t = 0;
-#pragma unroll
-                    for (int w = 0; w < kWarps; w++) t += wcnt[w][threadIdx.x];
-                    run[threadIdx.x] += t;
-                }
-                if (ok) dst[pos] = v;
-                __syncthreads();  // wcnt[] and run[] are read above before the next round rewrites them
-            }
-            __syncthreads();
-            int32_t *t = src;
-            src = dst;
-            dst = t;
-        }
-        if (passes & 1)  // the sorted row is in the scratch array
-            for (int e = threadIdx.x; e < len; e += kThreads) data[a + e] = scratch[a + e];
-        __syncthreads();
-    }
+    uint32_t *c = counts + (size_t)blockIdx.x * kDigits;
+    int total;
+    const int ex = block_exscan((int)c[threadIdx.x], sh, &total);
+    c[threadIdx.x] = (uint32_t)ex;
 }
 
-int grid_of(int64_t items, int sms, int per_sm = 8) {
-    const int64_t b = (items + kThreads - 1) / kThreads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sms * per_sm));
+// A tile's published count of one digit: bits [0, 32) the count, bit 32 set
+// when the count is the tile's own (aggregate), bit 33 when it includes every
+// earlier tile (inclusive), bits [40, 48) the pass it belongs to (so the
+// words of the previous pass read as not yet published).
+constexpr unsigned long long kStAgg = 1ull << 32, kStIncl = 1ull << 33;
+constexpr int kSpinLimit = 1 << 20;  // look-back polls without progress before a tile gives up
+constexpr int kLookBack = 8;         // status words read per look-back step
+constexpr int kMatchEvery = 3;       // ranking rounds that use the warp match instruction (0: none)
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v) {
+    *(volatile unsigned long long *)p = v;
+}
+
+// One digit pass over tiles of R * kThreads keys.  A block takes the next
+// tile number from a counter (so every earlier tile belongs to a block that
+// has already started) and ranks the tile's keys: warp w holds the keys
+// w * R * 32 + r * 32 + lane in registers and, in order of r, ranks each among
+// the equal digits of its segment (the lanes with equal digits come from one
+// ballot per digit bit; one of them reads and advances the warp's running
+// count of the digit).  The warps' counts, summed per digit in warp order, and
+// a block scan over the digits give the tile's own digit-sorted order.  Thread
+// d publishes the tile's count of digit d, looks back through the earlier
+// tiles' words until it meets an inclusive one, and publishes its inclusive
+// count.  The keys, placed in the tile's order in shared memory, then go out
+// with consecutive threads writing consecutive keys, so each digit's run of
+// the tile is one contiguous piece.  A look-back that polls kSpinLimit times
+// without progress sets *err and the tile writes nothing.
+template <int R, bool VALS>
+__global__ void __launch_bounds__(kThreads, 3) k_radix_pass(const uint64_t *keys, const int32_t *vals, int64_t n,
+                                                        int shift, int nbits, const uint32_t *starts,
+                                                        unsigned long long *status, int epoch,
+                                                        unsigned int *tile_ctr, int *err, uint64_t *keys_out,
+                                                        int32_t *vals_out) {
+    constexpr int T = R * kThreads;
+    __shared__ uint64_t skeys[T];
+    __shared__ int32_t svals[VALS ? T : 1];
+    __shared__ int whist[kWarps][kDigits];
+    __shared__ int lstart[kDigits];
+    __shared__ int64_t gbase[kDigits];
+    __shared__ int sh[32];
+    __shared__ unsigned int s_tile;
+    __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(tile_ctr, 1u);
+        s_bad = 0;
+    }
+    for (int k = threadIdx.x; k < kWarps * kDigits; k += kThreads) (&whist[0][0])[k] = 0;
+    __syncthreads();
+    const unsigned int t = s_tile;
+    const int64_t base = (int64_t)t * T;
+    uint64_t key[R];
+    int dig[R], rank[R];
+    int32_t val[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t i = base + wid * (R * 32) + r * 32 + lane;
+        const bool ok = i < n;
+        key[r] = ok ? keys[i] : 0;
+        dig[r] = ok ? digit_of(key[r], shift, nbits) : -1;
+        if (VALS) val[r] = ok ? vals[i] : 0;
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    const bool full = base + T <= n;  // every key of the tile is valid (all tiles but the last)
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int d = dig[r];
+        // The lanes holding the same digit.  Rounds r with r % kMatchEvery == 0
+        // take the warp match instruction, the others one ballot per digit bit:
+        // the two run on different pipes, so mixing them spreads the load.
+        unsigned same;
+        if (kMatchEvery > 0 && r % kMatchEvery == 0) {
+            same = __match_any_sync(0xffffffffu, d);
+        } else {
+            same = full ? 0xffffffffu : ~(__ballot_sync(0xffffffffu, d < 0) ^ (d < 0 ? 0xffffffffu : 0u));
+#pragma unroll
+            for (int b = 0; b < 8; b++) {  // digits above nbits are 0 on every lane
+                const unsigned m = 0u - ((unsigned)(d >> b) & 1u);
+                same &= ~(__ballot_sync(0xffffffffu, m != 0) ^ m);
+            }
+        }
+        const int leader = __ffs(same) - 1;
+        int before = 0;
+        if (d >= 0 && lane == leader) {  // one lane per digit reads and advances the warp's count
+            before = whist[wid][d];
+            whist[wid][d] = before + __popc(same);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[r] = before + __popc(same & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    {  // thread d = digit d
+        const int d = threadIdx.x;
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
+            const int c = whist[w][d];
+            whist[w][d] = tot;
+            tot += c;
+        }
+        int total;
+        lstart[d] = block_exscan(tot, sh, &total);
+        const unsigned long long E = (unsigned long long)(epoch & 0xFF) << 40;
+        unsigned long long *mine = status + (size_t)t * kDigits + d;
+        uint32_t excl = 0;
+        if (t == 0) {
+            st_status(mine, E | kStIncl | (uint32_t)tot);
+        } else {
+            st_status(mine, E | kStAgg | (uint32_t)tot);
+            // Look back kLookBack words at a time (independent loads); tile 0
+            // always publishes an inclusive word, so the walk ends there at the
+            // latest.
+            int64_t j = (int64_t)t - 1;
+            int spins = 0;
+            bool ok = true;
+            while (true) {
+                unsigned long long v[kLookBack];
+#pragma unroll
+                for (int w = 0; w < kLookBack; w++) v[w] = j - w >= 0 ? ld_status(status + (size_t)(j - w) * kDigits + d) : 0;
+                int used = 0;
+                bool incl = false;
+#pragma unroll
+                for (int w = 0; w < kLookBack; w++) {
+                    if (used < w || incl) break;  // an earlier word was not ready, or the walk is over
+                    if (((v[w] >> 40) & 0xFF) != (unsigned long long)(epoch & 0xFF) || !(v[w] & (kStAgg | kStIncl)))
+                        break;
+                    excl += (uint32_t)v[w];
+                    used++;
+                    incl = (v[w] & kStIncl) != 0;
+                }
+                if (incl) break;
+                j -= used;
+                if (used == 0) {
+                    if (++spins >= kSpinLimit) {
+                        ok = false;
+                        s_bad = 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            // (a tile that gave up leaves its aggregate: later tiles look past it)
+            if (ok) st_status(mine, E | kStIncl | (uint32_t)(excl + (uint32_t)tot));
+        }
+        gbase[d] = (int64_t)starts[d] + excl;
+    }
+    __syncthreads();
+    if (s_bad) {  // every thread sees the same flag after the barrier
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int d = dig[r];
+        if (d < 0) continue;
+        const int pos = lstart[d] + whist[wid][d] + rank[r];
+        skeys[pos] = key[r];
+        if (VALS) svals[pos] = val[r];
+    }
+    __syncthreads();
+    const int cnt = (int)(n - base < T ? n - base : T);
+    if (cnt == T) {  // a full tile: independent iterations, unrolled
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int p = r * kThreads + threadIdx.x;
+            const uint64_t k = skeys[p];
+            const int d = digit_of(k, shift, nbits);
+            const int64_t g = gbase[d] + (p - lstart[d]);
+            keys_out[g] = k;
+            if (VALS) vals_out[g] = svals[p];
+        }
+    } else {
+        for (int p = threadIdx.x; p < cnt; p += kThreads) {
+            const uint64_t k = skeys[p];
+            const int d = digit_of(k, shift, nbits);
+            const int64_t g = gbase[d] + (p - lstart[d]);
+            keys_out[g] = k;
+            if (VALS) vals_out[g] = svals[p];
+        }
+    }
 }
 
 }  // namespace
 
 static_assert(kThreads == kDigits, "the block scans of the sorts give one digit per thread");
 
-pr_status scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, cudaStream_t s) {
+pr_status scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, const Scratch &sc, cudaStream_t s) {
     if (n <= 0) {
         if (total) PR_CK(cudaMemsetAsync(total, 0, sizeof(int32_t), s));
         return PR_OK;
     }
     const int64_t nt = (n + kScanTile - 1) / kScanTile;
     Buf sums;
-    PR_TRY(sums.alloc(sizeof(int32_t) * nt, s));
+    PR_TRY(sc.get(sums, sizeof(int32_t) * nt, s));
     k_scan_tile_sums<<<(unsigned)nt, kThreads, 0, s>>>(in, n, sums.as<int32_t>());
     k_scan_sums<<<1, kThreads, 0, s>>>(sums.as<int32_t>(), nt, total);
     k_scan_tiles<<<(unsigned)nt, kThreads, 0, s>>>(in, n, sums.as<int32_t>(), out);
@@ -287,50 +340,57 @@ pr_status scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, c
 }
 
 pr_status radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int begin_bit, int end_bit, uint64_t *keys_alt,
-                     int32_t *vals_alt, cudaStream_t s) {
+                     int32_t *vals_alt, uint32_t *counts, int *err, const Scratch &sc, cudaStream_t s,
+                     bool *in_alt) {
+    if (in_alt) *in_alt = false;
     if (n <= 1 || end_bit <= begin_bit) return PR_OK;
     if (n > INT32_MAX) return fail(PR_EINVAL, "radix_sort: more than 2^31 keys");
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    Buf hist;
-    PR_TRY(hist.alloc(sizeof(int32_t) * kDigits * ntiles, s));
+    const int npass = (end_bit - begin_bit + 7) / 8;
+    if (npass > kMaxPasses) return fail(PR_EINVAL, "radix_sort: more than 64 bits");
+    // keys only: 16 per thread; with values: 8 (shared memory)
+    const int T = (vals ? 8 : 16) * kThreads;
+    const int64_t ntiles = (n + T - 1) / T;
+    Buf own, status;
+    PR_TRY(sc.get(own, sizeof(uint32_t) * (kMaxPasses * kDigits + kMaxPasses), s));
+    PR_TRY(sc.get(status, sizeof(unsigned long long) * kDigits * ntiles, s));
+    unsigned int *ctr = own.as<uint32_t>() + kMaxPasses * kDigits;
+    PR_CK(cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * kMaxPasses, s));
+    PR_CK(cudaMemsetAsync(status.p, 0, sizeof(unsigned long long) * kDigits * ntiles, s));
+    uint32_t *cnt = counts;
+    if (!cnt) {
+        cnt = own.as<uint32_t>();
+        PR_CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * kMaxPasses * kDigits, s));
+        int dev = 0, sms = 0;
+        PR_CK(cudaGetDevice(&dev));
+        PR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t cg = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)sms * 4);
+        k_radix_counts<<<(unsigned)cg, kThreads, 0, s>>>(keys, n, begin_bit, end_bit, cnt);
+    }
+    k_radix_starts<<<npass, kThreads, 0, s>>>(cnt);
     uint64_t *ka = keys, *kb = keys_alt;
     int32_t *va = vals, *vb = vals_alt;
-    int passes = 0;
-    for (int shift = begin_bit; shift < end_bit; shift += 8, passes++) {
+    for (int p = 0; p < npass; p++) {
+        const int shift = begin_bit + 8 * p;
         const int nb = std::min(8, end_bit - shift);
-        const int64_t nh = ((int64_t)1 << nb) * ntiles;
-        k_radix_hist<<<(unsigned)ntiles, kThreads, 0, s>>>(ka, n, shift, nb, ntiles, hist.as<int32_t>());
-        PR_TRY(scan_i32(hist.as<int32_t>(), hist.as<int32_t>(), nh, nullptr, s));
-        k_radix_scatter<<<(unsigned)ntiles, kThreads, 0, s>>>(ka, va, n, shift, nb, ntiles, hist.as<int32_t>(), kb,
-                                                             vb);
+        unsigned long long *st = status.as<unsigned long long>();
+        // the pass number tags the status words, so one zeroing serves every pass
+        if (vals)
+            k_radix_pass<8, true><<<(unsigned)ntiles, kThreads, 0, s>>>(ka, va, n, shift, nb, cnt + p * kDigits, st,
+                                                                       p + 1, ctr + p, err, kb, vb);
+        else
+            k_radix_pass<16, false><<<(unsigned)ntiles, kThreads, 0, s>>>(ka, nullptr, n, shift, nb,
+                                                                         cnt + p * kDigits, st, p + 1, ctr + p, err,
+                                                                         kb, nullptr);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
-    if (passes & 1) {  // the result is in the alternate buffers
+    if ((npass & 1) && in_alt && !vals) {  // the caller takes the result from keys_alt
+        *in_alt = true;
+    } else if (npass & 1) {  // the result is in the alternate buffers
         PR_CK(cudaMemcpyAsync(keys, keys_alt, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
         if (vals) PR_CK(cudaMemcpyAsync(vals, vals_alt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
     PR_CK(cudaGetLastError());
-    return PR_OK;
-}
-
-pr_status sort_rows(int32_t *data, const int32_t *off, int32_t nrows, int64_t m, int bits, int sms, cudaStream_t s) {
-    if (nrows <= 0 || m <= 1) return PR_OK;
-    k_rows_small<<<grid_of(nrows, sms), kThreads, 0, s>>>(data, off, nrows);
-    Buf flag, pos, list, scratch, cnt;
-    PR_TRY(flag.alloc(sizeof(int32_t) * nrows, s));
-    PR_TRY(pos.alloc(sizeof(int32_t) * nrows, s));
-    PR_TRY(list.alloc(sizeof(int32_t) * nrows, s));
-    PR_TRY(cnt.alloc(sizeof(int32_t), s));
-    k_rows_big_flag<<<grid_of(nrows, sms), kThreads, 0, s>>>(off, nrows, flag.as<int32_t>());
-    PR_TRY(scan_i32(flag.as<int32_t>(), pos.as<int32_t>(), nrows, cnt.as<int32_t>(), s));
-    k_rows_big_list<<<grid_of(nrows, sms), kThreads, 0, s>>>(flag.as<int32_t>(), pos.as<int32_t>(), nrows,
-                                                             list.as<int32_t>());
-    PR_TRY(scratch.alloc(sizeof(int32_t) * m, s));
-    k_rows_big<<<sms * 4, kThreads, 0, s>>>(data, scratch.as<int32_t>(), off, list.as<int32_t>(), cnt.as<int32_t>(),
-                                            bits);
-    PR_CK(cudaGetLastError());
-    PR_CK(cudaStreamSynchronize(s));  // the scratch buffers are released on return
     return PR_OK;
 }
 

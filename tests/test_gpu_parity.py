@@ -352,6 +352,54 @@ def test_pull_is_deterministic_and_graph_matches_host_loop(prec):
             assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def long_rows_graph():
+    """Rows of every length class of graph creation's row sorts (one lane up to
+    32 entries, a warp up to 1024, a block up to 8192, one radix sort beyond):
+    in-rows of 20000, 5000 and 500 entries and out-rows of 12000 and 3000 over
+    a sparse random graph."""
+    rng = np.random.default_rng(11)
+    n = 30000
+    src = [np.arange(1, 20001), np.arange(2, 5002), np.arange(3, 503), np.full(12000, 3), np.full(3000, 4),
+           rng.integers(0, n, 90000)]
+    dst = [np.zeros(20000, np.int64), np.full(5000, 1), np.full(500, 2), np.arange(4, 12004), np.arange(5, 3005),
+           rng.integers(0, n, 90000)]
+    return gg.from_edges(n, np.concatenate(src), np.concatenate(dst), drop_loops=True)
+
+
+def shuffled_rows(off, ent, seed):
+    """The entries of every row in a seeded random order."""
+    rng = np.random.default_rng(seed)
+    row = np.repeat(np.arange(off.size - 1), np.diff(off))
+    return np.ascontiguousarray(ent[np.lexsort((rng.random(ent.size), row))])
+
+
+@pytest.mark.parametrize("with_csc", (False, True))
+def test_rows_of_every_length_in_any_order(with_csc):
+    g = long_rows_graph()
+    off, dst = g.csr32()
+    ioff, isrc = g.csc32()
+    dst_s, isrc_s = shuffled_rows(off, dst, 1), shuffled_rows(ioff, isrc, 2)
+    assert not np.array_equal(dst_s, dst)
+    truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
+    extra = (ioff, isrc_s) if with_csc else ()
+    with pr.Graph(g.n, g.m, off, dst_s, *extra) as G, gpu_graph(g) as G0:
+        assert G.info["max_indeg"] == g.indeg.max() >= 20000 and G.info["max_outdeg"] == g.outdeg.max() >= 12000
+        for mode in (pr.PR_MODE_PUSH, pr.PR_MODE_PULL):
+            out = G.solve(C, 1e-12, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=mode))[0]
+            assert l1(out, truth) <= 1e-10, mode
+        # the internal lists do not depend on the order of the caller's rows: the
+        # deterministic pull rounds give the same bits on both graphs
+        out = G.solve(C, 1e-12, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=pr.PR_MODE_PULL))[0]
+        assert np.array_equal(out, G0.solve(C, 1e-12, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=pr.PR_MODE_PULL))[0])
+    if with_csc:  # one source of the longest in-row replaced by a vertex with no edge to it
+        bad = isrc_s.copy()
+        absent = np.setdiff1d(np.arange(g.n), isrc[ioff[0]:ioff[1]])[-1]
+        bad[ioff[0] + 7] = absent
+        with pytest.raises(pr.PrError) as e:
+            pr.pr_graph_create(g.n, g.m, off, dst_s, ioff, bad)
+        assert e.value.status == pr.PR_EINVAL
+
+
 def test_torch_allocator_hook():
     g = gg.rmat(12, 8, dangling=0.15, unref=0.1, seed=2)
     truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
