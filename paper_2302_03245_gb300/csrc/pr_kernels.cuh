@@ -530,12 +530,10 @@ template <int LANES> struct EntriesInFlight {
 template <typename T> struct UseTiles {
     static constexpr bool value = PR_PULL_TILES && std::is_same<T, double>::value;
 };
-// rows per warp batch of the double-precision warp rows (see kWarpBatch), and
-// the shared doubles each warp parks their partials in
+// rows per warp batch of the double-precision warp rows (see kWarpBatch)
 #ifndef PR_WARP_BATCH
 #define PR_WARP_BATCH 4
 #endif
-constexpr int kWarpBatchPark = PR_WARP_BATCH * 9;
 // A tile's pending values (in-list order) and its rows' entry offsets relative
 // to the tile's first entry, in shared memory.
 template <typename V> struct TileSmem {
@@ -547,14 +545,12 @@ template <typename T> struct TileRows {
     T v[kTileRows];
 };
 
-// The shared memory of a double-precision segment: gather tiles, or the warp
-// rows' parked partials (a block serves one segment, so they never coexist).
-template <typename T, typename V> union SegSmem {
+// The shared memory of a double-precision segment's gather tiles.
+template <typename T, typename V> struct SegSmem {
     struct {
         TileSmem<V> sm;
         TileRows<T> rs;
     } tile;
-    double park[(kThreads / 32) * kWarpBatchPark];
 };
 
 // Stages tile t: every thread first loads its kTileE / kThreads in-list
@@ -618,14 +614,13 @@ __device__ __forceinline__ typename GT<V>::A tile_row_sum(const TileSmem<V> &sm,
 // warp pays each FP64 instruction of its lane reduction and of its epilogue
 // (run by one lane) for one row.  So double-precision warp rows go through in
 // batches of kWarpBatch rows per warp: every row's 32 lanes sum their entries
-// (lane l: entries l, l + 32, ... in order, kWarpU loads in flight), reduce to
-// 8 partials by two shuffle steps, and park them in shared memory; then lane k
-// adds the 8 partials of row k in a fixed tree and runs that row's epilogue,
-// so each FP64 instruction after the gather serves kWarpBatch rows.
+// (lane l: entries l, l + 32, ... in order, kWarpU loads in flight), one
+// reduce-scatter over the warp finishes all the batch's rows with every lane
+// adding (warp_batch_sums64), and lane k runs row k's epilogue, so each FP64
+// instruction after the gather serves kWarpBatch rows.  Measured on R-MAT
+// scale 22 (IEEE FP64 pull round): batches of 2, 4 and 8 rows take 0.213,
+// 0.205 and 0.242 ms (8 rows run short of registers).
 constexpr int kWarpBatch = PR_WARP_BATCH;  // 1 turns the batches off (shuffle-reduced lane bins)
-constexpr int kParkStride = 9;  // 8 partials + 1 pad per row (bank spread)
-constexpr int kParkPerWarp = kWarpBatch * kParkStride;
-static_assert(kParkPerWarp == kWarpBatchPark, "shared memory of the warp rows");
 static_assert(kWarpBatch <= 32, "a lane finishes each row of a batch");
 
 // lane's share of row j's sum: entries off[j] + lane, + 32, ... in order,
@@ -635,7 +630,8 @@ static_assert(kWarpBatch <= 32, "a lane finishes each row of a batch");
 // warp-uniform bound; lanes past the end add an exact 0.0).  Measured on
 // R-MAT scale 22, IEEE FP64 pull round: 0.254 ms with the shuffle-reduced
 // lane bins, 0.226 ms with batches of 4 rows, 0.207 ms with batches of 4 and
-// this pipelining (8 entries per step spill at the 40-register cap).
+// this pipelining (8 entries per step spill at the 40-register cap), 0.205 ms
+// with the batch's reduce-scatter instead of partials parked in shared memory.
 constexpr int kWarpU = 4;
 template <bool NC = true>
 __device__ __forceinline__ double warp_row_part64(const int32_t *__restrict__ off, const int32_t *__restrict__ src,
@@ -669,31 +665,46 @@ __device__ __forceinline__ double warp_row_part64(const int32_t *__restrict__ of
 
 // The sums of rows j0 .. j0 + kWarpBatch - 1 (those below hi) by one warp: lane
 // k < kWarpBatch returns row j0 + k's sum.  off2/src2: an optional second
-// in-list segment, added to each lane's share before the reduction.
+// in-list segment, added to each lane's share before the reduction.  Every
+// lane keeps its share of every row of the batch; a reduce-scatter then halves
+// the rows a lane holds at each exchange (partner lane ^ 16, ^ 8, ...) until
+// each group of 32 / kWarpBatch lanes holds one row, which a butterfly over
+// the group finishes.  All 32 lanes add in every step: kWarpBatch - 1 + log2(32
+// / kWarpBatch) double adds per batch, against 2 per row plus 7 for one lane
+// per row when each row is reduced on its own.  The order of the additions is
+// fixed, so the sums do not depend on scheduling.
 template <bool NC = true>
 __device__ __forceinline__ double warp_batch_sums64(const int32_t *off, const int32_t *src, const int32_t *off2,
                                                     const int32_t *src2, int nsrc, int j0, int hi, const double *val,
-                                                    double *park, int lane) {
-#pragma unroll 1
+                                                    int lane) {
+    static_assert((kWarpBatch & (kWarpBatch - 1)) == 0, "a power of two of rows per batch");
+    constexpr int kGroup = 32 / kWarpBatch;  // lanes that end up holding one row
+    double a[kWarpBatch];
+#pragma unroll
     for (int k = 0; k < kWarpBatch; k++) {
         const int j = j0 + k;
-        double a = 0.0;
+        a[k] = 0.0;
         if (j < hi) {  // warp-uniform
-            a = warp_row_part64<NC>(off, src, nsrc, j, val, lane);
-            if (off2) a += warp_row_part64<NC>(off2, src2, nsrc, j, val, lane);
+            a[k] = warp_row_part64<NC>(off, src, nsrc, j, val, lane);
+            if (off2) a[k] += warp_row_part64<NC>(off2, src2, nsrc, j, val, lane);
         }
-        a += __shfl_down_sync(0xffffffffu, a, 16);
-        a += __shfl_down_sync(0xffffffffu, a, 8);
-        if (lane < 8) park[k * kParkStride + lane] = a;
     }
-    __syncwarp();
-    double s = 0.0;
-    if (lane < kWarpBatch) {
-        const double *p = park + lane * kParkStride;
-        s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    // reduce-scatter: after the exchange with lane ^ o a lane keeps the upper
+    // half of its rows when (lane & o), else the lower half
+#pragma unroll
+    for (int o = 16, cnt = kWarpBatch; cnt > 1; o >>= 1, cnt >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < cnt / 2; i++) {
+            const double send = upper ? a[i] : a[i + cnt / 2];
+            const double keep = upper ? a[i + cnt / 2] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
-    __syncwarp();  // park is rewritten by the next batch
-    return s;
+    // lane l now holds part of row l / kGroup; finish it over its group
+#pragma unroll
+    for (int o = kGroup / 2; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+    return __shfl_sync(0xffffffffu, a[0], (lane % kWarpBatch) * kGroup);
 }
 
 // ------------------------------------------------------------ round decision
@@ -1039,14 +1050,14 @@ template <bool IFP2, int EPI = 0>
 __device__ __forceinline__ void round_warp_rows64(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
                                                   const RoundBuf &B, const double *wprev, double *wnext,
                                                   bool use_unref, int want, uint32_t *bcnt, double &Rl, long long &Fl,
-                                                  long long &El, int &ul, double *park) {
+                                                  long long &El, int &ul) {
     constexpr int WPB = kThreads / 32;
     const int lane = threadIdx.x & 31;
     const int nbatch = (S.hi - S.lo + kWarpBatch - 1) / kWarpBatch;
     for (int bt = lb * WPB + (int)(threadIdx.x >> 5); bt < nbatch; bt += S.nblk * WPB) {
         const int j0 = S.lo + bt * kWarpBatch;
-        const double sum = warp_batch_sums64<EPI == 0>(G.inr_off, G.inr_src, use_unref ? G.inu_off : nullptr, G.inu_src, G.n_nd, j0,
-                                             S.hi, wprev, park, lane);
+        const double sum = warp_batch_sums64<EPI == 0>(G.inr_off, G.inr_src, use_unref ? G.inu_off : nullptr,
+                                                       G.inu_src, G.n_nd, j0, S.hi, wprev, lane);
         const int j = j0 + lane;
         bool act = false;
         int pd = 0;
@@ -1108,8 +1119,7 @@ __device__ __forceinline__ void round_segment(const DevGraph &G, const Seg &S, i
             return;
         }
         if (kWarpBatch > 1 && S.lanes == 32) {
-            round_warp_rows64<IFP2, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul,
-                                         smu.park + (threadIdx.x >> 5) * kParkPerWarp);
+            round_warp_rows64<IFP2, EPI>(G, S, lb, ctl, B, wprev, wnext, use_unref, want, bcnt, Rl, Fl, El, ul);
             return;
         }
     }
@@ -1897,14 +1907,13 @@ __device__ __forceinline__ void sweep_tiles(const DevGraph &G, const Seg &S, int
 // warp (see round_warp_rows64); both in-list segments are always read.
 template <int OP>
 __device__ __forceinline__ void sweep_warp_rows64(const DevGraph &G, const Seg &S, int lb, const Ctl *ctl,
-                                                  SweepArgs<double> &a, double &s1, double &s2, double &s3,
-                                                  double *park) {
+                                                  SweepArgs<double> &a, double &s1, double &s2, double &s3) {
     constexpr int WPB = kThreads / 32;
     const int lane = threadIdx.x & 31;
     const int nbatch = (S.hi - S.lo + kWarpBatch - 1) / kWarpBatch;
     for (int bt = lb * WPB + (int)(threadIdx.x >> 5); bt < nbatch; bt += S.nblk * WPB) {
         const int j0 = S.lo + bt * kWarpBatch;
-        const double sum = warp_batch_sums64(G.inr_off, G.inr_src, G.inu_off, G.inu_src, G.n_nd, j0, S.hi, a.val, park, lane);
+        const double sum = warp_batch_sums64(G.inr_off, G.inr_src, G.inu_off, G.inu_src, G.n_nd, j0, S.hi, a.val, lane);
         const int j = j0 + lane;
         if (lane < kWarpBatch && j < S.hi) sweep_epilogue<double, OP>(G, ctl, a, j, sum, s1, s2, s3);
     }
@@ -1924,7 +1933,7 @@ __device__ __forceinline__ void sweep_segment(const DevGraph &G, const Seg &S, i
             return;
         }
         if (kWarpBatch > 1 && S.lanes == 32) {
-            sweep_warp_rows64<OP>(G, S, lb, ctl, a, s1, s2, s3, smu.park + (threadIdx.x >> 5) * kParkPerWarp);
+            sweep_warp_rows64<OP>(G, S, lb, ctl, a, s1, s2, s3);
             return;
         }
     }

@@ -133,6 +133,9 @@ ROUND_GRAPHS = [
     ("small3000", lambda: gg.random_small(3000, 6.0, 0.25, 0.1, seed=2)),
     ("rmat13", lambda: gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=4)),
     ("hub20k", lambda: hub_graph(20000, 3)),
+    # the paper's losing case: every edge also taken reversed (no dangling or
+    # unreferenced vertices but the isolated ones)
+    ("undirected12", lambda: gg.rmat(12, 8, dangling=0.0, unref=0.0, undirected=True, seed=5)),
 ]
 
 
@@ -188,6 +191,29 @@ def test_rmat_scale14_all_algorithms(seed):
             assert status == pr.PR_OK and err <= 1e-6, (algo, err)
         out, st, status = G.solve(C, 1e-8, pr.PR_POWER, pr.PR_FP32)
         assert status == pr.PR_OK and l1(out, truth) <= 1e-6
+
+
+def test_undirected_rmat_every_form():
+    """The undirected stress graph (R-MAT scale 13, every sampled edge also
+    taken reversed): IFP1 and IFP2 in every delivery mode and precision, and
+    Power, against the exact PageRank, within the certified bound."""
+    g = gg.rmat(13, 8, dangling=0.0, unref=0.0, undirected=True, seed=6)
+    assert np.array_equal(np.sort(g.out_dst), np.sort(g.in_src))  # symmetric: in-lists = out-lists
+    truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
+    modes = (pr.PR_MODE_AUTO, pr.PR_MODE_PUSH, pr.PR_MODE_PULL, pr.PR_MODE_ASYNC, pr.PR_MODE_APULL)
+    with gpu_graph(g) as G:
+        for algo in (pr.PR_IFP1, pr.PR_IFP2):
+            for prec in (pr.PR_FP64, pr.PR_DF64):
+                for mode in modes:
+                    out, st, status = G.solve(C, 1e-10, algo, prec, opts=dict(mode=mode))
+                    err = l1(out, truth)
+                    assert status == pr.PR_OK and err <= 1e-9, (algo, prec, mode, err)
+                    assert err <= st["err_bound"] + 1e-13
+            out, st, status = G.solve(C, 1e-7, algo, pr.PR_FP32)
+            assert status == pr.PR_OK and l1(out, truth) <= 1e-6
+        for prec in (pr.PR_FP64, pr.PR_DF64):
+            out, st, status = G.solve(C, 1e-11, pr.PR_POWER, prec)
+            assert status == pr.PR_OK and l1(out, truth) <= st["err_bound"] + 1e-13 and l1(out, truth) <= 1e-10
 
 
 def test_ifp1_ifp2_agree_and_ifp2_pushes_less():
