@@ -469,12 +469,18 @@ pr_status pr_server_get_stats(pr_server *s, pr_server_stats *st);
  * pr_debug_inject: a test hook: the checks at `site` (0 = none) fail from the
  *   next solve on -- an index check sees half its bound, an invariant check
  *   fails outright -- so the net itself can be tested with no invalid access.
+ *   Site 6 instead makes every bounded wait of graph creation's radix sort
+ *   (a tile waiting for the counts of the tiles before it) give up at once:
+ *   creating a graph whose sorts span more than one tile (over 2048 vertices
+ *   or 4096 edges) returns PR_ECUDA, with nothing written outside its
+ *   buffers, and creations succeed again once the site is cleared.
  * Both return PR_EINVAL in a release build.
  */
 typedef struct {
     int64_t checks, fails;           /* invariant checks run; failed checks of any kind */
     int32_t first_site, pad;         /* 1 in-list source, 2 out-list target, 3 frontier entry,
-                                        4 permutation, 5 tile bounds, 16 mass, 17 identity */
+                                        4 permutation, 5 tile bounds, 16 mass, 17 identity
+                                        (6: the sort-wait test hook, never recorded) */
     int64_t first_value, first_bound;
     double max_mass_dev, max_identity_dev;
 } pr_debug_report;

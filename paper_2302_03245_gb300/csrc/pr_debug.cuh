@@ -31,6 +31,7 @@ enum {
     DBG_BIN = 3,         // frontier bin entry
     DBG_PERM = 4,        // caller id of an internal vertex (normalisation)
     DBG_TILE_ROW = 5,    // first row of a gather tile
+    DBG_SORT_WAIT = 6,   // test hook only: every look-back wait of graph creation's radix sort gives up
     DBG_MASS = 16,       // mass balance after a round (value, bound: deviation and tolerance, x 1e18)
     DBG_IDENTITY = 17,   // residual identity after a round (same units)
 };
@@ -78,6 +79,9 @@ bool dbg_reset_batch(int inject);
 bool dbg_read_batch(DbgRec *out);
 bool dbg_reset_group(int inject);
 bool dbg_read_group(DbgRec *out);
+bool dbg_reset_sort(int inject);
+// the site pr_debug_inject named (0: none)
+int dbg_injected();
 // around a single or batched solve: clear the records (keeping the injected
 // site), then collect them; a failure turns st into PR_ECHECK
 void dbg_begin(cudaStream_t s);

@@ -20,6 +20,7 @@
 #include <thread>
 #include <vector>
 
+#include "pr_debug.cuh"
 #include "pr_internal.cuh"
 #include "pr_sort.cuh"
 
@@ -1231,6 +1232,9 @@ extern "C" pr_status pr_graph_create_ex(int32_t n, int64_t m, const int32_t *out
     if (!G) return fail(PR_ENOMEM, "host allocation failed");
     static std::atomic<uint64_t> serial{0};
     G->uid = ++serial;
+#ifdef PR_DEBUG
+    dbg_reset_sort(dbg_injected());  // the radix sort's test hook (DBG_SORT_WAIT)
+#endif
     pr_status st = create_impl(n, m, out_off, out_dst, in_off, in_src, mem_is_device,
                                (cudaStream_t)cuda_stream, levels, G);
     if (!allocator_hooked()) {  // keep at most kCreationCache bytes of freed temporaries mapped

@@ -1163,6 +1163,11 @@ static void dbg_merge(const DbgRec &d) {
     g_dbg_acc.max_identity_dev = std::max(g_dbg_acc.max_identity_dev, d.max_identity_dev);
 }
 
+int dbg_injected() {
+    std::lock_guard<std::mutex> lock(g_dbg_mu);
+    return g_dbg_inject;
+}
+
 void dbg_begin(cudaStream_t s) {
 #ifdef PR_DEBUG
     cudaStreamSynchronize(s);

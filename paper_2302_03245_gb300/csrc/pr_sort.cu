@@ -13,6 +13,7 @@
 
 #include <algorithm>
 
+#include "pr_debug.cuh"
 #include "pr_internal.cuh"
 #include "pr_sort.cuh"
 
@@ -253,7 +254,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_radix_pass(const uint64_t *keys
             int64_t j = (int64_t)t - 1;
             int spins = 0;
             bool ok = true;
+#ifdef PR_DEBUG
+            // test hook of the debug build: every wait runs out at its first poll
+            const int spin_limit = g_pr_dbg.inject == DBG_SORT_WAIT ? 0 : kSpinLimit;
+#else
+            constexpr int spin_limit = kSpinLimit;
+#endif
             while (true) {
+                if (spins >= spin_limit) {
+                    ok = false;
+                    s_bad = 1;
+                    break;
+                }
                 unsigned long long v[kLookBack];
 #pragma unroll
                 for (int w = 0; w < kLookBack; w++) v[w] = j - w >= 0 ? ld_status(status + (size_t)(j - w) * kDigits + d) : 0;
@@ -271,11 +283,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_radix_pass(const uint64_t *keys
                 if (incl) break;
                 j -= used;
                 if (used == 0) {
-                    if (++spins >= kSpinLimit) {
-                        ok = false;
-                        s_bad = 1;
-                        break;
-                    }
+                    ++spins;
                     __nanosleep(32);
                 }
             }
@@ -323,6 +331,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_radix_pass(const uint64_t *keys
 }  // namespace
 
 static_assert(kThreads == kDigits, "the block scans of the sorts give one digit per thread");
+
+// host side of this translation unit's debug record (only the test hook is read)
+bool dbg_reset_sort(int inject) {
+#ifdef PR_DEBUG
+    DbgRec z{};
+    z.inject = inject;
+    return cudaMemcpyToSymbol(g_pr_dbg, &z, sizeof(z)) == cudaSuccess;
+#else
+    (void)inject;
+    return false;
+#endif
+}
 
 pr_status scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, const Scratch &sc, cudaStream_t s) {
     if (n <= 0) {

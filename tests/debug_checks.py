@@ -17,6 +17,7 @@ import paper_2302_03245_gb300 as pr  # noqa: E402
 
 C = 0.85
 DBG_IN_SRC, DBG_OUT_DST, DBG_BIN, DBG_PERM, DBG_MASS, DBG_IDENTITY = 1, 2, 3, 4, 16, 17
+DBG_SORT_WAIT = 6
 
 
 def l1(a, b):
@@ -83,6 +84,21 @@ def main():
         assert status == pr.PR_OK
         assert pr.pr_debug_report_get(reset=True)["fails"] == 0
     out["forced"] = forced
+    # graph creation's radix sort: every bounded wait gives up at once, the
+    # creation fails cleanly with PR_ECUDA, and the next creation works
+    pr.pr_debug_inject(DBG_SORT_WAIT)
+    try:
+        pr.pr_graph_create(g.n, g.m, *g.csr32())
+        raise AssertionError("the forced sort wait did not fail the creation")
+    except pr.PrError as e:
+        assert e.status == pr.PR_ECUDA and "gave up" in str(e), e
+    pr.pr_debug_inject(0)
+    with pr.Graph(g.n, g.m, *g.csr32()) as G:
+        res, st, status = G.solve(C, 1e-10, pr.PR_IFP2, pr.PR_FP64)
+        assert status == pr.PR_OK
+        assert l1(res, oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]) <= 1e-9
+    assert pr.pr_debug_report_get(reset=True)["fails"] == 0
+    out["sort_wait"] = True
     print(json.dumps(out))
 
 

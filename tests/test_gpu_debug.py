@@ -8,6 +8,8 @@ PR_LIBRARY=debug: clean solves of every algorithm, precision and delivery mode
 on small graphs must pass every check and match the oracle, and a check forced
 to fail at each site (a test hook that halves a bound or fails an invariant
 outright, so no invalid access happens) must turn the solve into PR_ECHECK.
+The bounded waits of graph creation's radix sort are made to give up at once:
+the creation must return PR_ECUDA and the next one must work.
 """
 import json
 import os
@@ -33,3 +35,4 @@ def test_debug_build_checks_hold_and_fire():
     assert res["solves"] > 150
     assert res["clean"]["fails"] == 0 and res["clean"]["checks"] > 500
     assert sorted(int(k) for k in res["forced"]) == [1, 2, 3, 4, 16, 17]
+    assert res["sort_wait"]  # graph creation's bounded waits fail cleanly
