@@ -349,7 +349,10 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
         ladder = []
         for tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11):
             ms, st = median_solve(G, flush, 2, C, tol, pr.PR_POWER, pprec, out=out)
-            ladder.append(dict(tol=tol, ms=ms, iters=st["rounds"], l1=float((out - truth).abs().sum())))
+            # Power's algorithmic bytes per iteration: m (4 + s) + n (4 + 3 s), s = 8 (FP64, double-float)
+            hb = st["rounds"] * (G.info["m"] * 12 + G.info["n"] * 28) / (ms / 1e3) / 1e9
+            ladder.append(dict(tol=tol, ms=ms, iters=st["rounds"], l1=float((out - truth).abs().sum()),
+                               hbm_frac=hb / hbm_peak))
             if ladder[-1]["l1"] <= target:
                 break
         res[f"power_{pname}_ladder"] = ladder
@@ -1006,7 +1009,11 @@ def main():
                 st = solve(algo=pr.PR_POWER, prec=pprec, eps=tol)
                 tms.append(st["ms"])
             err = accuracy()[0]
-            power.append(dict(tol=tol, ms=statistics.median(tms), l1=err, iters=st["rounds"]))
+            # Power's algorithmic bytes per iteration: m (4 + s) + n (4 + 3 s), s = the state's bytes
+            sp = 4 if pprec == pr.PR_FP32 else 8
+            hb = st["rounds"] * (info["m"] * (4 + sp) + info["n"] * (4 + 3 * sp)) / (statistics.median(tms) / 1e3) / 1e9
+            power.append(dict(tol=tol, ms=statistics.median(tms), l1=err, iters=st["rounds"],
+                              hbm_frac=hb / hbm_peak))
             if err <= ref["l1"]:
                 break
         eq = next((q for q in power if q["l1"] <= ref["l1"]), None)
@@ -1030,6 +1037,9 @@ def main():
         alg_solve += algorithmic_bytes_activate(info["n_nd"], s)
     alg_solve += info["m_d"] * (4 + s) + info["n_d"] * (8 + 2 * s)
     line["solve_hbm_frac"] = alg_solve / (t_step / 1e3) / 1e9 / hbm_peak
+    # the same figure for the GPU Power method it is compared with (IEEE FP64, equal L1)
+    pe = line["vs_power"].get("power_fp64_at_equal_l1")
+    line["power_hbm_frac"] = pe["hbm_frac"] if pe else None
 
     # ---- end to end through the C ABI with pinned host buffers
     off, dst = g.csr32()
