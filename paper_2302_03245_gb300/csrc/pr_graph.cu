@@ -1054,7 +1054,7 @@ pr_status create_impl(int32_t n, int64_t m, const int32_t *out_off, const int32_
     // first.  A second stable sort, on the src bits, orders them by (src, dst)
     // (the flag is a function of src): the out-lists.  Each sort covers B+1 or
     // B bits, where one sort of whole keys covers 2B.
-    const uint64_t low_mask = (1ULL << (B + 1)) - 1, id_mask = (1ULL << B) - 1;
+    const uint64_t id_mask = (1ULL << B) - 1;
     PR_TRY(g->out_off.alloc(sizeof(int32_t) * (n + 1), s));
     PR_TRY(g->out_dst.alloc(sizeof(int32_t) * std::max<int64_t>(m, 1), s));
     {

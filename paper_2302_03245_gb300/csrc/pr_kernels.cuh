@@ -833,7 +833,7 @@ __device__ __forceinline__ T push_mass(const Ctl *ctl, bool async, T *x, T *r, d
 template <typename T, bool IFP2>
 __device__ __forceinline__ void push_list(const DevGraph &G, T *r, double *din, int e0, int e1, T wi, int lane,
                                           int lanes) {
-    const int bound = IFP2 ? G.n_nd : G.n;
+    [[maybe_unused]] const int bound = IFP2 ? G.n_nd : G.n;  // the debug build's index check
     for (int e = e0 + lane; e < e1; e += lanes) {
         const int t = PR_IDX(G.out_dst[e], bound, DBG_OUT_DST);
         if (t >= 0) ST<T>::push_to(r, din, t, wi);

@@ -1151,6 +1151,7 @@ static std::mutex g_dbg_mu;
 static pr_debug_report g_dbg_acc{};
 static int g_dbg_inject = 0;
 
+#ifdef PR_DEBUG
 static void dbg_merge(const DbgRec &d) {
     g_dbg_acc.checks += (int64_t)d.checks;
     if (d.fails && !g_dbg_acc.fails) {
@@ -1158,6 +1159,7 @@ static void dbg_merge(const DbgRec &d) {
         g_dbg_acc.first_value = d.value;
         g_dbg_acc.first_bound = d.bound;
     }
+#endif
     g_dbg_acc.fails += (int64_t)d.fails;
     g_dbg_acc.max_mass_dev = std::max(g_dbg_acc.max_mass_dev, d.max_mass_dev);
     g_dbg_acc.max_identity_dev = std::max(g_dbg_acc.max_identity_dev, d.max_identity_dev);
