@@ -1159,11 +1159,11 @@ static void dbg_merge(const DbgRec &d) {
         g_dbg_acc.first_value = d.value;
         g_dbg_acc.first_bound = d.bound;
     }
-#endif
     g_dbg_acc.fails += (int64_t)d.fails;
     g_dbg_acc.max_mass_dev = std::max(g_dbg_acc.max_mass_dev, d.max_mass_dev);
     g_dbg_acc.max_identity_dev = std::max(g_dbg_acc.max_identity_dev, d.max_identity_dev);
 }
+#endif
 
 int dbg_injected() {
     std::lock_guard<std::mutex> lock(g_dbg_mu);
