@@ -319,7 +319,7 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
 
     eps = 1e-9
     for name, mode, reps in (("auto", pr.PR_MODE_AUTO, 3), ("pull", pr.PR_MODE_PULL, 3), ("push", pr.PR_MODE_PUSH, 2),
-                             ("async", pr.PR_MODE_ASYNC, 2)):
+                             ("async", pr.PR_MODE_ASYNC, 2), ("apull", pr.PR_MODE_APULL, 3)):
         ms, st = median_solve(G, flush, reps, C, eps, pr.PR_IFP2, pr.PR_FP32, out=out, opts=dict(mode=mode))
         res[f"ifp2_fp32_{name}"] = entry(ms, st)
     ms, st = median_solve(G, flush, 3, C, EPS_FP64, pr.PR_IFP2, pr.PR_FP32, out=out)
@@ -343,6 +343,7 @@ def leg_dag(pr, torch, stream, flush, hbm_peak, peak_src):
     # FP32 form (FP64 correction and finish) is compared with Power in FP64
     for pname, pprec, vs in (("fp64", pr.PR_FP64, "ifp2_fp64_auto"), ("df64", pr.PR_DF64, "ifp2_df64_auto"),
                              ("fp64_vs_fp32_form", pr.PR_FP64, "ifp2_fp32_auto"),
+                             ("fp64_vs_fp32_form_apull", pr.PR_FP64, "ifp2_fp32_apull"),
                              ("fp64_vs_apull", pr.PR_FP64, "ifp2_fp64_apull"),
                              ("df64_vs_apull", pr.PR_DF64, "ifp2_df64_apull")):
         target = res[vs]["l1"]
@@ -981,6 +982,7 @@ def main():
             ("ifp2_fp64_async", pr.PR_IFP2, pr.PR_FP64, EPS_FP64, pr.PR_MODE_ASYNC),
             ("ifp2_df64_async", pr.PR_IFP2, pr.PR_DF64, EPS_FP64, pr.PR_MODE_ASYNC),
             ("ifp2_fp64_apull", pr.PR_IFP2, pr.PR_FP64, EPS_FP64, pr.PR_MODE_APULL),
+            ("ifp2_fp32_apull", pr.PR_IFP2, pr.PR_FP32, EPS_FP32, pr.PR_MODE_APULL),
             ("ifp2_df64_apull", pr.PR_IFP2, pr.PR_DF64, EPS_FP64, pr.PR_MODE_APULL),
             ("ifp1_fp64_apull", pr.PR_IFP1, pr.PR_FP64, EPS_FP64, pr.PR_MODE_APULL)]
     for nm, algo, prec, eps, mode in runs:
@@ -999,7 +1001,8 @@ def main():
     # first ||delta||_1 tolerance whose L1 error is at most that solve's
     for pname, pprec, vs in (("fp64", pr.PR_FP64, "ifp2_fp64"), ("df64", pr.PR_DF64, "ifp2_df64"),
                              ("fp32", pr.PR_FP32, "ifp2_fp32"), ("fp64_vs_apull", pr.PR_FP64, "ifp2_fp64_apull"),
-                             ("df64_vs_apull", pr.PR_DF64, "ifp2_df64_apull")):
+                             ("df64_vs_apull", pr.PR_DF64, "ifp2_df64_apull"),
+                             ("fp32_vs_apull", pr.PR_FP32, "ifp2_fp32_apull")):
         ref = legs[vs]
         power = []
         for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11):

@@ -108,10 +108,13 @@ typedef enum {
                           residual the round leaves (the commits' pushes counted as
                           possibly not yet taken), so the certified bound holds.
                           Fewer rounds than synchronous ones; the schedule varies
-                          from run to run.  PR_FP64 and PR_DF64 only (the recompute
-                          cancels to the state's precision: FP32 would stall near
-                          1e-7 of the mass); PR_EINVAL with PR_POWER, PR_FP32, and in
-                          pr_solve_batch and the server */
+                          from run to run.  With PR_FP32 the recompute cancels to
+                          FP32's precision (about 1e-6 of the mass), so FP32 rounds
+                          run to a residual of max(eps, 1e-5) and IEEE FP64 rounds
+                          continue from the reserve to eps (their first recompute
+                          corrects the FP32 rounds, as the FP32 form's correction
+                          sweep does; pr_stats.fp64_rounds counts them).  PR_EINVAL
+                          with PR_POWER, and in pr_solve_batch and the server */
 } pr_mode;
 
 /*

@@ -124,6 +124,30 @@ __global__ void k_to_fp64(DevGraph G, const Ctl *ctl, const float *x32, double *
     }
 }
 
+// FP32 asynchronous pull rounds -> IEEE FP64 ones: the reserve in double and
+// the gather values q = x / ((1-c) deg) from it.  The unreferenced
+// non-dangling sources get exactly (1-c) p_i, the value they commit in round
+// 0 and keep (they receive nothing), so the unreferenced share U the FP64
+// rounds gather once agrees with them.  The FP64 rounds recompute every row's
+// residual from the reserve (Eq. 4's identity), so the first one does what
+// the FP32 form's correction sweep does.
+__global__ void k_apull_to_fp64(DevGraph G, const Ctl *ctl, const float *x32, double *x, double *q, PVals pv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.n; i += gridDim.x * blockDim.x) {
+        const bool unref = i >= G.n_ref && i < G.n_nd;
+        const double xv = unref ? ctl->one_minus_c * ST<double>::p(ctl, pv, i) : (double)x32[i];
+        x[i] = xv;
+        if (i < G.n_nd) q[i] = xv * (G.inv_deg64[i] * ctl->inv_om);
+    }
+}
+
+// the stop threshold of the next run of rounds, with a fresh decision state
+__global__ void k_set_stop(Ctl *ctl, double eps) {
+    ctl->eps = eps;
+    ctl->done = 0;
+    ctl->status = 0;
+    ctl->ticket = 0;
+}
+
 // q_u = x_u / ((1-c) deg(u)) for the IFP2 phase-2 pull
 template <typename T>
 __global__ void k_phase2_q(DevGraph G, const Ctl *ctl, const T *x, typename ST<T>::V *q) {
@@ -370,7 +394,7 @@ struct Workspace {
     struct CG {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-    } graphs[17];
+    } graphs[19];
     void drop_graphs() {
         for (auto &g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -510,6 +534,7 @@ template <> int power_key<float2>() { return 12; }
 template <typename T> static int apull_key();  // 2 per format (IFP1, IFP2)
 template <> int apull_key<double>() { return 13; }
 template <> int apull_key<float2>() { return 15; }
+template <> int apull_key<float>() { return 17; }
 
 // ------------------------------------------------------------ plans
 // The plans of a kernel instantiation: the tiled ones where its kernels carry
@@ -819,9 +844,10 @@ static pr_status setup_p(pr_graph *g, Workspace &W, const pr_pvec *p, Ctl &h, do
 // ------------------------------------------------------------ asynchronous pull rounds
 // PR_MODE_APULL: round 0 (every vertex commits p), the unreferenced sources'
 // constant share U, then pull rounds until the stop flag, inside a CUDA-graph
-// while node (kUnroll rounds per body) or host-driven.
+// while node (kUnroll rounds per body) or host-driven.  fresh = false: no
+// round 0 (the reserve and q are already set), U from the q in place.
 template <typename T, bool IFP2>
-static pr_status run_apull(pr_graph *g, Workspace &W, bool use_graph, Prof *prof) {
+static pr_status run_apull(pr_graph *g, Workspace &W, bool use_graph, Prof *prof, bool fresh = true) {
     const DevGraph &G = g->G;
     cudaStream_t s = g->stream;
     Ctl *ctl = W.ctl.as<Ctl>();
@@ -831,7 +857,7 @@ static pr_status run_apull(pr_graph *g, Workspace &W, bool use_graph, Prof *prof
     B.pv = pvals_of(W);
     const Plan &PL = plan_nd_of<T>(g);
     const int sms = g->num_sms;
-    {
+    if (fresh) {  // else the rounds continue from a reserve and q already in place
         const size_t e0 = prof ? prof->mark(s) : 0;
         k_apull_init<T, IFP2><<<grid_n(G.n_nd, sms, 8), kThreads, 0, s>>>(G, ctl, P, B, tr);
         if (prof) prof->add(PR_K_ACTIVATE, e0, prof->mark(s));
@@ -887,6 +913,11 @@ static void apull_final_residual(pr_graph *g, Workspace &W) {
 }
 
 // ------------------------------------------------------------ solve
+// PR_MODE_APULL with PR_FP32: where the FP32 rounds hand over to IEEE FP64 ones
+// (at least this residual; the FP32 recompute's own error is near 1e-6 of the
+// mass, the sum of the rows' rounding of x_j / (1 - c))
+constexpr double kApullF32Stop = 1e-5;
+
 template <typename T>
 static pr_status ifp_phase1(pr_graph *g, Workspace &W, int algo, bool use_graph, bool levels, Prof *prof) {
     if (algo == PR_IFP2) return run_rounds<T, true>(g, W, use_graph, levels, prof);
@@ -957,8 +988,6 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     if (opt.mode == PR_MODE_ASYNC && algo == PR_POWER) return fail(PR_EINVAL, "PR_MODE_ASYNC runs IFP1 and IFP2");
     const bool apull = opt.mode == PR_MODE_APULL;
     if (apull && algo == PR_POWER) return fail(PR_EINVAL, "PR_MODE_APULL runs IFP1 and IFP2");
-    if (apull && prec == PR_FP32)
-        return fail(PR_EINVAL, "PR_MODE_APULL needs PR_FP64 or PR_DF64 (its recompute cancels to the state's precision)");
     const bool levels = opt.mode == PR_MODE_LEVELS;
     if (levels && algo != PR_IFP2) return fail(PR_EINVAL, "PR_MODE_LEVELS runs IFP2 only");
     if (levels && g->levels <= 0) return fail(PR_EINVAL, "PR_MODE_LEVELS needs a graph created with levels");
@@ -1025,10 +1054,10 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
     };
     // asynchronous pull rounds: launches of round 0, the unreferenced share, the
     // rounds (kUnroll per graph body) and the finish
-    auto apull_launches = [&]() -> pr_status {
+    auto apull_launches = [&](int first_round = 0) -> pr_status {
         PR_CK(cudaMemcpyAsync(&W.hctl->round, &ctl->round, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PR_CK(cudaStreamSynchronize(s));
-        const int64_t rr = std::max(W.hctl->round - 1, 0);
+        const int64_t rr = std::max(W.hctl->round - first_round - (first_round ? 0 : 1), 0);
         launches += 2 + ((use_graph && !prof) ? ((rr + kUnroll - 1) / kUnroll + 1) * (kUnroll + 1) : rr);
         return PR_OK;
     };
@@ -1047,6 +1076,31 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         }
         finish_ifp<double>(g, W, algo, dout, launches);
         launches += 1;
+    } else if (apull && prec == PR_FP32) {
+        // FP32 asynchronous pull rounds down to max(eps, kApullF32Stop), where
+        // the recompute's cancellation in FP32 (about 1e-6 of the mass) is
+        // still well below the residual; then IEEE FP64 asynchronous pull
+        // rounds from the reserve to eps
+        k_init_state<float><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s32.x.as<float>(), W.s32.r.as<float>());
+        k_set_stop<<<1, 1, 0, s>>>(ctl, std::max(eps, kApullF32Stop));
+        if (algo == PR_IFP2) PR_TRY((run_apull<float, true>(g, W, use_graph, prof)));
+        else PR_TRY((run_apull<float, false>(g, W, use_graph, prof)));
+        PR_TRY(apull_launches());
+        const int32_t r32_rounds = W.hctl->round;
+        double *x64 = W.s64.x.as<double>(), *r64 = W.s64.r.as<double>();
+        k_init_state<double><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, x64, r64);
+        k_apull_to_fp64<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), x64, W.s64.w[0].as<double>(), pv);
+        k_set_stop<<<1, 1, 0, s>>>(ctl, eps);
+        if (algo == PR_IFP2) PR_TRY((run_apull<double, true>(g, W, use_graph, prof, false)));
+        else PR_TRY((run_apull<double, false>(g, W, use_graph, prof, false)));
+        PR_TRY(apull_launches(r32_rounds));
+        fp64_rounds = W.hctl->round - r32_rounds;
+        if (algo == PR_IFP1) {
+            apull_final_residual<double>(g, W);
+            launches += 1;
+        }
+        finish_ifp<double>(g, W, algo, dout, launches);
+        launches += 5;  // the two inits, the conversion, the two stop settings
     } else if (apull) {  // double-float
         PR_CK(cudaMemsetAsync(W.sdf.din.p, 0, sizeof(double) * G.n, s));
         k_init_state<float2><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.sdf.x.as<float2>(), W.sdf.r.as<float2>());

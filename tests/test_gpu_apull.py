@@ -123,7 +123,48 @@ def test_apull_round_cap_and_refusals():
     with pr.Graph(g.n, g.m, *g.csr32()) as G:
         out, st, s = G.solve(C, 1e-14, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=pr.PR_MODE_APULL, max_rounds=3))
         assert s == pr.PR_ENOTCONV and st["rounds"] == 3
-        for algo, prec in ((pr.PR_POWER, pr.PR_FP64), (pr.PR_IFP2, pr.PR_FP32)):
-            with pytest.raises(pr.PrError) as e:
-                G.solve(C, 1e-9, algo, prec, opts=dict(mode=pr.PR_MODE_APULL))
-            assert e.value.status == pr.PR_EINVAL
+        with pytest.raises(pr.PrError) as e:
+            G.solve(C, 1e-9, pr.PR_POWER, pr.PR_FP64, opts=dict(mode=pr.PR_MODE_APULL))
+        assert e.value.status == pr.PR_EINVAL
+
+
+@pytest.mark.parametrize("gcase", GRAPHS, ids=lambda c: c[0])
+@pytest.mark.parametrize("algo", (pr.PR_IFP1, pr.PR_IFP2))
+def test_apull_fp32_form(gcase, algo):
+    """PR_FP32 with asynchronous pull rounds: FP32 rounds to a residual of 1e-5
+    (or eps, if larger), then IEEE FP64 rounds from the reserve, whose first
+    recompute corrects what the FP32 rounds left.  At the FP32 form's stop
+    (5e-7) the result meets the FP32 gate; asked for 1e-11 it reaches FP64
+    accuracy, within the certified bound."""
+    g = gcase[1]()
+    p = gg.p_uniform(g.n)
+    truth = oracle.power(g, C, p, tol=1e-15)[0]
+    with pr.Graph(g.n, g.m, *g.csr32()) as G:
+        for eps, gate in ((5e-7, 1e-6), (1e-11, 1e-9)):
+            for use_graph in (0, -1):
+                out, st, s = G.solve(C, eps, algo, pr.PR_FP32, opts=dict(mode=pr.PR_MODE_APULL, use_graph=use_graph))
+                assert s == pr.PR_OK, pr.pr_last_error()
+                err = l1(out, truth)
+                assert st["resid_l1"] <= eps and err <= gate, (eps, err)
+                assert err <= st["err_bound"] + 1e-13
+                assert abs(float(np.sum(out)) - 1.0) < 1e-12
+                assert 0 < st["fp64_rounds"] < st["rounds"]
+
+
+def test_apull_fp32_form_personalized_and_loose_stop():
+    g = gg.rmat(13, 8, dangling=0.15, unref=0.10, seed=11)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(g.n, size=9, replace=False).astype(np.int32)
+    val = rng.uniform(0.5, 2.0, size=9)
+    pv = np.zeros(g.n)
+    np.add.at(pv, idx, val)
+    pv /= pv.sum()
+    truth = oracle.power(g, C, pv, tol=1e-15)[0]
+    with pr.Graph(g.n, g.m, *g.csr32()) as G:
+        for algo in (pr.PR_IFP1, pr.PR_IFP2):
+            out, st, s = G.solve(C, 1e-10, algo, pr.PR_FP32, p=val, p_idx=idx, opts=dict(mode=pr.PR_MODE_APULL))
+            assert s == pr.PR_OK and l1(out, truth) <= min(1e-9, st["err_bound"] + 1e-13)
+            # a stop above the hand-over point: the FP32 rounds reach it, one FP64 round confirms it
+            out, st, s = G.solve(C, 1e-4, algo, pr.PR_FP32, p=val, p_idx=idx, opts=dict(mode=pr.PR_MODE_APULL))
+            assert s == pr.PR_OK and l1(out, truth) <= st["err_bound"] + 1e-12
+            assert st["fp64_rounds"] >= 1
