@@ -109,9 +109,11 @@ typedef enum {
                           possibly not yet taken), so the certified bound holds.
                           Fewer rounds than synchronous ones; the schedule varies
                           from run to run.  With PR_FP32 the recompute cancels to
-                          FP32's precision (about 1e-6 of the mass), so FP32 rounds
-                          run to a residual of max(eps, 1e-5) and IEEE FP64 rounds
-                          continue from the reserve to eps (their first recompute
+                          FP32's precision (at most about 1.2e-7/(1-c) of the mass),
+                          so FP32 rounds run to a residual of max(eps, ten times
+                          that) -- or until the residual stops falling -- and
+                          IEEE FP64 rounds continue from the reserve to eps (their
+                          first recompute
                           corrects the FP32 rounds, as the FP32 form's correction
                           sweep does; pr_stats.fp64_rounds counts them).  PR_EINVAL
                           with PR_POWER, and in pr_solve_batch and the server */

@@ -84,6 +84,11 @@ struct Ctl {
     // 1 the first level-ordered round, 2 level-ordered, 3 commit only: the
     // round cap stops the run at the start of the first level-ordered round)
     int32_t gs_phase, pad6;
+    // asynchronous pull rounds that hand over to another precision: the run
+    // also ends once R has not fallen below 0.9 of its best for stall_cap
+    // rounds (0: never)
+    int32_t stall_cap, stall;
+    double r_best;
 };
 
 struct Partials {
@@ -1306,6 +1311,14 @@ __device__ __forceinline__ void apull_decision(Ctl *ctl, int t, double R, long l
     } else if (t + 1 >= ctl->max_rounds) {
         ctl->done = 1;
         ctl->status = 1;
+    } else if (ctl->stall_cap > 0) {  // a hand-over run: R stopped falling, hand over now
+        if (R < 0.9 * ctl->r_best) {
+            ctl->r_best = R;
+            ctl->stall = 0;
+        } else if (++ctl->stall >= ctl->stall_cap) {
+            ctl->done = 1;
+            ctl->status = 0;
+        }
     }
 }
 

@@ -141,11 +141,15 @@ __global__ void k_apull_to_fp64(DevGraph G, const Ctl *ctl, const float *x32, do
 }
 
 // the stop threshold of the next run of rounds, with a fresh decision state
-__global__ void k_set_stop(Ctl *ctl, double eps) {
+// (stall_cap > 0: the run also ends when R stops falling; see Ctl)
+__global__ void k_set_stop(Ctl *ctl, double eps, int stall_cap) {
     ctl->eps = eps;
     ctl->done = 0;
     ctl->status = 0;
     ctl->ticket = 0;
+    ctl->stall_cap = stall_cap;
+    ctl->stall = 0;
+    ctl->r_best = 1e300;
 }
 
 // q_u = x_u / ((1-c) deg(u)) for the IFP2 phase-2 pull
@@ -913,10 +917,16 @@ static void apull_final_residual(pr_graph *g, Workspace &W) {
 }
 
 // ------------------------------------------------------------ solve
-// PR_MODE_APULL with PR_FP32: where the FP32 rounds hand over to IEEE FP64 ones
-// (at least this residual; the FP32 recompute's own error is near 1e-6 of the
-// mass, the sum of the rows' rounding of x_j / (1 - c))
-constexpr double kApullF32Stop = 1e-5;
+// PR_MODE_APULL with PR_FP32: the FP32 rounds hand over to IEEE FP64 ones at a
+// residual kApullF32Margin times the FP32 recompute's own error, which is at
+// most about 2 x 2^-24 / (1 - c) of the mass (the rounding of every stored
+// x_j / (1 - c) and q_i, summed over the rows; the gathered sums are double):
+// 7.9e-6 at c = 0.85.  Should R stop falling first (kApullF32Stall rounds
+// without a 10% gain), they hand over then.  Measured on R-MAT scale 22 and
+// the scale-24 DAG-heavy graph: the FP32 rounds still fall below 5e-7, and
+// handing over at 1e-6 instead of 1e-5 saves 3-5% of the time.
+constexpr double kApullF32Margin = 10.0;
+constexpr int kApullF32Stall = 8;
 
 template <typename T>
 static pr_status ifp_phase1(pr_graph *g, Workspace &W, int algo, bool use_graph, bool levels, Prof *prof) {
@@ -1077,12 +1087,12 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         finish_ifp<double>(g, W, algo, dout, launches);
         launches += 1;
     } else if (apull && prec == PR_FP32) {
-        // FP32 asynchronous pull rounds down to max(eps, kApullF32Stop), where
-        // the recompute's cancellation in FP32 (about 1e-6 of the mass) is
-        // still well below the residual; then IEEE FP64 asynchronous pull
-        // rounds from the reserve to eps
+        // FP32 asynchronous pull rounds down to max(eps, the hand-over point),
+        // where the recompute's cancellation in FP32 is still well below the
+        // residual; then IEEE FP64 asynchronous pull rounds from the reserve to eps
         k_init_state<float><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, W.s32.x.as<float>(), W.s32.r.as<float>());
-        k_set_stop<<<1, 1, 0, s>>>(ctl, std::max(eps, kApullF32Stop));
+        const double handover = kApullF32Margin * 2.0 * std::ldexp(1.0, -24) / (1.0 - c);
+        k_set_stop<<<1, 1, 0, s>>>(ctl, std::max(eps, handover), kApullF32Stall);
         if (algo == PR_IFP2) PR_TRY((run_apull<float, true>(g, W, use_graph, prof)));
         else PR_TRY((run_apull<float, false>(g, W, use_graph, prof)));
         PR_TRY(apull_launches());
@@ -1090,7 +1100,7 @@ static pr_status solve_impl(pr_graph *g, double c, double eps, pr_algo algo, pr_
         double *x64 = W.s64.x.as<double>(), *r64 = W.s64.r.as<double>();
         k_init_state<double><<<gn, kThreads, 0, s>>>(G.n, ctl, pv, x64, r64);
         k_apull_to_fp64<<<gn, kThreads, 0, s>>>(G, ctl, W.s32.x.as<float>(), x64, W.s64.w[0].as<double>(), pv);
-        k_set_stop<<<1, 1, 0, s>>>(ctl, eps);
+        k_set_stop<<<1, 1, 0, s>>>(ctl, eps, 0);
         if (algo == PR_IFP2) PR_TRY((run_apull<double, true>(g, W, use_graph, prof, false)));
         else PR_TRY((run_apull<double, false>(g, W, use_graph, prof, false)));
         PR_TRY(apull_launches(r32_rounds));

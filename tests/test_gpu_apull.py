@@ -131,8 +131,8 @@ def test_apull_round_cap_and_refusals():
 @pytest.mark.parametrize("gcase", GRAPHS, ids=lambda c: c[0])
 @pytest.mark.parametrize("algo", (pr.PR_IFP1, pr.PR_IFP2))
 def test_apull_fp32_form(gcase, algo):
-    """PR_FP32 with asynchronous pull rounds: FP32 rounds to a residual of 1e-5
-    (or eps, if larger), then IEEE FP64 rounds from the reserve, whose first
+    """PR_FP32 with asynchronous pull rounds: FP32 rounds to a residual of about
+    8e-6 (or eps, if larger), then IEEE FP64 rounds from the reserve, whose first
     recompute corrects what the FP32 rounds left.  At the FP32 form's stop
     (5e-7) the result meets the FP32 gate; asked for 1e-11 it reaches FP64
     accuracy, within the certified bound."""
@@ -168,3 +168,17 @@ def test_apull_fp32_form_personalized_and_loose_stop():
             out, st, s = G.solve(C, 1e-4, algo, pr.PR_FP32, p=val, p_idx=idx, opts=dict(mode=pr.PR_MODE_APULL))
             assert s == pr.PR_OK and l1(out, truth) <= st["err_bound"] + 1e-12
             assert st["fp64_rounds"] >= 1
+
+
+@pytest.mark.parametrize("c", (0.5, 0.95))
+def test_apull_fp32_form_other_damping(c):
+    """The hand-over point follows 1/(1-c): at c = 0.95 it is three times
+    higher than at 0.85; the FP64 rounds still end at eps."""
+    g = gg.rmat(12, 8, dangling=0.2, unref=0.1, seed=13)
+    truth = oracle.power(g, c, gg.p_uniform(g.n), tol=1e-15)[0]
+    with pr.Graph(g.n, g.m, *g.csr32()) as G:
+        for algo in (pr.PR_IFP1, pr.PR_IFP2):
+            out, st, s = G.solve(c, 1e-11, algo, pr.PR_FP32, opts=dict(mode=pr.PR_MODE_APULL))
+            assert s == pr.PR_OK and st["resid_l1"] <= 1e-11
+            assert l1(out, truth) <= st["err_bound"] + 1e-13
+            assert 0 < st["fp64_rounds"] < st["rounds"]
