@@ -426,6 +426,31 @@ def test_rows_of_every_length_in_any_order(with_csc):
         assert e.value.status == pr.PR_EINVAL
 
 
+def exact_graph(n, m, seed):
+    """A graph of exactly m distinct edges (self loops allowed) on n vertices."""
+    rng = np.random.default_rng(seed)
+    code = rng.choice(n * n, size=m, replace=False)
+    return gg.from_edges(n, code // n, code % n)
+
+
+@pytest.mark.parametrize("n,m", [(2047, 4095), (2048, 4096), (2049, 4097), (3000, 8192), (4500, 12289),
+                                 (4096, 20480), (20000, 61439)])
+def test_graph_sizes_at_the_sort_tile_edges(n, m):
+    """Graph creation sorts vertex keys in tiles of 2048 and edge keys in tiles
+    of 4096: counts on either side of those edges, and several ragged tiles."""
+    g = exact_graph(n, m, seed=n + m)
+    assert g.m == m
+    truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
+    ioff, isrc = g.csc32()
+    for extra in ((), (ioff, isrc)):
+        with pr.Graph(g.n, g.m, *g.csr32(), *extra) as G:
+            I = G.info
+            assert (I["m"], I["max_indeg"], I["max_outdeg"]) == (m, g.indeg.max(), g.outdeg.max())
+            for mode in (pr.PR_MODE_PUSH, pr.PR_MODE_PULL):
+                out = G.solve(C, 1e-12, pr.PR_IFP2, pr.PR_FP64, opts=dict(mode=mode))[0]
+                assert l1(out, truth) <= 1e-10, (n, m, mode)
+
+
 def test_torch_allocator_hook():
     g = gg.rmat(12, 8, dangling=0.15, unref=0.1, seed=2)
     truth = oracle.power(g, C, gg.p_uniform(g.n), tol=1e-15)[0]
