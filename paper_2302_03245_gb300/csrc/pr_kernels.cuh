@@ -85,7 +85,7 @@ struct Ctl {
     // round cap stops the run at the start of the first level-ordered round)
     int32_t gs_phase, pad6;
     // asynchronous pull rounds that hand over to another precision: the run
-    // also ends once R has not fallen below 0.9 of its best for stall_cap
+    // also ends once R has not fallen below 0.99 of its best for stall_cap
     // rounds (0: never)
     int32_t stall_cap, stall;
     double r_best;
@@ -1312,7 +1312,7 @@ __device__ __forceinline__ void apull_decision(Ctl *ctl, int t, double R, long l
         ctl->done = 1;
         ctl->status = 1;
     } else if (ctl->stall_cap > 0) {  // a hand-over run: R stopped falling, hand over now
-        if (R < 0.9 * ctl->r_best) {
+        if (R < 0.99 * ctl->r_best) {
             ctl->r_best = R;
             ctl->stall = 0;
         } else if (++ctl->stall >= ctl->stall_cap) {

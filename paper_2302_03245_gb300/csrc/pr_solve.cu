@@ -922,7 +922,7 @@ static void apull_final_residual(pr_graph *g, Workspace &W) {
 // most about 2 x 2^-24 / (1 - c) of the mass (the rounding of every stored
 // x_j / (1 - c) and q_i, summed over the rows; the gathered sums are double):
 // 7.9e-6 at c = 0.85.  Should R stop falling first (kApullF32Stall rounds
-// without a 10% gain), they hand over then.  Measured on R-MAT scale 22 and
+// without a 1% gain), they hand over then.  Measured on R-MAT scale 22 and
 // the scale-24 DAG-heavy graph: the FP32 rounds still fall below 5e-7, and
 // handing over at 1e-6 instead of 1e-5 saves 3-5% of the time.
 constexpr double kApullF32Margin = 10.0;

@@ -182,3 +182,15 @@ def test_apull_fp32_form_other_damping(c):
             assert s == pr.PR_OK and st["resid_l1"] <= 1e-11
             assert l1(out, truth) <= st["err_bound"] + 1e-13
             assert 0 < st["fp64_rounds"] < st["rounds"]
+
+
+def test_apull_fp32_form_slow_contraction():
+    """A directed cycle at c = 0.99: the residual falls by only 1% a round, the
+    FP32 rounds run long before the hand-over; the result is still the exact
+    uniform vector."""
+    n = 64
+    with pr.Graph(n, n, *gg.cycle(n).csr32()) as G:
+        for algo in (pr.PR_IFP1, pr.PR_IFP2):
+            out, st, s = G.solve(0.99, 1e-10, algo, pr.PR_FP32, opts=dict(mode=pr.PR_MODE_APULL))
+            assert s == pr.PR_OK and st["fp64_rounds"] > 0
+            assert l1(out, np.full(n, 1.0 / n)) <= max(1e-10, st["err_bound"] + 1e-13)
